@@ -1,0 +1,314 @@
+"""Throughput benchmark of the fused axisymmetric MRT-LB step on GB300.
+
+Workload (one GPU): the single large porous annulus, nr x nz = 4096 x 8192, R* = 2,
+porosity = seeded uniform[0.3, 0.9] white noise smoothed by a Gaussian of sigma = 16
+cells (seed 2), Da = 1e-4, Ra = 1e6, Pr = 0.71, Ergun drag, FP32 arithmetic; storage
+FP32 by default (--storage f16 / bf16 for deviation storage).  A step is one pass
+of the whole hot path over the domain: pull streaming, wall rebuild, recovery,
+MRT + D2Q5 collision, store.  The state (3.8 GB in FP32) is far larger than L2,
+so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the domain (no data
+exchange; weak scaling); value = all ranks' node updates / max time over ranks.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample
+of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NR, NZ = 4096, 8192
+WORKLOAD = dict(nr=NR, nz=NZ, radius_ratio=2.0, Ra=1e6, Da=1e-4, Pr=0.71, F_eps=-1.0)
+PHI_RECIPE = dict(lo=0.3, hi=0.9, sigma=16.0, seed=2)
+METRIC = "MLUPS & % HBM roofline; time-to-steady vs plain FP32 GPU at |ΔNu|≤1e-3"
+SAMPLE_NR, SAMPLE_NZ = 256, 512   # bounded CPU sample: the same recipe on a 256 x 512 annulus
+
+
+def _set_grid(nr: int, nz: int):
+    global NR, NZ
+    NR, NZ = nr, nz
+    WORKLOAD.update(nr=nr, nz=nz)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload_name(storage):
+    return (f"porous annulus {NR}x{NZ}, R*=2, phi~U[0.3,0.9] smoothed sigma=16 (seed 2), "
+            f"Ra=1e6, Da=1e-4, Pr=0.71, Ergun drag, {storage} storage")
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.05)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1409_5929_gb300 import inputs, lbm
+
+    torch.cuda.set_device(local_rank)
+    phi = inputs.porosity_field(NR, NZ, PHI_RECIPE["lo"], PHI_RECIPE["hi"], PHI_RECIPE["sigma"], PHI_RECIPE["seed"])
+    p = lbm.lbm_params_default(storage=args.storage, eps_mean=float(phi.mean(dtype=np.float64)), **WORKLOAD)
+    s = lbm.Solver(p)
+    stream = torch.cuda.Stream()
+    s.set_stream(stream.cuda_stream)
+    s.set_porosity(phi)
+    s.init_fields()
+    info = s.info()
+    nodes = NR * NZ
+    interior = (NR - 2) * (NZ - 2)
+    es = 4 if args.storage == "f32" else 2
+    bulk_bytes = interior * (28 * es + es)          # algorithmic bytes of one bulk launch
+
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    lbm.lbm_set_timing(s.h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    bulk_ms, bulk_n, wall_ms, wall_n = lbm.lbm_kernel_times(s.h)
+    lbm.lbm_set_timing(s.h, False)
+    ck = clocks.stop()
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        if world > 1:
+            dist.barrier()
+    ms_max = float(t.item())
+    value = world * nodes * args.steps / (ms_max * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: upload the porosity field from
+    # pinned host memory, one step, read the Nusselt numbers back (synchronising)
+    ke = max(3, min(args.steps // 10, 50))
+    phi_pinned = torch.from_numpy(phi).pin_memory()
+    nu = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        lbm.lbm_set_porosity(s.h, phi_pinned.data_ptr(), False)
+        s.step(1)
+        nu = s.nusselt()
+    t1 = time.perf_counter()
+    te = torch.tensor([t1 - t0], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = world * nodes * ke / float(te.item()) / 1e6
+    s.close()
+    if rank != 0:
+        return None
+
+    peak, peak_kind = _peaks()
+    bulk_avg = bulk_ms / max(bulk_n, 1)
+    achieved = bulk_bytes / (bulk_avg * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": _workload_name(args.storage), "storage": args.storage, "nodes": nodes,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "state larger than L2 (no flush)",
+                   "bytes_per_step": info.bytes_per_step},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": f"k_bulk<{args.storage}>", "peak_source": f"{peak_kind} hbm_gbs",
+                     "avg_launch_ms": round(bulk_avg, 5), "bytes_per_launch": bulk_bytes,
+                     "wall_kernel_avg_ms": round(wall_ms / max(wall_n, 1), 5)},
+        "e2e": {"value": round(e2e_val, 2), "unit": "MLUPS", "h2d_bytes_per_step": nodes * 4,
+                "d2h_bytes_per_step": 16, "steps": ke, "nusselt": list(nu) if nu else None},
+        "gpu_launches": 2 * args.steps,
+        "clocks": ck,
+    }
+    return line
+
+
+def cpu_sample(seconds: float):
+    """The oracle as it stands on a bounded sample: the same recipe on a 256 x 512
+    annulus, all host cores, timed for about `seconds`."""
+    from oracle import oracle as O
+
+    from paper_1409_5929_gb300 import inputs
+
+    O.build()
+    phi = inputs.porosity_field(SAMPLE_NR, SAMPLE_NZ, PHI_RECIPE["lo"], PHI_RECIPE["hi"], PHI_RECIPE["sigma"],
+                                PHI_RECIPE["seed"])
+    p = O.params(nr=SAMPLE_NR, nz=SAMPLE_NZ, radius_ratio=2.0, Ra=1e6, Da=1e-4, Pr=0.71, F_eps=-1.0,
+                 eps_mean=float(phi.mean(dtype=np.float64)))
+    st = O.State(p, phi=phi.astype(np.float64))
+    cores = os.cpu_count() or 1
+    st.run(2, cores)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        st.run(10, cores)
+        steps += 10
+    dt = time.perf_counter() - t0
+    mlups = SAMPLE_NR * SAMPLE_NZ * steps / dt / 1e6
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, same recipe on a {SAMPLE_NR}x{SAMPLE_NZ} annulus, {steps} steps, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    from oracle import oracle as O
+
+    from paper_1409_5929_gb300 import inputs
+
+    O.build()
+    phi = inputs.porosity_field(SAMPLE_NR, SAMPLE_NZ, PHI_RECIPE["lo"], PHI_RECIPE["hi"], PHI_RECIPE["sigma"],
+                                PHI_RECIPE["seed"])
+    p = O.params(nr=SAMPLE_NR, nz=SAMPLE_NZ, radius_ratio=2.0, Ra=1e6, Da=1e-4, Pr=0.71, F_eps=-1.0,
+                 eps_mean=float(phi.mean(dtype=np.float64)))
+    st = O.State(p, phi=phi.astype(np.float64))
+    cores = os.cpu_count() or 1
+    st.run(args.warmup, cores)
+    t0 = time.perf_counter()
+    st.run(args.steps, cores)
+    dt = time.perf_counter() - t0
+    value = SAMPLE_NR * SAMPLE_NZ * args.steps / dt / 1e6
+    sample = f"FP64 oracle, same recipe on a {SAMPLE_NR}x{SAMPLE_NZ} annulus, {args.steps} steps"
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _workload_name("f64") + f" (sampled at {SAMPLE_NR}x{SAMPLE_NZ})"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--nr", type=int, default=NR, help="override the grid (profiling of small cases only)")
+    ap.add_argument("--nz", type=int, default=NZ)
+    args = ap.parse_args()
+    _set_grid(args.nr, args.nz)
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            ref_args = argparse.Namespace(steps=min(args.steps, 40), warmup=min(args.warmup, 3))
+            print(json.dumps(run_reference(ref_args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    from paper_1409_5929_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        line["cpu_baseline"] = cpu_sample(args.cpu_seconds) if world == 1 else None
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

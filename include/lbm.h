@@ -1,0 +1,194 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) axisymmetric MRT lattice Boltzmann solver
+ * for thermal flow in porous media at the REV scale (Liu, He & Li, arXiv 1409.5929).
+ *
+ * The paper states its problem (Sec. 4.2-4.4, Fig. 3) as: a vertical annulus
+ * r_i <= r <= r_o, 0 <= z <= H, filled with a porous medium of porosity phi
+ * (Eq. 8); parameters Ra, Da, Pr, J, lambda, F_phi (Eq. 9); a hot inner wall, a cold
+ * outer wall, adiabatic top and bottom, no slip; fluid initially at rest; the
+ * average Nusselt numbers of Eq. 42 as the result.  This interface follows that
+ * statement: create a problem, give it a porosity field, step it, read the fields,
+ * the Nusselt numbers and the convergence residual.
+ *
+ * One time step (Sec. 3.1-3.2) at every node is: pull streaming (Eq. 22, 33);
+ * non-equilibrium extrapolation at wall nodes (Sec. 4, ref. [47]); T (Eq. 38),
+ * rho (Eq. 26), u from the quadratic drag relation (Eq. 28-30); body force
+ * (Eq. 6-7), axisymmetric force a_r (Eq. 25) and moment-space source (Eq. 24);
+ * MRT relaxation in moment space (Eq. 21, 23) and f+ = M^-1 m+ (Eq. 22); the D2Q5
+ * temperature update with its axisymmetric source (Eq. 33-37).
+ *
+ * Grid and units (lattice units, delta_t = delta_r = 1, c = 1, rho0 = 1):
+ *   nodes (kr, kz), 0 <= kr < nr, 0 <= kz < nz; z is the fastest index of every
+ *   nr*nz array this interface reads or writes (row-major [kr][kz]).
+ *   Annulus: walls are the outermost nodes; L = nr - 1, H = nz - 1,
+ *   r_i = L / (R* - 1), r(kr) = r_i + kr.  Corners belong to the side walls.
+ *   Pipe (periodic z): the axis lies half a cell below row 0, r(kr) = kr + 1/2,
+ *   row nr - 1 is the no-slip wall, L = nr - 1/2.
+ *
+ * Conventions for every entry point:
+ *   - Returns LBM_OK (0) or a positive LBM_ERR_* code; lbm_last_error() then gives
+ *     a message (thread-local, valid until the next call on that thread).
+ *   - No exception or longjmp crosses the interface.
+ *   - A handle owns all its device memory; it is not thread-safe (one thread at a
+ *     time per handle).  Input arrays are copied; the caller keeps ownership of
+ *     every pointer it passes.
+ *   - Device work is queued on the handle's stream (lbm_set_stream); calls that
+ *     return host data synchronise that stream.
+ *   - on_device = 1: the pointer is CUDA device memory on the handle's device;
+ *     on_device = 0: ordinary (or pinned) host memory.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK 0
+#define LBM_ERR_INVALID 1   /* bad argument or parameter (tau <= 1/2, phi outside (0, 1], ...) */
+#define LBM_ERR_CUDA 2      /* a CUDA runtime call failed */
+#define LBM_ERR_OOM 3       /* device or pinned host allocation failed */
+#define LBM_ERR_DIVERGED 4  /* NaN or Inf found in the fields */
+#define LBM_ERR_TIMEOUT 5   /* a bounded device wait ran out */
+
+/* geometry */
+#define LBM_ANNULUS 0             /* Fig. 3: walls on all four sides */
+#define LBM_ANNULUS_PERIODIC_Z 1  /* side walls only, periodic in z */
+#define LBM_PIPE_PERIODIC_Z 2     /* axis (specular image row) + outer wall, periodic in z */
+
+/* storage type of the distributions between steps (arithmetic is always FP32) */
+#define LBM_F32 0
+#define LBM_F16 1
+#define LBM_BF16 2
+
+/* node classes written by lbm_node_class */
+#define LBM_FLUID 0
+#define LBM_WALL_IN 1
+#define LBM_WALL_OUT 2
+#define LBM_BOTTOM 3
+#define LBM_TOP 4
+#define LBM_AXIS 5
+
+typedef struct lbm_params {
+    int32_t nr, nz;          /* grid; both >= 3 */
+    int32_t geometry;        /* LBM_ANNULUS, LBM_ANNULUS_PERIODIC_Z, LBM_PIPE_PERIODIC_Z */
+    int32_t storage;         /* LBM_F32, LBM_F16, LBM_BF16 */
+    double radius_ratio;     /* R* = r_o / r_i > 1 (annulus geometries) */
+    double Ra, Da, Pr, J, lambda;  /* Eq. 9; the paper uses J = lambda = 1 (Sec. 4) */
+    double Ma;               /* Mach number of Eq. 39 (0.1 in the paper); unused if tau_nu > 0 */
+    double tau_nu;           /* > 0: viscous relaxation time given; <= 0: from Eq. 39 */
+    double F_eps;            /* < 0: Ergun F_phi per node (Eq. 8); 0: no Forchheimer drag; > 0: constant */
+    double eps_mean;         /* porosity that, with Da, fixes the particle diameter of Eq. 8;
+                                1 = no solid matrix (K = Da L^2 everywhere) */
+    double T_hot, T_cold;    /* inner and outer wall temperatures; T0 = (T_hot + T_cold) / 2 */
+    double body_accel_z;     /* z component of the external acceleration a of Eq. 7 */
+    double init_noise;       /* cold start: T = T0 + init_noise * U(-1, 1) on non-wall nodes */
+    uint64_t seed;           /* SplitMix64 seed of that noise (draw number kr*nz + kz) */
+} lbm_params;
+
+/* Derived lattice constants (Eq. 9, 31, 39), for checks and reporting. */
+typedef struct lbm_info {
+    double L, H, r0;         /* characteristic length, height, r(kr = 0) */
+    double tau_nu, tau_T;    /* relaxation times (Eq. 39) */
+    double nu_e, nu;         /* effective and fluid kinematic viscosity (Eq. 31, J) */
+    double gbeta;            /* g * beta from U = Ma c_s = sqrt(g beta dT L) */
+    double T0;               /* reference temperature */
+    double Ma;
+    double Kbar;             /* Da * L^2 */
+    int64_t steps;           /* steps taken since the last (re)initialisation */
+    int64_t bytes_per_step;  /* algorithmic HBM bytes of one step: read + write of every
+                                population and one porosity read per node */
+} lbm_info;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Fill *p with the porous-annulus defaults (48 x 96, R* = 2, eps = 0.6, Da = 1e-2,
+ * Ra = 1e3, Pr = 1, J = lambda = 1, Ma = 0.1, Ergun F_eps, T_hot = 1, T_cold = 0,
+ * noise 1e-3, seed 1, FP32 storage). */
+void lbm_params_default(lbm_params *p);
+
+/* Validate *p and derive the lattice constants without touching a GPU. */
+int lbm_derive(const lbm_params *p, lbm_info *out);
+
+/* Allocate a problem on the current CUDA device: two state buffers (A/B),
+ * the porosity field (uniform eps_mean) and scratch; cold start (rho = 1, u = 0,
+ * noisy T).  *out receives the handle.  LBM_ERR_OOM if memory runs out. */
+int lbm_create(const lbm_params *p, lbm_handle **out);
+
+/* Queue all further device work of h on `stream` (a cudaStream_t, e.g. from
+ * torch.cuda.Stream.cuda_stream); NULL = the legacy default stream. */
+int lbm_set_stream(lbm_handle *h, void *stream);
+
+/* Replace the porosity field by phi[nr*nz] (each value in (0, 1]).  Takes effect
+ * from the next step; the state is not re-initialised (call lbm_init_fields). */
+int lbm_set_porosity(lbm_handle *h, const float *phi, int on_device);
+
+/* (Re)initialise the state from the fields (u_r, u_z, T), each nr*nz, or pass three
+ * NULLs for the cold start.  The populations are f = M^-1(m_eq - S/2) (Eq. 19-20,
+ * 24, so that Eq. 29 returns the given u at rest), g = g_eq(T, u) (Eq. 35), after
+ * one collision; wall nodes take u = 0 and their wall temperature.  Resets the
+ * step count. */
+int lbm_init_fields(lbm_handle *h, const float *ur, const float *uz, const float *T, int on_device);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the handle's stream). */
+int lbm_step(lbm_handle *h, int64_t nsteps);
+
+/* Fields of the current state (what the next step's pull sees, after the wall
+ * rebuild) into caller-owned float arrays of nr*nz: rho (Eq. 26), u_r, u_z
+ * (Eq. 28; 0 on walls), T (Eq. 38; the wall temperature on walls).  Any pointer
+ * may be NULL.  Synchronises when on_device = 0. */
+int lbm_moments(lbm_handle *h, float *rho, float *ur, float *uz, float *T, int on_device);
+
+/* Average Nusselt numbers of Eq. 42 on the inner and outer wall of the current
+ * state: one-sided second-order dT/dr at the wall, trapezoid rule over the nz wall
+ * nodes, H = nz - 1, dT = T_hot - T_cold.  FP64 reduction.  Synchronises.  The
+ * inner value is NaN for the pipe. */
+int lbm_nusselt(lbm_handle *h, double *nu_inner, double *nu_outer);
+
+/* Convergence residual between the current state n and the previous state n - 1:
+ * max(|u^n - u^(n-1)|_2 / |u^n|_2, |T^n - T^(n-1)|_2 / |T^n|_2) over non-wall
+ * nodes, and the mass sum over all nodes of r * rho (= sum_i f_i), both in FP64.
+ * Needs at least one step since initialisation (LBM_ERR_INVALID otherwise).
+ * Returns LBM_ERR_DIVERGED if a field holds NaN or Inf.  Synchronises. */
+int lbm_residual(lbm_handle *h, double *res, double *mass);
+
+/* Step until the residual is <= tol, checking every check_every steps, or until
+ * max_steps.  *steps_done and *res (either may be NULL) receive the steps taken
+ * and the last residual.  LBM_ERR_DIVERGED on NaN/Inf. */
+int lbm_run(lbm_handle *h, int64_t max_steps, int64_t check_every, double tol, int64_t *steps_done,
+            double *res);
+
+/* Node classes (LBM_FLUID ... LBM_AXIS) into out[nr*nz] (host memory). */
+int lbm_node_class(lbm_handle *h, uint8_t *out);
+
+/* Export the current state's post-collision populations of rows
+ * [row0, row0 + nrows) in FP64, undoing the storage encoding: f[i][row][kz]
+ * (9 planes of nrows*nz) and g[i][row][kz] (5 planes), host memory, r-weighted
+ * as in Eq. 17.  For checks against an FP64 reference and for inspection.
+ * Synchronises. */
+int lbm_export_populations(lbm_handle *h, int32_t row0, int32_t nrows, double *f, double *g);
+
+/* Derived constants and step count of h. */
+int lbm_get_info(lbm_handle *h, lbm_info *out);
+
+/* Per-launch timing of the step kernels with CUDA events on the handle's stream.
+ * enable = 1 starts recording (and clears the totals), 0 stops.  lbm_kernel_times
+ * synchronises and returns the summed milliseconds and launch counts of the bulk
+ * step kernel and of the wall-node kernel since timing was enabled. */
+int lbm_set_timing(lbm_handle *h, int enable);
+int lbm_kernel_times(lbm_handle *h, double *bulk_ms, int64_t *bulk_launches, double *wall_ms,
+                     int64_t *wall_launches);
+
+/* Free everything h owns.  h may be NULL. */
+int lbm_destroy(lbm_handle *h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -674,6 +674,25 @@ int orc_collide_node(const orc_params *p, const double *s_override, int cartesia
     return 0;
 }
 
+/* Full update of one node (kr, kz) of a state: post-streaming populations and
+ * fields (node_state) and the collision, without touching any other node.  Only
+ * rows kr - 2 .. kr + 2 of f, g and phi are read. */
+int orc_node_update(const orc_params *p, const double *phi, const double *f, const double *g, int kr, int kz,
+                    double *fo, double *go, double *macro_out)
+{
+    orc_consts c;
+    if (orc_derive(p, &c)) return 1;
+    build_minv();
+    double ff[9], gg[5], rho, ur, uz, T;
+    node_state(p, &c, phi, f, g, kr, kz, ff, gg, &rho, &ur, &uz, &T);
+    orc_collide(p, &c, c.r0 + kr, phi[(size_t)kr * p->nz + kz], ff, gg, rho, ur, uz, T, fo, go);
+    macro_out[0] = rho;
+    macro_out[1] = ur;
+    macro_out[2] = uz;
+    macro_out[3] = T;
+    return 0;
+}
+
 int orc_derive_export(const orc_params *p, double *out)
 {
     orc_consts c;

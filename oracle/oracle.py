@@ -91,6 +91,7 @@ def lib():
             L.orc_splitmix64.restype = C.c_uint64
             L.orc_collide_node.argtypes = [pp, dp, C.c_int, C.c_double, C.c_double, dp, dp, C.c_int,
                                            C.c_double, dp, dp, dp]
+            L.orc_node_update.argtypes = [pp, dp, dp, dp, C.c_int, C.c_int, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -204,6 +205,19 @@ class State:
         b = C.c_double()
         lib().orc_nusselt(C.byref(self.p), _d(T), C.byref(a), C.byref(b))
         return a.value, b.value
+
+
+def node_update(p: Params, phi, f, g, kr: int, kz: int):
+    """Update of one node from a state given as full float64 arrays phi[nr, nz],
+    f[9, nr, nz], g[5, nr, nz]; only rows kr-2..kr+2 are read.
+    Returns (f+, g+, (rho, u_r, u_z, T))."""
+    for a in (phi, f, g):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    fo, go, mo = np.zeros(9), np.zeros(5), np.zeros(4)
+    rc = lib().orc_node_update(C.byref(p), _d(phi), _d(f), _d(g), int(kr), int(kz), _d(fo), _d(go), _d(mo))
+    if rc:
+        raise ValueError("invalid oracle parameters")
+    return fo, go, mo
 
 
 def residual(p: Params, cur, prev):

@@ -1,0 +1,964 @@
+// lbm.cu -- kernels and host runtime behind the C ABI of include/lbm.h.
+//
+// Axisymmetric D2Q9 MRT flow + D2Q5 temperature lattice Boltzmann step for porous
+// media (Liu, He & Li, arXiv 1409.5929, Sec. 3-4) on one GB300 (sm_103a).
+//
+// Data layout in HBM (per handle):
+//   state A, state B: 14 planes (f_0..f_8, g_0..g_4), each nr*nz elements, z fastest,
+//                     plane stride padded to 64 elements; element type = storage
+//                     type (FP32, FP16 or BF16), holding the deviations of
+//                     lbm_physics.cuh.  A step reads one buffer and writes the other.
+//   phi:              nr*nz porosity values (FP32, or FP16 with 16-bit storage).
+//   macro snapshots, reduction scratch, staging: only for diagnostics.
+//
+// A step is two launches on the handle's stream:
+//   k_bulk  every non-wall node: pull (Eq. 22, 33), recovery (Eq. 26-30, 38),
+//           collision (Eq. 21-24, 33-37), store.  Grid (nz / 128, nr).
+//   k_wall  every wall node: rebuild from the interior neighbour by
+//           non-equilibrium extrapolation (Sec. 4, ref. [47]), collision with
+//           u = 0 and the wall temperature, store.  One thread per wall node.
+// Both read only the source buffer and write disjoint nodes of the destination.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_physics.cuh"
+
+using namespace lbm;
+
+// ------------------------------------------------------------ storage types --
+template <int STO> struct St;
+template <> struct St<LBM_F32> {
+    using T = float;
+    using P = float;
+    __device__ static __forceinline__ float ld(const T* p) { return __ldg(p); }
+    __device__ static __forceinline__ void st(T* p, float v) { *p = v; }
+    __device__ static __forceinline__ float ldp(const P* p) { return __ldg(p); }
+    __host__ __device__ static __forceinline__ P mkp(float v) { return v; }
+};
+template <> struct St<LBM_F16> {
+    using T = __half;
+    using P = __half;
+    __device__ static __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v); }
+    __device__ static __forceinline__ float ldp(const P* p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ P mkp(float v) { return __float2half_rn(v); }
+};
+template <> struct St<LBM_BF16> {
+    using T = __nv_bfloat16;
+    using P = __half;
+    __device__ static __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
+    __device__ static __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ float ldp(const P* p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ P mkp(float v) { return __float2half_rn(v); }
+};
+
+static size_t elem_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
+static size_t phi_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
+
+constexpr int BULK_THREADS = 128;
+
+// ------------------------------------------------------------- pull (Eq. 22) --
+// Post-streaming deviations at (kr, kz) from the post-collision buffer A: f_i(x) =
+// f_i+(x - e_i), minus e_ir w_i for the change of r.  Periodic z wraps; in the pipe,
+// row 0 pulls its e_r = +1 populations from the mirror image of itself (the ghost
+// row below the axis), with e_r reversed and no change of r.
+template <int STO, typename R>
+__device__ __forceinline__ void pull(const Consts<R>& c, const typename St<STO>::T* __restrict__ A, int64_t plane,
+                                     int kr, int kz, R* fh, R* gh) {
+    using S = St<STO>;
+    const bool pz = c.geometry != ANNULUS;
+    const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;       // source column for e_z = +1
+    const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;       // source column for e_z = -1
+    const int64_t row = (int64_t)kr * c.nz;
+    const int64_t rowm = row - c.nz, rowp = row + c.nz;
+    const bool axis = (kr == 0);                              // reached only in the pipe
+    const R w1 = R(1) / R(9), w5 = R(1) / R(36);
+    // e_r = +1 populations: from row kr - 1, or on the axis row from the mirror image
+    const int64_t i1 = axis ? 3 * plane + row + kz : 1 * plane + rowm + kz;
+    const int64_t i5 = axis ? 6 * plane + row + zm : 5 * plane + rowm + zm;
+    const int64_t i8 = axis ? 7 * plane + row + zp : 8 * plane + rowm + zp;
+    const R c1 = axis ? R(0) : w1, c5 = axis ? R(0) : w5;
+    fh[0] = R(S::ld(A + row + kz));
+    fh[1] = R(S::ld(A + i1)) - c1;
+    fh[2] = R(S::ld(A + 2 * plane + row + zm));
+    fh[3] = R(S::ld(A + 3 * plane + rowp + kz)) + w1;
+    fh[4] = R(S::ld(A + 4 * plane + row + zp));
+    fh[5] = R(S::ld(A + i5)) - c5;
+    fh[6] = R(S::ld(A + 6 * plane + rowp + zm)) + w5;
+    fh[7] = R(S::ld(A + 7 * plane + rowp + zp)) + w5;
+    fh[8] = R(S::ld(A + i8)) - c5;
+    const typename S::T* G = A + 9 * plane;
+    gh[0] = R(S::ld(G + row + kz));
+    gh[1] = R(S::ld(G + (axis ? 3 * plane + row + kz : 1 * plane + rowm + kz)));
+    gh[2] = R(S::ld(G + 2 * plane + row + zm));
+    gh[3] = R(S::ld(G + 3 * plane + rowp + kz));
+    gh[4] = R(S::ld(G + 4 * plane + row + zp));
+}
+
+template <int STO, typename R>
+__device__ __forceinline__ void store(typename St<STO>::T* __restrict__ B, int64_t plane, int64_t n, const R* fh,
+                                      const R* gh) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) St<STO>::st(B + i * plane + n, float(fh[i]));
+#pragma unroll
+    for (int i = 0; i < 5; ++i) St<STO>::st(B + (9 + i) * plane + n, float(gh[i]));
+}
+
+// Wall node state: rebuild (Sec. 4, ref. [47]) from the interior neighbour, then
+// rho from Eq. 26 and the wall temperature (T_hot, T_cold, or T_f when adiabatic).
+template <int STO, typename R>
+__device__ __forceinline__ void wall_state(const Consts<R>& c, const typename St<STO>::T* __restrict__ A,
+                                           const typename St<STO>::P* __restrict__ phi, int64_t plane, int cls,
+                                           int kr, int kz, R* fh, R* gh, R& m0, R& rho, R& dTb) {
+    int fr, fz;
+    fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
+    R fhf[9], ghf[5];
+    pull<STO>(c, A, plane, fr, fz, fhf, ghf);
+    const R rf = c.r0 + R(fr), rb = c.r0 + R(kr);
+    const R phif = R(St<STO>::ldp(phi + (int64_t)fr * c.nz + fz));
+    R m0f, rhof, urf, uzf, dTf;
+    recover(c, rf, R(1) / rf, phif, fhf, ghf, m0f, rhof, urf, uzf, dTf);
+    rebuild_flow(rb, rf, phif, m0f, rhof, urf, uzf, fhf, fh);
+    dTb = cls == WALL_IN ? c.T_hot - c.T0 : cls == WALL_OUT ? c.T_cold - c.T0 : dTf;
+    rebuild_thermal(c.T0, dTf, dTb, urf, uzf, ghf, gh);
+    m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
+    rho = R(1) + m0 / rb;
+}
+
+// Wall node t -> (kr, kz): inner wall (annulus), outer wall, then bottom and top
+// without the corners (closed annulus).
+__device__ __forceinline__ void wall_node(int geometry, int nr, int nz, int t, int& kr, int& kz) {
+    if (geometry != PIPE_PERIODIC_Z) {
+        if (t < nz) { kr = 0; kz = t; return; }
+        t -= nz;
+    }
+    if (t < nz) { kr = nr - 1; kz = t; return; }
+    t -= nz;
+    if (t < nr - 2) { kr = 1 + t; kz = 0; return; }
+    t -= nr - 2;
+    kr = 1 + t;
+    kz = nz - 1;
+}
+
+static int wall_count(int geometry, int nr, int nz) {
+    if (geometry == ANNULUS) return 2 * nz + 2 * (nr - 2);
+    if (geometry == ANNULUS_PERIODIC_Z) return 2 * nz;
+    return nz;
+}
+
+// ------------------------------------------------------------------ kernels --
+template <int STO>
+__global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Consts<float> c, const typename St<STO>::T* __restrict__ A,
+                                                       typename St<STO>::T* __restrict__ B,
+                                                       const typename St<STO>::P* __restrict__ phi, int64_t plane) {
+    const int kz = blockIdx.x * BULK_THREADS + threadIdx.x;
+    const int kr = blockIdx.y;
+    if (kz >= c.nz) return;
+    if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) return;
+    float fh[9], gh[5];
+    pull<STO>(c, A, plane, kr, kz, fh, gh);
+    const int64_t n = (int64_t)kr * c.nz + kz;
+    const float r = c.r0 + float(kr), inv_r = 1.0f / r;
+    const float ph = St<STO>::ldp(phi + n);
+    float m0, rho, ur, uz, dT;
+    recover(c, r, inv_r, ph, fh, gh, m0, rho, ur, uz, dT);
+    collide(c, r, inv_r, ph, fh, gh, m0, rho, ur, uz, dT);
+    store<STO>(B, plane, n, fh, gh);
+}
+
+template <int STO>
+__global__ void k_wall(const Consts<float> c, const typename St<STO>::T* __restrict__ A,
+                       typename St<STO>::T* __restrict__ B, const typename St<STO>::P* __restrict__ phi,
+                       int64_t plane, int count) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    int kr, kz;
+    wall_node(c.geometry, c.nr, c.nz, t, kr, kz);
+    const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
+    float fh[9], gh[5], m0, rho, dTb;
+    wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dTb);
+    const int64_t n = (int64_t)kr * c.nz + kz;
+    const float r = c.r0 + float(kr);
+    collide(c, r, 1.0f / r, St<STO>::ldp(phi + n), fh, gh, m0, rho, 0.0f, 0.0f, dTb);
+    store<STO>(B, plane, n, fh, gh);
+}
+
+// Fields of a state at every node (NULL outputs skipped).
+template <int STO>
+__global__ void k_moments(const Consts<float> c, const typename St<STO>::T* __restrict__ A,
+                          const typename St<STO>::P* __restrict__ phi, int64_t plane, float* rho_o, float* ur_o,
+                          float* uz_o, float* T_o) {
+    const int kz = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kr = blockIdx.y;
+    if (kz >= c.nz) return;
+    const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
+    const int64_t n = (int64_t)kr * c.nz + kz;
+    float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT;
+    if (is_wall(cls)) {
+        wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dT);
+    } else {
+        pull<STO>(c, A, plane, kr, kz, fh, gh);
+        const float r = c.r0 + float(kr);
+        recover(c, r, 1.0f / r, St<STO>::ldp(phi + n), fh, gh, m0, rho, ur, uz, dT);
+    }
+    if (rho_o) rho_o[n] = rho;
+    if (ur_o) ur_o[n] = ur;
+    if (uz_o) uz_o[n] = uz;
+    if (T_o) T_o[n] = c.T0 + dT;
+}
+
+// Start state (FP64 arithmetic, one launch per initialisation): pre-collision
+// f = M^-1(m_eq - S/2) at rho = 1 (Eq. 19-20, 24), g = g_eq(T, u) (Eq. 35), then one
+// collision at the node.  Cold start: T = T0 + noise * U(-1, 1) from SplitMix64.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + (n + 1) * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double start_T(const Consts<double>& c, const float* T_in, double noise, uint64_t seed,
+                                          int64_t n) {
+    if (T_in) return (double)T_in[n];
+    const double u01 = (double)(splitmix64(seed, (uint64_t)n) >> 11) * (1.0 / 9007199254740992.0);
+    return c.T0 + noise * (2 * u01 - 1);
+}
+
+template <int STO>
+__global__ void k_init(const Consts<double> c, typename St<STO>::T* __restrict__ B,
+                       const typename St<STO>::P* __restrict__ phi, int64_t plane, const float* ur_in,
+                       const float* uz_in, const float* T_in, double noise, uint64_t seed) {
+    const int kz = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kr = blockIdx.y;
+    if (kz >= c.nz) return;
+    const int64_t n = (int64_t)kr * c.nz + kz;
+    const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
+    const double r = c.r0 + kr, inv_r = 1.0 / r;
+    double T = start_T(c, T_in, noise, seed, n), ur = 0, uz = 0;
+    if (cls == WALL_IN) T = c.T_hot;
+    else if (cls == WALL_OUT) T = c.T_cold;
+    else if (cls == BOTTOM || cls == TOP) {
+        int fr, fz;
+        fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
+        T = start_T(c, T_in, noise, seed, (int64_t)fr * c.nz + fz);
+    } else if (ur_in && uz_in) {
+        ur = ur_in[n];
+        uz = uz_in[n];
+    }
+    const double ph = (double)St<STO>::ldp(phi + n);
+    double lin, nl;
+    porous(c, ph, lin, nl);
+    const double um = sqrt(ur * ur + uz * uz);
+    const double Ftr = -ph * (lin + nl * um) * ur + cs2<double>() * (1 - c.two_taum * ur * inv_r) * inv_r;
+    const double Ftz = -ph * (lin + nl * um) * uz + ph * (c.gbeta * (T - c.T0) + c.az);
+    const double iphi = 1.0 / ph, u2 = ur * ur + uz * uz;
+    // m_eq(rho = 1) - r(1, -2, 1, 0, ...) - S / 2
+    const double S1 = 6 * r * (ur * Ftr + uz * Ftz) * iphi, S3 = r * Ftr, S5 = r * Ftz;
+    const double S7 = 2 * r * (ur * Ftr - uz * Ftz) * iphi, S8 = r * (ur * Ftz + uz * Ftr) * iphi;
+    const double q = 3 * r * u2 * iphi;
+    const double mpre[9] = {0.0,
+                            q - 0.5 * S1,
+                            -q + 0.5 * S1,
+                            r * ur - 0.5 * S3,
+                            -r * ur + 0.5 * S3,
+                            r * uz - 0.5 * S5,
+                            -r * uz + 0.5 * S5,
+                            r * (ur * ur - uz * uz) * iphi - 0.5 * S7,
+                            r * ur * uz * iphi - 0.5 * S8};
+    double fh[9], gh[5];
+    minv(mpre, fh);
+    const double dTs = T - c.T0;
+    gh[0] = 0.6 * dTs;
+    gh[1] = 0.1 * dTs + 0.5 * T * ur;
+    gh[2] = 0.1 * dTs + 0.5 * T * uz;
+    gh[3] = 0.1 * dTs - 0.5 * T * ur;
+    gh[4] = 0.1 * dTs - 0.5 * T * uz;
+    double m0, rho, u_r = 0, u_z = 0, dT;
+    if (is_wall(cls)) {
+        m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
+        rho = 1 + m0 * inv_r;
+        dT = dTs;
+    } else {
+        recover(c, r, inv_r, ph, fh, gh, m0, rho, u_r, u_z, dT);
+    }
+    collide(c, r, inv_r, ph, fh, gh, m0, rho, u_r, u_z, dT);
+    store<STO>(B, plane, n, fh, gh);
+}
+
+// Porosity upload: validate (0 < phi <= 1) and convert to the storage type.
+template <int STO>
+__global__ void k_phi(const float* __restrict__ src, typename St<STO>::P* __restrict__ dst, int64_t n,
+                      unsigned int* bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = src[i];
+    if (!(v > 0.f && v <= 1.f)) atomicAdd(bad, 1u);
+    dst[i] = St<STO>::mkp(v);
+}
+
+template <int STO>
+__global__ void k_phi_fill(typename St<STO>::P* __restrict__ dst, int64_t n, float v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = St<STO>::mkp(v);
+}
+
+__global__ void k_node_class(int geometry, int nr, int nz, uint8_t* out) {
+    const int kz = blockIdx.x * blockDim.x + threadIdx.x;
+    const int kr = blockIdx.y;
+    if (kz < nz) out[(int64_t)kr * nz + kz] = (uint8_t)node_class(geometry, nr, nz, kr, kz);
+}
+
+// ----------------------------------------------------- FP64 reductions --
+// Block sum of NV doubles per thread (warp shuffles, then shared memory).
+template <int NV>
+__device__ __forceinline__ void block_sum(double* v, double* out_if_thread0) {
+    __shared__ double sh[32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], o);
+    if (lane == 0)
+        for (int j = 0; j < NV; ++j) sh[warp][j] = v[j];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double x = lane < nw ? sh[lane][j] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) out_if_thread0[j] = x;
+        }
+    }
+}
+
+// Residual partials over nodes: |du|^2, |u|^2, dT^2, T^2 on non-wall nodes, mass
+// r * rho on all nodes, and a count of non-finite values; one row of 6 per block.
+constexpr int RES_NV = 6;
+__global__ void k_resid_partial(int geometry, int nr, int nz, double r0, const float* __restrict__ cur,
+                                const float* __restrict__ prev, int64_t fstride, double* __restrict__ partials) {
+    double v[RES_NV] = {0, 0, 0, 0, 0, 0};
+    const int64_t N = (int64_t)nr * nz;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const int kr = (int)(n / nz), kz = (int)(n - (int64_t)kr * nz);
+        const float rho = cur[n], ur = cur[fstride + n], uz = cur[2 * fstride + n], T = cur[3 * fstride + n];
+        if (!isfinite(rho) || !isfinite(ur) || !isfinite(uz) || !isfinite(T)) v[5] += 1;
+        v[4] += (r0 + kr) * (double)rho;
+        if (is_wall(node_class(geometry, nr, nz, kr, kz))) continue;
+        const double a = (double)ur - prev[fstride + n], b = (double)uz - prev[2 * fstride + n];
+        const double d = (double)T - prev[3 * fstride + n];
+        v[0] += a * a + b * b;
+        v[1] += (double)ur * ur + (double)uz * uz;
+        v[2] += d * d;
+        v[3] += (double)T * T;
+    }
+    double out[RES_NV];
+    block_sum<RES_NV>(v, out);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < RES_NV; ++j) partials[blockIdx.x * RES_NV + j] = out[j];
+}
+
+__global__ void k_sum_rows(const double* __restrict__ partials, int rows, double* __restrict__ result) {
+    double v[RES_NV] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < rows; b += blockDim.x)
+        for (int j = 0; j < RES_NV; ++j) v[j] += partials[b * RES_NV + j];
+    double out[RES_NV];
+    block_sum<RES_NV>(v, out);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < RES_NV; ++j) result[j] = out[j];
+}
+
+// Temperature of node (kr, kz) of a state: wall temperature, the interior
+// neighbour's T on adiabatic walls, else sum of the pulled g (Eq. 38), in FP64.
+template <int STO>
+__device__ double node_T(const Consts<float>& c, const typename St<STO>::T* __restrict__ A, int64_t plane, int kr,
+                         int kz) {
+    const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
+    if (cls == WALL_IN) return (double)c.T_hot;
+    if (cls == WALL_OUT) return (double)c.T_cold;
+    if (cls == BOTTOM || cls == TOP) {
+        int fr, fz;
+        fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
+        kr = fr;
+        kz = fz;
+    }
+    float fh[9], gh[5];
+    pull<STO>(c, A, plane, kr, kz, fh, gh);
+    return (double)c.T0 + (((double)gh[0] + gh[1]) + ((double)gh[2] + gh[3]) + gh[4]);
+}
+
+// Eq. 42 for both walls in one block: one-sided second-order dT/dr, trapezoid in z.
+template <int STO>
+__global__ void k_nusselt(const Consts<float> c, const typename St<STO>::T* __restrict__ A, int64_t plane,
+                          double ri, double ro, double H, double dTw, double* __restrict__ result) {
+    double v[2] = {0, 0};
+    for (int kz = threadIdx.x; kz < c.nz; kz += blockDim.x) {
+        const double wz = (kz == 0 || kz == c.nz - 1) ? 0.5 : 1.0;
+        const double t0 = node_T<STO>(c, A, plane, 0, kz), t1 = node_T<STO>(c, A, plane, 1, kz);
+        const double t2 = node_T<STO>(c, A, plane, 2, kz);
+        const double u0 = node_T<STO>(c, A, plane, c.nr - 1, kz), u1 = node_T<STO>(c, A, plane, c.nr - 2, kz);
+        const double u2 = node_T<STO>(c, A, plane, c.nr - 3, kz);
+        v[0] += wz * (-3 * t0 + 4 * t1 - t2) * 0.5;
+        v[1] += wz * (3 * u0 - 4 * u1 + u2) * 0.5;
+    }
+    double out[2];
+    block_sum<2>(v, out);
+    if (threadIdx.x == 0) {
+        result[0] = -ri * out[0] / (H * dTw);
+        result[1] = -ro * out[1] / (H * dTw);
+    }
+}
+
+// FP64 export of rows [row0, row0 + nrows): raw post-collision populations
+// f_i = fh_i + r w_i, g_i = gh_i + wT_i T0.
+template <int STO>
+__global__ void k_export(const Consts<float> c, const typename St<STO>::T* __restrict__ A, int64_t plane, int row0,
+                         int nrows, double r0, double T0, double* __restrict__ out) {
+    const int kz = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (kz >= c.nz || j >= nrows) return;
+    const int kr = row0 + j;
+    const int64_t n = (int64_t)kr * c.nz + kz, m = (int64_t)j * c.nz + kz, P = (int64_t)nrows * c.nz;
+    const double r = r0 + kr;
+    for (int i = 0; i < 9; ++i) out[i * P + m] = (double)St<STO>::ld(A + i * plane + n) + r * w9<double>(i);
+    const double wt[5] = {0.6, 0.1, 0.1, 0.1, 0.1};
+    for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)St<STO>::ld(A + (9 + i) * plane + n) + wt[i] * T0;
+}
+
+// ------------------------------------------------------------ host runtime --
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            (void)cudaGetLastError();                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+        }                                                                                          \
+    } while (0)
+
+struct lbm_handle {
+    lbm_params p;
+    lbm_info info;
+    Consts<float> cf;
+    Consts<double> cd;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t plane = 0;       // elements per plane (padded)
+    int64_t N = 0;           // nr * nz
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;             // buffer holding the current state
+    void* phi = nullptr;
+    float* fstage = nullptr; // N floats: porosity / init field upload
+    float* mac = nullptr;    // two snapshots of 4 planes: rho, ur, uz, T
+    int64_t mstride = 0;
+    double* partials = nullptr;
+    int pblocks = 0;
+    double* result = nullptr;   // 8 doubles
+    unsigned int* bad = nullptr;
+    uint8_t* cls = nullptr;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;   // (start, after bulk, after wall) per timed step
+};
+
+static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
+    memset(o, 0, sizeof(*o));
+    if (!p) return fail(LBM_ERR_INVALID, "params is NULL");
+    if (p->nr < 3 || p->nz < 3) return fail(LBM_ERR_INVALID, "grid %d x %d: need nr, nz >= 3", p->nr, p->nz);
+    if (p->nr > 65535) return fail(LBM_ERR_INVALID, "nr = %d exceeds 65535", p->nr);
+    if (p->geometry < 0 || p->geometry > 2) return fail(LBM_ERR_INVALID, "unknown geometry %d", p->geometry);
+    if (p->storage < 0 || p->storage > 2) return fail(LBM_ERR_INVALID, "unknown storage %d", p->storage);
+    if (!(p->J > 0) || !(p->lambda > 0) || !(p->Pr > 0))
+        return fail(LBM_ERR_INVALID, "J, lambda and Pr must be positive");
+    if (!(p->eps_mean > 0 && p->eps_mean <= 1)) return fail(LBM_ERR_INVALID, "eps_mean %g outside (0, 1]", p->eps_mean);
+    const double cs = std::sqrt(1.0 / 3.0);
+    if (p->geometry == PIPE_PERIODIC_Z) {
+        o->r0 = 0.5;
+        o->L = (p->nr - 1) + 0.5;
+    } else {
+        if (!(p->radius_ratio > 1)) return fail(LBM_ERR_INVALID, "radius_ratio %g must exceed 1", p->radius_ratio);
+        o->L = p->nr - 1;
+        o->r0 = o->L / (p->radius_ratio - 1);
+    }
+    o->H = p->nz - 1;
+    const double dTw = p->T_hot - p->T_cold;
+    if (p->tau_nu > 0) {
+        o->tau_nu = p->tau_nu;
+        o->Ma = p->Ra > 0 ? (o->tau_nu - 0.5) * cs * std::sqrt(p->Ra) / (p->J * o->L * std::sqrt(p->Pr)) : 0.0;
+    } else {
+        if (!(p->Ra > 0)) return fail(LBM_ERR_INVALID, "Ra must be positive when tau_nu is not given");
+        o->Ma = p->Ma;
+        o->tau_nu = 0.5 + p->Ma * p->J * o->L * std::sqrt(p->Pr) / (cs * std::sqrt(p->Ra));   // Eq. 39
+    }
+    if (!(o->tau_nu > 0.5)) return fail(LBM_ERR_INVALID, "tau_nu = %g must exceed 1/2", o->tau_nu);
+    o->tau_T = (1.0 / 3.0) * p->lambda * (o->tau_nu - 0.5) / (0.2 * p->J * p->Pr);            // Eq. 39
+    o->nu_e = (o->tau_nu - 0.5) / 3.0;                                                           // Eq. 31
+    o->nu = o->nu_e / p->J;
+    if (p->Ra > 0) {
+        if (dTw == 0) return fail(LBM_ERR_INVALID, "T_hot == T_cold with Ra > 0");
+        const double U = o->Ma * cs;                                                             // Ma = U / c_s
+        o->gbeta = U * U / (dTw * o->L);                                                         // U^2 = g beta dT L
+    }
+    o->T0 = 0.5 * (p->T_hot + p->T_cold);
+    o->Kbar = p->Da * o->L * o->L;
+    const int64_t N = (int64_t)p->nr * p->nz;
+    o->bytes_per_step = N * (28 * (int64_t)elem_size(p->storage) + (int64_t)phi_size(p->storage));
+    if (cd) {
+        Consts<double>& c = *cd;
+        memset(&c, 0, sizeof(c));
+        c.nr = p->nr;
+        c.nz = p->nz;
+        c.geometry = p->geometry;
+        c.porous_mode = !(p->Da > 0) ? 0 : (p->eps_mean >= 1 ? 1 : 2);
+        c.ergun = p->F_eps < 0;
+        c.r0 = o->r0;
+        c.cs2tau = (o->tau_nu - 0.5) / 3.0;
+        c.two_taum = 2 * (o->tau_nu - 0.5);
+        c.s_e = 1.1;
+        c.s_eps = 1.1;
+        c.s_j = 1.0;
+        c.s_q = 1.2;
+        c.s_nu = 1.0 / o->tau_nu;
+        c.tauT = o->tau_T;
+        c.wg_den = 1.0 / (o->tau_T + 0.5);
+        c.gbeta = o->gbeta;
+        c.T0 = o->T0;
+        c.az = p->body_accel_z;
+        c.nu = o->nu;
+        c.invKbar = p->Da > 0 ? 1.0 / o->Kbar : 0.0;
+        const double em = p->eps_mean;
+        c.c_kappa = (p->Da > 0 && em < 1) ? em * em * em / ((1 - em) * (1 - em) * o->Kbar) : 0.0;
+        c.F_eps = p->F_eps > 0 ? p->F_eps : 0.0;
+        c.T_hot = p->T_hot;
+        c.T_cold = p->T_cold;
+    }
+    return LBM_OK;
+}
+
+static Consts<float> to_float(const Consts<double>& d) {
+    Consts<float> f;
+    f.nr = d.nr; f.nz = d.nz; f.geometry = d.geometry; f.porous_mode = d.porous_mode; f.ergun = d.ergun; f.pad = 0;
+    f.r0 = (float)d.r0; f.cs2tau = (float)d.cs2tau; f.two_taum = (float)d.two_taum;
+    f.s_e = (float)d.s_e; f.s_eps = (float)d.s_eps; f.s_j = (float)d.s_j; f.s_q = (float)d.s_q; f.s_nu = (float)d.s_nu;
+    f.tauT = (float)d.tauT; f.wg_den = (float)d.wg_den; f.gbeta = (float)d.gbeta; f.T0 = (float)d.T0;
+    f.az = (float)d.az; f.nu = (float)d.nu; f.invKbar = (float)d.invKbar; f.c_kappa = (float)d.c_kappa;
+    f.F_eps = (float)d.F_eps; f.T_hot = (float)d.T_hot; f.T_cold = (float)d.T_cold;
+    return f;
+}
+
+static dim3 grid2d(const lbm_handle* h, int threads) {
+    return dim3((unsigned)((h->p.nz + threads - 1) / threads), (unsigned)h->p.nr);
+}
+
+// Dispatch a templated launch on the storage type.
+#define DISPATCH_STO(sto, ...)                      \
+    switch (sto) {                                  \
+        case LBM_F32: { constexpr int S_ = LBM_F32; __VA_ARGS__; } break;  \
+        case LBM_F16: { constexpr int S_ = LBM_F16; __VA_ARGS__; } break;  \
+        default: { constexpr int S_ = LBM_BF16; __VA_ARGS__; } break;      \
+    }
+
+template <int STO> using TT = typename St<STO>::T;
+template <int STO> using PP = typename St<STO>::P;
+
+extern "C" {
+
+void lbm_params_default(lbm_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->nr = 48;
+    p->nz = 96;
+    p->geometry = LBM_ANNULUS;
+    p->storage = LBM_F32;
+    p->radius_ratio = 2.0;
+    p->Ra = 1e3;
+    p->Da = 1e-2;
+    p->Pr = 1.0;
+    p->J = 1.0;
+    p->lambda = 1.0;
+    p->Ma = 0.1;
+    p->tau_nu = 0.0;
+    p->F_eps = -1.0;
+    p->eps_mean = 0.6;
+    p->T_hot = 1.0;
+    p->T_cold = 0.0;
+    p->body_accel_z = 0.0;
+    p->init_noise = 1e-3;
+    p->seed = 1;
+}
+
+int lbm_derive(const lbm_params* p, lbm_info* out) {
+    if (!out) return fail(LBM_ERR_INVALID, "out is NULL");
+    return derive(p, out, nullptr);
+}
+
+int lbm_destroy(lbm_handle* h) {
+    if (!h) return LBM_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* b : h->buf) cudaFree(b);
+    cudaFree(h->phi);
+    cudaFree(h->fstage);
+    cudaFree(h->mac);
+    cudaFree(h->partials);
+    cudaFree(h->result);
+    cudaFree(h->bad);
+    cudaFree(h->cls);
+    for (auto e : h->ev) cudaEventDestroy(e);
+    delete h;
+    return LBM_OK;
+}
+
+static int launch_init(lbm_handle* h, const float* ur, const float* uz, const float* T) {
+    void* dst = h->buf[0];
+    dim3 g = grid2d(h, 128);
+    DISPATCH_STO(h->p.storage,
+                 k_init<S_><<<g, 128, 0, h->stream>>>(h->cd, (TT<S_>*)dst, (const PP<S_>*)h->phi, h->plane, ur, uz,
+                                                      T, h->p.init_noise, h->p.seed));
+    CK(cudaGetLastError());
+    h->cur = 0;
+    h->info.steps = 0;
+    return LBM_OK;
+}
+
+int lbm_create(const lbm_params* p, lbm_handle** out) {
+    if (!out) return fail(LBM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    lbm_handle* h = new lbm_handle();
+    int rc = derive(p, &h->info, &h->cd);
+    if (rc) { delete h; return rc; }
+    h->p = *p;
+    h->cf = to_float(h->cd);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { delete h; return fail(LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    h->N = (int64_t)p->nr * p->nz;
+    h->plane = (h->N + 63) / 64 * 64;
+    h->mstride = h->plane;
+    const size_t es = elem_size(p->storage);
+    h->pblocks = 1024;
+#define ALLOC(ptr, bytes)                                                       \
+    do {                                                                        \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                   \
+        if (e_ != cudaSuccess) {                                                \
+            (void)cudaGetLastError();                                           \
+            lbm_destroy(h);                                                     \
+            return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, \
+                        "cudaMalloc(%zu bytes): %s", (size_t)(bytes), cudaGetErrorString(e_)); \
+        }                                                                       \
+    } while (0)
+    ALLOC(h->buf[0], 14 * h->plane * es);
+    ALLOC(h->buf[1], 14 * h->plane * es);
+    ALLOC(h->phi, h->plane * phi_size(p->storage));
+    ALLOC(h->partials, (size_t)h->pblocks * RES_NV * sizeof(double));
+    ALLOC(h->result, 8 * sizeof(double));
+    ALLOC(h->bad, sizeof(unsigned int));
+#undef ALLOC
+    // uniform porosity eps_mean, then the cold start
+    const int thr = 256;
+    const unsigned blocks = (unsigned)((h->N + thr - 1) / thr);
+    DISPATCH_STO(p->storage, k_phi_fill<S_><<<blocks, thr, 0, h->stream>>>((PP<S_>*)h->phi, h->N, (float)p->eps_mean));
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        rc = launch_init(h, nullptr, nullptr, nullptr);
+        if (rc) { lbm_destroy(h); return rc; }
+        e = cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess) {
+        lbm_destroy(h);
+        return fail(LBM_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_handle* h, void* stream) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    h->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+static int ensure_fstage(lbm_handle* h) {
+    if (!h->fstage) CK(cudaMalloc((void**)&h->fstage, 3 * h->plane * sizeof(float)));
+    return LBM_OK;
+}
+
+int lbm_set_porosity(lbm_handle* h, const float* phi, int on_device) {
+    if (!h || !phi) return fail(LBM_ERR_INVALID, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    const float* src = phi;
+    if (!on_device) {
+        int rc = ensure_fstage(h);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(h->fstage, phi, h->N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        src = h->fstage;
+    }
+    CK(cudaMemsetAsync(h->bad, 0, sizeof(unsigned int), h->stream));
+    const int thr = 256;
+    const unsigned blocks = (unsigned)((h->N + thr - 1) / thr);
+    DISPATCH_STO(h->p.storage, k_phi<S_><<<blocks, thr, 0, h->stream>>>(src, (PP<S_>*)h->phi, h->N, h->bad));
+    CK(cudaGetLastError());
+    unsigned int bad = 0;
+    CK(cudaMemcpyAsync(&bad, h->bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (bad) return fail(LBM_ERR_INVALID, "%u porosity values outside (0, 1]", bad);
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_handle* h, const float* ur, const float* uz, const float* T, int on_device) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    if ((ur == nullptr) != (uz == nullptr)) return fail(LBM_ERR_INVALID, "give both u_r and u_z or neither");
+    CK(cudaSetDevice(h->device));
+    const float *dur = ur, *duz = uz, *dT = T;
+    if (!on_device && (ur || T)) {
+        int rc = ensure_fstage(h);
+        if (rc) return rc;
+        if (ur) {
+            CK(cudaMemcpyAsync(h->fstage, ur, h->N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(h->fstage + h->plane, uz, h->N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+            dur = h->fstage;
+            duz = h->fstage + h->plane;
+        }
+        if (T) {
+            CK(cudaMemcpyAsync(h->fstage + 2 * h->plane, T, h->N * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+            dT = h->fstage + 2 * h->plane;
+        }
+    }
+    int rc = launch_init(h, dur, duz, dT);
+    if (rc) return rc;
+    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+static int launch_step(lbm_handle* h) {
+    const void* A = h->buf[h->cur];
+    void* B = h->buf[h->cur ^ 1];
+    const dim3 g = grid2d(h, BULK_THREADS);
+    const int nw = wall_count(h->p.geometry, h->p.nr, h->p.nz);
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (h->timing) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventCreate(&e2));
+        CK(cudaEventRecord(e0, h->stream));
+    }
+    DISPATCH_STO(h->p.storage,
+                 k_bulk<S_><<<g, BULK_THREADS, 0, h->stream>>>(h->cf, (const TT<S_>*)A, (TT<S_>*)B,
+                                                                (const PP<S_>*)h->phi, h->plane));
+    CK(cudaGetLastError());
+    if (h->timing) CK(cudaEventRecord(e1, h->stream));
+    DISPATCH_STO(h->p.storage,
+                 k_wall<S_><<<(nw + 127) / 128, 128, 0, h->stream>>>(h->cf, (const TT<S_>*)A, (TT<S_>*)B,
+                                                                     (const PP<S_>*)h->phi, h->plane, nw));
+    CK(cudaGetLastError());
+    if (h->timing) {
+        CK(cudaEventRecord(e2, h->stream));
+        h->ev.push_back(e0);
+        h->ev.push_back(e1);
+        h->ev.push_back(e2);
+    }
+    h->cur ^= 1;
+    h->info.steps += 1;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    if (nsteps < 0) return fail(LBM_ERR_INVALID, "nsteps < 0");
+    CK(cudaSetDevice(h->device));
+    for (int64_t s = 0; s < nsteps; ++s) {
+        int rc = launch_step(h);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+static int launch_moments(lbm_handle* h, int which, float* rho, float* ur, float* uz, float* T) {
+    const dim3 g = grid2d(h, 128);
+    DISPATCH_STO(h->p.storage,
+                 k_moments<S_><<<g, 128, 0, h->stream>>>(h->cf, (const TT<S_>*)h->buf[which], (const PP<S_>*)h->phi,
+                                                         h->plane, rho, ur, uz, T));
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+static int ensure_mac(lbm_handle* h) {
+    if (!h->mac) CK(cudaMalloc((void**)&h->mac, 8 * h->mstride * sizeof(float)));
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_handle* h, float* rho, float* ur, float* uz, float* T, int on_device) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    if (on_device) return launch_moments(h, h->cur, rho, ur, uz, T);
+    int rc = ensure_mac(h);
+    if (rc) return rc;
+    float* m = h->mac;
+    rc = launch_moments(h, h->cur, m, m + h->mstride, m + 2 * h->mstride, m + 3 * h->mstride);
+    if (rc) return rc;
+    float* outs[4] = {rho, ur, uz, T};
+    for (int j = 0; j < 4; ++j)
+        if (outs[j])
+            CK(cudaMemcpyAsync(outs[j], m + j * h->mstride, h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_nusselt(lbm_handle* h, double* nu_inner, double* nu_outer) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    const double dTw = h->p.T_hot - h->p.T_cold;
+    const double ri = h->info.r0, ro = h->info.r0 + (h->p.nr - 1);
+    DISPATCH_STO(h->p.storage,
+                 k_nusselt<S_><<<1, 1024, 0, h->stream>>>(h->cf, (const TT<S_>*)h->buf[h->cur], h->plane, ri, ro,
+                                                          h->info.H, dTw, h->result));
+    CK(cudaGetLastError());
+    double r[2];
+    CK(cudaMemcpyAsync(r, h->result, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (nu_inner) *nu_inner = h->p.geometry == LBM_PIPE_PERIODIC_Z ? NAN : r[0];
+    if (nu_outer) *nu_outer = r[1];
+    return LBM_OK;
+}
+
+int lbm_residual(lbm_handle* h, double* res, double* mass) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    if (h->info.steps < 1) return fail(LBM_ERR_INVALID, "residual needs at least one step since initialisation");
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_mac(h);
+    if (rc) return rc;
+    float* cur = h->mac;
+    float* prev = h->mac + 4 * h->mstride;
+    rc = launch_moments(h, h->cur, cur, cur + h->mstride, cur + 2 * h->mstride, cur + 3 * h->mstride);
+    if (rc) return rc;
+    rc = launch_moments(h, h->cur ^ 1, prev, prev + h->mstride, prev + 2 * h->mstride, prev + 3 * h->mstride);
+    if (rc) return rc;
+    const int blocks = (int)std::min<int64_t>(h->pblocks, (h->N + 255) / 256);
+    k_resid_partial<<<blocks, 256, 0, h->stream>>>(h->p.geometry, h->p.nr, h->p.nz, h->info.r0, cur, prev,
+                                                   h->mstride, h->partials);
+    CK(cudaGetLastError());
+    k_sum_rows<<<1, 256, 0, h->stream>>>(h->partials, blocks, h->result);
+    CK(cudaGetLastError());
+    double s[RES_NV];
+    CK(cudaMemcpyAsync(s, h->result, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (s[5] > 0) return fail(LBM_ERR_DIVERGED, "%.0f nodes hold NaN or Inf", s[5]);
+    const double ru = s[1] > 0 ? std::sqrt(s[0] / s[1]) : (s[0] > 0 ? INFINITY : 0.0);
+    const double rt = s[3] > 0 ? std::sqrt(s[2] / s[3]) : (s[2] > 0 ? INFINITY : 0.0);
+    if (res) *res = ru > rt ? ru : rt;
+    if (mass) *mass = s[4];
+    return LBM_OK;
+}
+
+int lbm_run(lbm_handle* h, int64_t max_steps, int64_t check_every, double tol, int64_t* steps_done, double* res) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    if (max_steps < 0 || check_every < 1) return fail(LBM_ERR_INVALID, "max_steps >= 0 and check_every >= 1 required");
+    int64_t done = 0;
+    double r = INFINITY;
+    while (done < max_steps) {
+        const int64_t k = std::min(check_every, max_steps - done);
+        int rc = lbm_step(h, k);
+        if (rc) return rc;
+        done += k;
+        double m;
+        rc = lbm_residual(h, &r, &m);
+        if (rc) {
+            if (steps_done) *steps_done = done;
+            if (res) *res = r;
+            return rc;
+        }
+        if (r <= tol) break;
+    }
+    if (steps_done) *steps_done = done;
+    if (res) *res = r;
+    return LBM_OK;
+}
+
+int lbm_node_class(lbm_handle* h, uint8_t* out) {
+    if (!h || !out) return fail(LBM_ERR_INVALID, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    if (!h->cls) CK(cudaMalloc((void**)&h->cls, h->N));
+    k_node_class<<<grid2d(h, 128), 128, 0, h->stream>>>(h->p.geometry, h->p.nr, h->p.nz, h->cls);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, h->cls, h->N, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_export_populations(lbm_handle* h, int32_t row0, int32_t nrows, double* f, double* g) {
+    if (!h || !f || !g) return fail(LBM_ERR_INVALID, "NULL argument");
+    if (row0 < 0 || nrows < 1 || row0 + nrows > h->p.nr) return fail(LBM_ERR_INVALID, "row range outside the grid");
+    CK(cudaSetDevice(h->device));
+    const int64_t P = (int64_t)nrows * h->p.nz;
+    double* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, 14 * P * sizeof(double), h->stream));
+    dim3 grid((unsigned)((h->p.nz + 127) / 128), (unsigned)nrows);
+    DISPATCH_STO(h->p.storage, k_export<S_><<<grid, 128, 0, h->stream>>>(h->cf, (const TT<S_>*)h->buf[h->cur], h->plane,
+                                                                          row0, nrows, h->info.r0, h->info.T0, d));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, 9 * P * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g, d + 9 * P, 5 * P * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "export: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_get_info(lbm_handle* h, lbm_info* out) {
+    if (!h || !out) return fail(LBM_ERR_INVALID, "NULL argument");
+    *out = h->info;
+    return LBM_OK;
+}
+
+int lbm_set_timing(lbm_handle* h, int enable) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    for (auto e : h->ev) cudaEventDestroy(e);
+    h->ev.clear();
+    h->timing = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_kernel_times(lbm_handle* h, double* bulk_ms, int64_t* bulk_launches, double* wall_ms,
+                     int64_t* wall_launches) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    double tb = 0, tw = 0;
+    for (size_t i = 0; i + 2 < h->ev.size(); i += 3) {
+        float a = 0, b = 0;
+        CK(cudaEventElapsedTime(&a, h->ev[i], h->ev[i + 1]));
+        CK(cudaEventElapsedTime(&b, h->ev[i + 1], h->ev[i + 2]));
+        tb += a;
+        tw += b;
+    }
+    const int64_t n = (int64_t)(h->ev.size() / 3);
+    if (bulk_ms) *bulk_ms = tb;
+    if (bulk_launches) *bulk_launches = n;
+    if (wall_ms) *wall_ms = tw;
+    if (wall_launches) *wall_launches = n;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+// lbm_physics.cuh -- per-node arithmetic of the axisymmetric MRT-LB step
+// (Liu, He & Li, arXiv 1409.5929, Sec. 3.1-3.2 and Sec. 4), device side.
+//
+// Variables.  The populations of Eq. 17 carry a factor r.  Between steps they are
+// stored as deviations from the rest state (rho0 = 1, T0):
+//     fh_i = f_i - r w_i          (w_i of Eq. 32)
+//     gh_i = g_i - wT_i T0        (wT_i of Eq. 36)
+// so that every quantity handled is small and FP32 (or FP16/BF16 storage) keeps
+// its relative precision.  Pulling a population across a row changes r by -e_ir,
+// so the pulled deviation is the stored one minus e_ir w_i (Eq. 22).  The moments
+// are taken of the deviations, mh = M fh = m - r (1, -2, 1, 0, ..., 0) (Eq. 16, 18),
+// and the collision of Eq. 21 is applied to mh: m - m_eq = mh - mh_eq because the
+// rest part cancels.  M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum { ANNULUS = 0, ANNULUS_PERIODIC_Z = 1, PIPE_PERIODIC_Z = 2 };
+enum { FLUID = 0, WALL_IN = 1, WALL_OUT = 2, BOTTOM = 3, TOP = 4, AXIS = 5 };
+
+// Lattice constants, in the arithmetic type R of the kernel that uses them.
+template <typename R>
+struct Consts {
+    int nr, nz, geometry;
+    int porous_mode;   // 0: no drag; 1: K = Da L^2 everywhere; 2: K(phi) from Eq. 8
+    int ergun;         // 1: F_phi from Eq. 8 per node; 0: constant F_eps
+    int pad;
+    R r0;              // r(kr = 0)
+    R cs2tau;          // c_s^2 (tau - 1/2)
+    R two_taum;        // 2 (tau - 1/2)
+    R s_e, s_eps, s_j, s_q, s_nu;   // Eq. 23 with the rates of Sec. 4
+    R tauT, wg_den;    // tau_T and 1 / (tau_T + 1/2)
+    R gbeta, T0, az;   // buoyancy, reference temperature, external acceleration (z)
+    R nu;              // fluid viscosity nu = nu_e / J
+    R invKbar;         // 1 / (Da L^2)
+    R c_kappa;         // 1/K(phi) = c_kappa (1 - phi)^2 / phi^3 (porous_mode 2)
+    R F_eps;           // constant F_phi (ergun = 0)
+    R T_hot, T_cold;
+};
+
+template <typename R> __host__ __device__ constexpr R cs2() { return R(1) / R(3); }
+
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+
+// Node class (Fig. 1, Fig. 3): walls on the outermost nodes, corners on the side walls.
+__host__ __device__ __forceinline__ int node_class(int geometry, int nr, int nz, int kr, int kz) {
+    if (kr == nr - 1) return WALL_OUT;
+    if (kr == 0) return geometry == PIPE_PERIODIC_Z ? AXIS : WALL_IN;
+    if (geometry == ANNULUS) {
+        if (kz == 0) return BOTTOM;
+        if (kz == nz - 1) return TOP;
+    }
+    return FLUID;
+}
+__host__ __device__ __forceinline__ bool is_wall(int cls) { return cls >= WALL_IN && cls <= TOP; }
+
+// Interior neighbour a wall node extrapolates from (wall normal; corners diagonal).
+__device__ __forceinline__ void fluid_neighbour(int geometry, int nr, int nz, int cls, int kr, int kz,
+                                                int& fr, int& fz) {
+    fr = kr;
+    fz = kz;
+    if (cls == WALL_IN) fr = 1;
+    else if (cls == WALL_OUT) fr = nr - 2;
+    else if (cls == BOTTOM) fz = 1;
+    else if (cls == TOP) fz = nz - 2;
+    if ((cls == WALL_IN || cls == WALL_OUT) && geometry == ANNULUS) {
+        if (kz == 0) fz = 1;
+        if (kz == nz - 1) fz = nz - 2;
+    }
+}
+
+// Eq. 8 per node: nu / K and F_phi / sqrt(K).
+template <typename R>
+__device__ __forceinline__ void porous(const Consts<R>& c, R phi, R& lin, R& nl) {
+    R invK;
+    if (c.porous_mode == 0) invK = R(0);
+    else if (c.porous_mode == 1) invK = c.invKbar;
+    else {
+        const R om = R(1) - phi;
+        invK = c.c_kappa * om * om / (phi * phi * phi);
+    }
+    const R Fphi = c.ergun ? R(1.75) / dsqrt(R(150) * phi * phi * phi) : c.F_eps;
+    lin = c.nu * invK;
+    nl = Fphi * dsqrt(invK);
+}
+
+// Macroscopic fields of a non-wall node from its post-streaming deviations:
+// T (Eq. 38), rho (Eq. 26), G (Eq. 7), v (Eq. 29), l_j0, l_1 (Eq. 30), u (Eq. 28,
+// literally per component with |v| = sqrt(v_r^2 + v_z^2)).
+template <typename R>
+__device__ __forceinline__ void recover(const Consts<R>& c, R r, R inv_r, R phi, const R* fh, const R* gh,
+                                        R& m0, R& rho, R& ur, R& uz, R& dT) {
+    dT = gh[0] + gh[1] + gh[2] + gh[3] + gh[4];
+    m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
+    rho = R(1) + m0 * inv_r;
+    const R jr = (fh[1] - fh[3]) + (fh[5] - fh[6]) + (fh[8] - fh[7]);
+    const R jz = (fh[2] - fh[4]) + (fh[5] + fh[6]) - (fh[7] + fh[8]);
+    const R Gz = c.gbeta * dT + c.az;
+    const R inv_rho = R(1) / rho;
+    const R vr = jr * inv_rho + R(0.5) * cs2<R>();
+    const R vz = jz * inv_rho + R(0.5) * r * phi * Gz;
+    R lin, nl;
+    porous(c, phi, lin, nl);
+    const R hd = R(0.25) * r * phi * lin;
+    const R lr0 = R(0.5) * (r + c.cs2tau * inv_r) + hd;
+    const R lz0 = R(0.5) * r + hd;
+    const R l1 = R(0.5) * r * phi * nl;
+    const R vm = dsqrt(vr * vr + vz * vz);
+    ur = vr / (lr0 + dsqrt(lr0 * lr0 + l1 * vm));
+    uz = vz / (lz0 + dsqrt(lz0 * lz0 + l1 * vm));
+}
+
+// f = M^-1 m with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+template <typename R>
+__device__ __forceinline__ void minv(const R* m, R* f) {
+    const R a0 = m[0] * R(1.0 / 9), a1 = m[1] * R(1.0 / 36), a2 = m[2] * R(1.0 / 36);
+    const R a3 = m[3] * R(1.0 / 6), a4 = m[4] * R(1.0 / 12), a5 = m[5] * R(1.0 / 6), a6 = m[6] * R(1.0 / 12);
+    const R a7 = m[7] * R(0.25), a8 = m[8] * R(0.25);
+    const R b14 = a0 - a1 - R(2) * a2;
+    const R b58 = a0 + R(2) * a1 + a2;
+    const R x3 = a3 - R(2) * a4, x5 = a5 - R(2) * a6;
+    const R y3 = a3 + a4, y5 = a5 + a6;
+    f[0] = a0 - R(4) * a1 + R(4) * a2;
+    f[1] = b14 + x3 + a7;
+    f[2] = b14 + x5 - a7;
+    f[3] = b14 - x3 + a7;
+    f[4] = b14 - x5 - a7;
+    f[5] = b58 + y3 + y5 + a8;
+    f[6] = b58 - y3 + y5 - a8;
+    f[7] = b58 - y3 - y5 + a8;
+    f[8] = b58 + y3 - y5 - a8;
+}
+
+// Collision of one node (in place on fh, gh): forces (Eq. 6, 25), source (Eq. 24),
+// MRT relaxation (Eq. 21) and f+ = M^-1 m+ (Eq. 22); D2Q5 update (Eq. 33, 35-37)
+// with omega_g,i = (1 + e_ir tau_T / r) / (tau_T + 1/2).  rho, u, T are given so
+// that wall nodes can impose u = 0 and their temperature; m0 = sum_i fh_i.
+template <typename R>
+__device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi, R* fh, R* gh, R m0, R rho,
+                                        R ur, R uz, R dT) {
+    R lin, nl;
+    porous(c, phi, lin, nl);
+    const R T = c.T0 + dT;
+    const R u2 = ur * ur + uz * uz;
+    const R um = dsqrt(u2);
+    const R Gz = c.gbeta * dT + c.az;
+    const R drag = lin + nl * um;
+    const R Ftr = -phi * drag * ur + cs2<R>() * (R(1) - c.two_taum * ur * inv_r) * inv_r;
+    const R Ftz = -phi * drag * uz + phi * Gz;
+    const R inv_phi = R(1) / phi;
+    const R rr = r * rho;
+    // Eq. 24
+    const R S1 = R(6) * rr * (ur * Ftr + uz * Ftz) * inv_phi;
+    const R S3 = rr * Ftr;
+    const R S5 = rr * Ftz;
+    const R S7 = R(2) * rr * (ur * Ftr - uz * Ftz) * inv_phi;
+    const R S8 = rr * (ur * Ftz + uz * Ftr) * inv_phi;
+    // m = M f on the deviations (Eq. 16, 18)
+    const R s14 = (fh[1] + fh[2]) + (fh[3] + fh[4]);
+    const R s58 = (fh[5] + fh[6]) + (fh[7] + fh[8]);
+    const R m1 = R(-4) * fh[0] - s14 + R(2) * s58;
+    const R m2 = R(4) * fh[0] - R(2) * s14 + s58;
+    const R d13 = fh[1] - fh[3], d24 = fh[2] - fh[4];
+    const R x58 = (fh[5] - fh[7]), x68 = (fh[6] - fh[8]);
+    const R m3 = d13 + x58 - x68;
+    const R m4 = R(-2) * d13 + x58 - x68;
+    const R m5 = d24 + x58 + x68;
+    const R m6 = R(-2) * d24 + x58 + x68;
+    const R m7 = (fh[1] + fh[3]) - (fh[2] + fh[4]);
+    const R m8 = (fh[5] + fh[7]) - (fh[6] + fh[8]);
+    // m_eq - r (1, -2, 1, 0, ...) (Eq. 19-20)
+    const R q = R(3) * rr * u2 * inv_phi;
+    const R e1 = R(-2) * m0 + q, e2 = m0 - q;
+    const R e3 = rr * ur, e5 = rr * uz;
+    const R e7 = rr * (ur * ur - uz * uz) * inv_phi, e8 = rr * ur * uz * inv_phi;
+    // Eq. 21 with Lambda = diag(1, s_e, s_eps, s_j, s_q, s_j, s_q, s_nu, s_nu)
+    const R p1 = m1 - c.s_e * (m1 - e1) + (R(1) - R(0.5) * c.s_e) * S1;
+    const R p2 = m2 - c.s_eps * (m2 - e2) - (R(1) - R(0.5) * c.s_eps) * S1;
+    const R p3 = m3 - c.s_j * (m3 - e3) + (R(1) - R(0.5) * c.s_j) * S3;
+    const R p4 = m4 - c.s_q * (m4 + e3) - (R(1) - R(0.5) * c.s_q) * S3;
+    const R p5 = m5 - c.s_j * (m5 - e5) + (R(1) - R(0.5) * c.s_j) * S5;
+    const R p6 = m6 - c.s_q * (m6 + e5) - (R(1) - R(0.5) * c.s_q) * S5;
+    const R p7 = m7 - c.s_nu * (m7 - e7) + (R(1) - R(0.5) * c.s_nu) * S7;
+    const R p8 = m8 - c.s_nu * (m8 - e8) + (R(1) - R(0.5) * c.s_nu) * S8;
+    // Eq. 22: f+ = M^-1 m+
+    const R mp[9] = {m0, p1, p2, p3, p4, p5, p6, p7, p8};
+    minv(mp, fh);
+    // D2Q5 (Eq. 33, 35-37)
+    const R k = c.tauT * inv_r;
+    const R wd = c.wg_den;
+    const R cu = -ur * inv_r;
+    const R Tr = R(0.5) * T * ur, Tz = R(0.5) * T * uz;
+    const R g0e = R(0.6) * dT;                     // g_eq - wT T0
+    const R g1e = R(0.1) * dT + Tr, g3e = R(0.1) * dT - Tr;
+    const R g2e = R(0.1) * dT + Tz, g4e = R(0.1) * dT - Tz;
+    const R wT0 = R(0.6) * c.T0, wT1 = R(0.1) * c.T0;
+    gh[0] = gh[0] - wd * (gh[0] - g0e) + cu * (g0e + wT0);
+    gh[1] = gh[1] - (R(1) + k) * wd * (gh[1] - g1e) + cu * (g1e + wT1);
+    gh[2] = gh[2] - wd * (gh[2] - g2e) + cu * (g2e + wT1);
+    gh[3] = gh[3] - (R(1) - k) * wd * (gh[3] - g3e) + cu * (g3e + wT1);
+    gh[4] = gh[4] - wd * (gh[4] - g4e) + cu * (g4e + wT1);
+}
+
+// D2Q9 direction tables (Eq. 14) and weights (Eq. 32).
+__host__ __device__ constexpr int ex9(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
+__host__ __device__ constexpr int ez9(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
+__host__ __device__ constexpr int mirror9(int i) { return i == 1 ? 3 : i == 3 ? 1 : i == 5 ? 6 : i == 6 ? 5 : i == 7 ? 8 : i == 8 ? 7 : i; }
+template <typename R> __host__ __device__ constexpr R w9(int i) { return i == 0 ? R(4) / R(9) : i < 5 ? R(1) / R(9) : R(1) / R(36); }
+
+// Wall node rebuild by non-equilibrium extrapolation (Sec. 4, ref. [47]) from the
+// interior neighbour's post-streaming deviations (fhf at radius rf):
+//   f_b = f_eq(r_b, rho_f, 0) + [f_f - f_eq(r_f, rho_f, u_f)]      (Eq. 32)
+// In deviations: fh_b,i = r_b w_i drho_f + fh_f,i - r_f w_i [drho_f + rho_f (3 eu
+// + 4.5 eu^2 / phi_f - 1.5 u^2 / phi_f)], drho_f = m0f / r_f.
+template <typename R>
+__device__ __forceinline__ void rebuild_flow(R rb, R rf, R phif, R m0f, R rhof, R urf, R uzf, const R* fhf,
+                                             R* fh) {
+    const R drho = m0f / rf;
+    const R u2 = urf * urf + uzf * uzf;
+    const R iphi = R(1) / phif;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R eu = R(ex9(i)) * urf + R(ez9(i)) * uzf;
+        const R q = drho + rhof * (R(3) * eu + R(4.5) * eu * eu * iphi - R(1.5) * u2 * iphi);
+        fh[i] = rb * w9<R>(i) * drho + fhf[i] - rf * w9<R>(i) * q;
+    }
+}
+
+// Thermal part of the wall rebuild: g_b = g_eq(T_b, 0) + [g_f - g_eq(T_f, u_f)]
+// (Eq. 35); in deviations gh_b,i = wT_i (T_b - T0) + gh_f,i - (g_eq,i(T_f, u_f) - wT_i T0).
+template <typename R>
+__device__ __forceinline__ void rebuild_thermal(R T0, R dTf, R dTb, R urf, R uzf, const R* ghf, R* gh) {
+    const R Tf = T0 + dTf;
+    const R tr = R(0.5) * Tf * urf, tz = R(0.5) * Tf * uzf;
+    gh[0] = R(0.6) * dTb + ghf[0] - R(0.6) * dTf;
+    gh[1] = R(0.1) * dTb + ghf[1] - (R(0.1) * dTf + tr);
+    gh[2] = R(0.1) * dTb + ghf[2] - (R(0.1) * dTf + tz);
+    gh[3] = R(0.1) * dTb + ghf[3] - (R(0.1) * dTf - tr);
+    gh[4] = R(0.1) * dTb + ghf[4] - (R(0.1) * dTf - tz);
+}
+
+}  // namespace lbm

@@ -1,0 +1,86 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every entry
+point the headers declare; host-side parameter derivation agrees with the oracle
+and rejects invalid input.  No device call is made here."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(lbm_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1409_5929_gb300 import build, lbm as L
+
+    build.build()
+    L.load()
+    return L
+
+
+def test_every_declared_symbol_is_exported(lbm):
+    names = _declared()
+    assert len(names) >= 15
+    lib = C.CDLL(lbm.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def _oracle_params(oracle, p):
+    return oracle.params(nr=p.nr, nz=p.nz, geometry=p.geometry, radius_ratio=p.radius_ratio, Ra=p.Ra, Da=p.Da,
+                         Pr=p.Pr, J=p.J, lam=p.lam, Ma=p.Ma, tau_nu=p.tau_nu, F_eps=p.F_eps, eps_mean=p.eps_mean,
+                         T_hot=p.T_hot, T_cold=p.T_cold, body_accel_z=p.body_accel_z, init_noise=p.init_noise,
+                         seed=p.seed)
+
+
+@pytest.mark.parametrize("kw", [
+    {},
+    dict(nr=4096, nz=8192, Ra=1e6, Da=1e-4, Pr=0.71),
+    dict(nr=8192, nz=8192, Ra=1e7, Da=1e-6, Pr=0.71, tau_nu=0.51, eps_mean=0.4, storage="f16"),
+    dict(nr=33, nz=4, geometry=2, Ra=0.0, tau_nu=0.8, Da=0.0625, F_eps=0.0, eps_mean=1.0, body_accel_z=1e-5),
+    dict(nr=100, nz=200, Ra=1e5, Pr=0.7, Da=1e8, eps_mean=1.0, F_eps=0.0),
+])
+def test_derivation_matches_oracle(lbm, oracle, kw):
+    p = lbm.lbm_params_default(**kw)
+    info = lbm.lbm_derive(p)
+    ref = oracle.derive(_oracle_params(oracle, p))
+    for k_lib, k_ref in (("L", "L"), ("H", "H"), ("r0", "r0"), ("tau_nu", "tau"), ("tau_T", "tauT"),
+                         ("nu_e", "nu_e"), ("nu", "nu"), ("gbeta", "gbeta"), ("T0", "T0"), ("Kbar", "Kbar")):
+        assert np.isclose(getattr(info, k_lib), ref[k_ref], rtol=1e-14, atol=0), k_lib
+    es = 4 if p.storage == 0 else 2
+    assert info.bytes_per_step == p.nr * p.nz * (28 * es + es)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nr=2), dict(nz=1), dict(tau_nu=0.5), dict(radius_ratio=1.0), dict(eps_mean=0.0), dict(eps_mean=1.5),
+    dict(geometry=7), dict(storage=5), dict(Ra=0.0, tau_nu=0.0), dict(Pr=0.0), dict(T_hot=0.0, T_cold=0.0),
+    dict(nr=70000),
+])
+def test_invalid_parameters_rejected(lbm, bad):
+    p = lbm.lbm_params_default(**bad)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_derive(p)
+    assert e.value.code == lbm.LBM_ERR_INVALID
+    assert lbm.load().lbm_last_error().decode()
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The library package never imports, links or loads the oracle (no CPU fallback)."""
+    pkg = os.path.join(ROOT, "paper_1409_5929_gb300")
+    pat = re.compile(r"(import\s+oracle|from\s+oracle|liblbm_oracle|\borc_\w+|lbm_oracle)")
+    for path in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            assert not pat.search(open(path).read()), path
