@@ -122,8 +122,8 @@ def run_ours(args, rank, world, local_rank):
     info = s.info()
     nodes = NR * NZ
     interior = (NR - 2) * (NZ - 2)
-    es = 4 if args.storage == "f32" else 2
-    bulk_bytes = interior * (28 * es + es)          # algorithmic bytes of one bulk launch
+    ef = 4 if args.storage == "f32" else 2          # flow populations; temperature populations are FP32
+    bulk_bytes = interior * (2 * (9 * ef + 5 * 4) + ef)   # algorithmic bytes of one bulk launch
 
     s.step(args.warmup)
     torch.cuda.synchronize()

@@ -5,9 +5,10 @@
 //
 // Data layout in HBM (per handle):
 //   state A, state B: 14 planes (f_0..f_8, g_0..g_4), each nr*nz elements, z fastest,
-//                     plane stride padded to 64 elements; element type = storage
-//                     type (FP32, FP16 or BF16), holding the deviations of
-//                     lbm_physics.cuh.  A step reads one buffer and writes the other.
+//                     plane stride padded to 64 elements; f planes in the storage
+//                     type (FP32, FP16 or BF16), g planes in FP32, holding the
+//                     deviations of lbm_physics.cuh.  A step reads one buffer and
+//                     writes the other.
 //   phi:              nr*nz porosity values (FP32, or FP16 with 16-bit storage).
 //   macro snapshots, reduction scratch, staging: only for diagnostics.
 //
@@ -35,88 +36,82 @@
 using namespace lbm;
 
 // ------------------------------------------------------------ storage types --
+// Flow populations in the storage type; temperature populations always FP32 (in
+// 16 bits the per-step change of g - wT T0, of order 0.05, falls below the format's
+// resolution and the temperature field stagnates); porosity FP32, or FP16 with
+// 16-bit storage.
+__device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float ldv(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ void stv(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stv(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void stv(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
 template <int STO> struct St;
-template <> struct St<LBM_F32> {
-    using T = float;
-    using P = float;
-    __device__ static __forceinline__ float ld(const T* p) { return __ldg(p); }
-    __device__ static __forceinline__ void st(T* p, float v) { *p = v; }
-    __device__ static __forceinline__ float ldp(const P* p) { return __ldg(p); }
-    __host__ __device__ static __forceinline__ P mkp(float v) { return v; }
-};
-template <> struct St<LBM_F16> {
-    using T = __half;
-    using P = __half;
-    __device__ static __forceinline__ float ld(const T* p) { return __half2float(__ldg(p)); }
-    __device__ static __forceinline__ void st(T* p, float v) { *p = __float2half_rn(v); }
-    __device__ static __forceinline__ float ldp(const P* p) { return __half2float(__ldg(p)); }
-    __device__ static __forceinline__ P mkp(float v) { return __float2half_rn(v); }
-};
-template <> struct St<LBM_BF16> {
-    using T = __nv_bfloat16;
-    using P = __half;
-    __device__ static __forceinline__ float ld(const T* p) { return __bfloat162float(__ldg(p)); }
-    __device__ static __forceinline__ void st(T* p, float v) { *p = __float2bfloat16_rn(v); }
-    __device__ static __forceinline__ float ldp(const P* p) { return __half2float(__ldg(p)); }
-    __device__ static __forceinline__ P mkp(float v) { return __float2half_rn(v); }
+template <> struct St<LBM_F32> { using TF = float; using TG = float; using P = float; };
+template <> struct St<LBM_F16> { using TF = __half; using TG = float; using P = __half; };
+template <> struct St<LBM_BF16> { using TF = __nv_bfloat16; using TG = float; using P = __half; };
+
+// One state buffer: nine flow planes then five temperature planes.
+template <int STO> struct Buf {
+    typename St<STO>::TF* f;
+    typename St<STO>::TG* g;
 };
 
-static size_t elem_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
+static size_t f_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
+static size_t g_size(int) { return 4; }
 static size_t phi_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
+static size_t state_bytes(int sto, int64_t plane) { return (size_t)plane * (9 * f_size(sto) + 5 * g_size(sto)); }
 
 constexpr int BULK_THREADS = 128;
 
 // ------------------------------------------------------------- pull (Eq. 22) --
-// Post-streaming deviations at (kr, kz) from the post-collision buffer A: f_i(x) =
-// f_i+(x - e_i), minus e_ir w_i for the change of r.  Periodic z wraps; in the pipe,
-// row 0 pulls its e_r = +1 populations from the mirror image of itself (the ghost
-// row below the axis), with e_r reversed and no change of r.
-template <int STO, typename R>
-__device__ __forceinline__ void pull(const Consts<R>& c, const typename St<STO>::T* __restrict__ A, int64_t plane,
-                                     int kr, int kz, R* fh, R* gh) {
-    using S = St<STO>;
+// Pre-collision deviations at (kr, kz) from the post-collision buffer A: a plain
+// copy of ft_i(x - e_i) (see lbm_physics.cuh).  Periodic z wraps; in the pipe, row 0
+// takes its e_r = +1 populations from the mirror image of itself (the ghost row
+// below the axis, e_r reversed).
+template <int STO, typename R, typename I = int64_t>
+__device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh, R* gh) {
     const bool pz = c.geometry != ANNULUS;
     const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;       // source column for e_z = +1
     const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;       // source column for e_z = -1
-    const int64_t row = (int64_t)kr * c.nz;
-    const int64_t rowm = row - c.nz, rowp = row + c.nz;
+    const I row = (I)kr * c.nz;
+    const I rowm = row - c.nz, rowp = row + c.nz;
     const bool axis = (kr == 0);                              // reached only in the pipe
-    const R w1 = R(1) / R(9), w5 = R(1) / R(36);
     // e_r = +1 populations: from row kr - 1, or on the axis row from the mirror image
-    const int64_t i1 = axis ? 3 * plane + row + kz : 1 * plane + rowm + kz;
-    const int64_t i5 = axis ? 6 * plane + row + zm : 5 * plane + rowm + zm;
-    const int64_t i8 = axis ? 7 * plane + row + zp : 8 * plane + rowm + zp;
-    const R c1 = axis ? R(0) : w1, c5 = axis ? R(0) : w5;
-    fh[0] = R(S::ld(A + row + kz));
-    fh[1] = R(S::ld(A + i1)) - c1;
-    fh[2] = R(S::ld(A + 2 * plane + row + zm));
-    fh[3] = R(S::ld(A + 3 * plane + rowp + kz)) + w1;
-    fh[4] = R(S::ld(A + 4 * plane + row + zp));
-    fh[5] = R(S::ld(A + i5)) - c5;
-    fh[6] = R(S::ld(A + 6 * plane + rowp + zm)) + w5;
-    fh[7] = R(S::ld(A + 7 * plane + rowp + zp)) + w5;
-    fh[8] = R(S::ld(A + i8)) - c5;
-    const typename S::T* G = A + 9 * plane;
-    gh[0] = R(S::ld(G + row + kz));
-    gh[1] = R(S::ld(G + (axis ? 3 * plane + row + kz : 1 * plane + rowm + kz)));
-    gh[2] = R(S::ld(G + 2 * plane + row + zm));
-    gh[3] = R(S::ld(G + 3 * plane + rowp + kz));
-    gh[4] = R(S::ld(G + 4 * plane + row + zp));
+    const I i1 = axis ? 3 * plane + row + kz : 1 * plane + rowm + kz;
+    const I i5 = axis ? 6 * plane + row + zm : 5 * plane + rowm + zm;
+    const I i8 = axis ? 7 * plane + row + zp : 8 * plane + rowm + zp;
+    const auto* __restrict__ F = A.f;
+    const auto* __restrict__ G = A.g;
+    fh[0] = R(ldv(F + row + kz));
+    fh[1] = R(ldv(F + i1));
+    fh[2] = R(ldv(F + 2 * plane + row + zm));
+    fh[3] = R(ldv(F + 3 * plane + rowp + kz));
+    fh[4] = R(ldv(F + 4 * plane + row + zp));
+    fh[5] = R(ldv(F + i5));
+    fh[6] = R(ldv(F + 6 * plane + rowp + zm));
+    fh[7] = R(ldv(F + 7 * plane + rowp + zp));
+    fh[8] = R(ldv(F + i8));
+    gh[0] = R(ldv(G + row + kz));
+    gh[1] = R(ldv(G + (axis ? 3 * plane + row + kz : 1 * plane + rowm + kz)));
+    gh[2] = R(ldv(G + 2 * plane + row + zm));
+    gh[3] = R(ldv(G + 3 * plane + rowp + kz));
+    gh[4] = R(ldv(G + 4 * plane + row + zp));
 }
 
-template <int STO, typename R>
-__device__ __forceinline__ void store(typename St<STO>::T* __restrict__ B, int64_t plane, int64_t n, const R* fh,
-                                      const R* gh) {
+template <int STO, typename R, typename I = int64_t>
+__device__ __forceinline__ void store(const Buf<STO>& B, I plane, I n, const R* fh, const R* gh) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) St<STO>::st(B + i * plane + n, float(fh[i]));
+    for (int i = 0; i < 9; ++i) stv(B.f + i * plane + n, float(fh[i]));
 #pragma unroll
-    for (int i = 0; i < 5; ++i) St<STO>::st(B + (9 + i) * plane + n, float(gh[i]));
+    for (int i = 0; i < 5; ++i) stv(B.g + i * plane + n, float(gh[i]));
 }
 
 // Wall node state: rebuild (Sec. 4, ref. [47]) from the interior neighbour, then
 // rho from Eq. 26 and the wall temperature (T_hot, T_cold, or T_f when adiabatic).
 template <int STO, typename R>
-__device__ __forceinline__ void wall_state(const Consts<R>& c, const typename St<STO>::T* __restrict__ A,
+__device__ __forceinline__ void wall_state(const Consts<R>& c, const Buf<STO> A,
                                            const typename St<STO>::P* __restrict__ phi, int64_t plane, int cls,
                                            int kr, int kz, R* fh, R* gh, R& m0, R& rho, R& dTb) {
     int fr, fz;
@@ -124,14 +119,15 @@ __device__ __forceinline__ void wall_state(const Consts<R>& c, const typename St
     R fhf[9], ghf[5];
     pull<STO>(c, A, plane, fr, fz, fhf, ghf);
     const R rf = c.r0 + R(fr), rb = c.r0 + R(kr);
-    const R phif = R(St<STO>::ldp(phi + (int64_t)fr * c.nz + fz));
-    R m0f, rhof, urf, uzf, dTf;
-    recover(c, rf, R(1) / rf, phif, fhf, ghf, m0f, rhof, urf, uzf, dTf);
-    rebuild_flow(rb, rf, phif, m0f, rhof, urf, uzf, fhf, fh);
+    const R phif = R(ldv(phi + (int64_t)fr * c.nz + fz));
+    R m0f, rhof, urf, uzf, dTf, lin, nl, ipf;
+    porous(c, phif, lin, nl, ipf);
+    recover(c, rf, rcp_acc(rf), phif, lin, nl, fhf, ghf, m0f, rhof, urf, uzf, dTf);
+    rebuild_flow(rb, rf, ipf, m0f, rhof, urf, uzf, fhf, fh);
     dTb = cls == WALL_IN ? c.T_hot - c.T0 : cls == WALL_OUT ? c.T_cold - c.T0 : dTf;
     rebuild_thermal(c.T0, dTf, dTb, urf, uzf, ghf, gh);
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
-    rho = R(1) + m0 / rb;
+    rho = R(1) + m0 * rcp_acc(rb);
 }
 
 // Wall node t -> (kr, kz): inner wall (annulus), outer wall, then bottom and top
@@ -156,28 +152,29 @@ static int wall_count(int geometry, int nr, int nz) {
 }
 
 // ------------------------------------------------------------------ kernels --
-template <int STO>
-__global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Consts<float> c, const typename St<STO>::T* __restrict__ A,
-                                                       typename St<STO>::T* __restrict__ B,
-                                                       const typename St<STO>::P* __restrict__ phi, int64_t plane) {
+// I: index type; 32-bit when the state buffer holds fewer than 2^31 elements.
+template <int STO, typename I>
+__global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
+                                                       const typename St<STO>::P* __restrict__ phi, I plane) {
     const int kz = blockIdx.x * BULK_THREADS + threadIdx.x;
     const int kr = blockIdx.y;
     if (kz >= c.nz) return;
     if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) return;
     float fh[9], gh[5];
-    pull<STO>(c, A, plane, kr, kz, fh, gh);
-    const int64_t n = (int64_t)kr * c.nz + kz;
-    const float r = c.r0 + float(kr), inv_r = 1.0f / r;
-    const float ph = St<STO>::ldp(phi + n);
-    float m0, rho, ur, uz, dT;
-    recover(c, r, inv_r, ph, fh, gh, m0, rho, ur, uz, dT);
-    collide(c, r, inv_r, ph, fh, gh, m0, rho, ur, uz, dT);
-    store<STO>(B, plane, n, fh, gh);
+    pull<STO, float, I>(c, A, plane, kr, kz, fh, gh);
+    const I n = (I)kr * c.nz + kz;
+    const float r = c.r0 + float(kr), inv_r = rcp_acc(r);
+    const float ph = ldv(phi + n);
+    float m0, rho, ur, uz, dT, lin, nl, iph;
+    porous(c, ph, lin, nl, iph);
+    recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+    collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
+    store<STO, float, I>(B, plane, n, fh, gh);
 }
 
 template <int STO>
-__global__ void k_wall(const Consts<float> c, const typename St<STO>::T* __restrict__ A,
-                       typename St<STO>::T* __restrict__ B, const typename St<STO>::P* __restrict__ phi,
+__global__ void k_wall(const Consts<float> c, const Buf<STO> A,
+                       const Buf<STO> B, const typename St<STO>::P* __restrict__ phi,
                        int64_t plane, int count) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
@@ -187,14 +184,16 @@ __global__ void k_wall(const Consts<float> c, const typename St<STO>::T* __restr
     float fh[9], gh[5], m0, rho, dTb;
     wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dTb);
     const int64_t n = (int64_t)kr * c.nz + kz;
-    const float r = c.r0 + float(kr);
-    collide(c, r, 1.0f / r, St<STO>::ldp(phi + n), fh, gh, m0, rho, 0.0f, 0.0f, dTb);
+    const float r = c.r0 + float(kr), ph = ldv(phi + n);
+    float lin, nl, iph;
+    porous(c, ph, lin, nl, iph);
+    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, m0, rho, 0.0f, 0.0f, dTb);
     store<STO>(B, plane, n, fh, gh);
 }
 
 // Fields of a state at every node (NULL outputs skipped).
 template <int STO>
-__global__ void k_moments(const Consts<float> c, const typename St<STO>::T* __restrict__ A,
+__global__ void k_moments(const Consts<float> c, const Buf<STO> A,
                           const typename St<STO>::P* __restrict__ phi, int64_t plane, float* rho_o, float* ur_o,
                           float* uz_o, float* T_o) {
     const int kz = blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,8 +206,10 @@ __global__ void k_moments(const Consts<float> c, const typename St<STO>::T* __re
         wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dT);
     } else {
         pull<STO>(c, A, plane, kr, kz, fh, gh);
-        const float r = c.r0 + float(kr);
-        recover(c, r, 1.0f / r, St<STO>::ldp(phi + n), fh, gh, m0, rho, ur, uz, dT);
+        const float r = c.r0 + float(kr), ph = ldv(phi + n);
+        float lin, nl, iph;
+        porous(c, ph, lin, nl, iph);
+        recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
     }
     if (rho_o) rho_o[n] = rho;
     if (ur_o) ur_o[n] = ur;
@@ -234,7 +235,7 @@ __device__ __forceinline__ double start_T(const Consts<double>& c, const float* 
 }
 
 template <int STO>
-__global__ void k_init(const Consts<double> c, typename St<STO>::T* __restrict__ B,
+__global__ void k_init(const Consts<double> c, const Buf<STO> B,
                        const typename St<STO>::P* __restrict__ phi, int64_t plane, const float* ur_in,
                        const float* uz_in, const float* T_in, double noise, uint64_t seed) {
     const int kz = blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,15 +255,17 @@ __global__ void k_init(const Consts<double> c, typename St<STO>::T* __restrict__
         ur = ur_in[n];
         uz = uz_in[n];
     }
-    const double ph = (double)St<STO>::ldp(phi + n);
-    double lin, nl;
-    porous(c, ph, lin, nl);
+    const double ph = (double)ldv(phi + n);
+    double lin, nl, iphi;
+    porous(c, ph, lin, nl, iphi);
     const double um = sqrt(ur * ur + uz * uz);
-    const double Ftr = -ph * (lin + nl * um) * ur + cs2<double>() * (1 - c.two_taum * ur * inv_r) * inv_r;
+    const double Fr = -ph * (lin + nl * um) * ur;
+    const double Ftr = Fr + cs2<double>() * (1 - c.two_taum * ur * inv_r) * inv_r;
     const double Ftz = -ph * (lin + nl * um) * uz + ph * (c.gbeta * (T - c.T0) + c.az);
-    const double iphi = 1.0 / ph, u2 = ur * ur + uz * uz;
-    // m_eq(rho = 1) - r(1, -2, 1, 0, ...) - S / 2
-    const double S1 = 6 * r * (ur * Ftr + uz * Ftz) * iphi, S3 = r * Ftr, S5 = r * Ftz;
+    const double u2 = ur * ur + uz * uz;
+    // deviation moments of f = M^-1 (m_eq - S/2) at rho = 1 (S_3 without its rest c_s^2)
+    const double S1 = 6 * r * (ur * Ftr + uz * Ftz) * iphi, S5 = r * Ftz;
+    const double S3 = r * Fr - cs2<double>() * c.two_taum * ur * inv_r;
     const double S7 = 2 * r * (ur * Ftr - uz * Ftz) * iphi, S8 = r * (ur * Ftz + uz * Ftr) * iphi;
     const double q = 3 * r * u2 * iphi;
     const double mpre[9] = {0.0,
@@ -288,11 +291,16 @@ __global__ void k_init(const Consts<double> c, typename St<STO>::T* __restrict__
         rho = 1 + m0 * inv_r;
         dT = dTs;
     } else {
-        recover(c, r, inv_r, ph, fh, gh, m0, rho, u_r, u_z, dT);
+        recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, u_r, u_z, dT);
     }
-    collide(c, r, inv_r, ph, fh, gh, m0, rho, u_r, u_z, dT);
+    collide(c, r, inv_r, ph, lin, nl, iphi, fh, gh, m0, rho, u_r, u_z, dT);
     store<STO>(B, plane, n, fh, gh);
 }
+
+template <int STO> __device__ __forceinline__ typename St<STO>::P mkp(float v);
+template <> __device__ __forceinline__ float mkp<LBM_F32>(float v) { return v; }
+template <> __device__ __forceinline__ __half mkp<LBM_F16>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half mkp<LBM_BF16>(float v) { return __float2half_rn(v); }
 
 // Porosity upload: validate (0 < phi <= 1) and convert to the storage type.
 template <int STO>
@@ -302,13 +310,13 @@ __global__ void k_phi(const float* __restrict__ src, typename St<STO>::P* __rest
     if (i >= n) return;
     const float v = src[i];
     if (!(v > 0.f && v <= 1.f)) atomicAdd(bad, 1u);
-    dst[i] = St<STO>::mkp(v);
+    dst[i] = mkp<STO>(v);
 }
 
 template <int STO>
 __global__ void k_phi_fill(typename St<STO>::P* __restrict__ dst, int64_t n, float v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = St<STO>::mkp(v);
+    if (i < n) dst[i] = mkp<STO>(v);
 }
 
 __global__ void k_node_class(int geometry, int nr, int nz, uint8_t* out) {
@@ -379,7 +387,7 @@ __global__ void k_sum_rows(const double* __restrict__ partials, int rows, double
 // Temperature of node (kr, kz) of a state: wall temperature, the interior
 // neighbour's T on adiabatic walls, else sum of the pulled g (Eq. 38), in FP64.
 template <int STO>
-__device__ double node_T(const Consts<float>& c, const typename St<STO>::T* __restrict__ A, int64_t plane, int kr,
+__device__ double node_T(const Consts<float>& c, const Buf<STO> A, int64_t plane, int kr,
                          int kz) {
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
     if (cls == WALL_IN) return (double)c.T_hot;
@@ -397,7 +405,7 @@ __device__ double node_T(const Consts<float>& c, const typename St<STO>::T* __re
 
 // Eq. 42 for both walls in one block: one-sided second-order dT/dr, trapezoid in z.
 template <int STO>
-__global__ void k_nusselt(const Consts<float> c, const typename St<STO>::T* __restrict__ A, int64_t plane,
+__global__ void __launch_bounds__(256) k_nusselt(const Consts<float> c, const Buf<STO> A, int64_t plane,
                           double ri, double ro, double H, double dTw, double* __restrict__ result) {
     double v[2] = {0, 0};
     for (int kz = threadIdx.x; kz < c.nz; kz += blockDim.x) {
@@ -418,9 +426,9 @@ __global__ void k_nusselt(const Consts<float> c, const typename St<STO>::T* __re
 }
 
 // FP64 export of rows [row0, row0 + nrows): raw post-collision populations
-// f_i = fh_i + r w_i, g_i = gh_i + wT_i T0.
+// f_i = ft_i + r w_i + e_ir w_i / 2, g_i = gh_i + wT_i T0.
 template <int STO>
-__global__ void k_export(const Consts<float> c, const typename St<STO>::T* __restrict__ A, int64_t plane, int row0,
+__global__ void k_export(const Consts<float> c, const Buf<STO> A, int64_t plane, int row0,
                          int nrows, double r0, double T0, double* __restrict__ out) {
     const int kz = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
@@ -428,9 +436,9 @@ __global__ void k_export(const Consts<float> c, const typename St<STO>::T* __res
     const int kr = row0 + j;
     const int64_t n = (int64_t)kr * c.nz + kz, m = (int64_t)j * c.nz + kz, P = (int64_t)nrows * c.nz;
     const double r = r0 + kr;
-    for (int i = 0; i < 9; ++i) out[i * P + m] = (double)St<STO>::ld(A + i * plane + n) + r * w9<double>(i);
+    for (int i = 0; i < 9; ++i) out[i * P + m] = (double)ldv(A.f + i * plane + n) + (r + 0.5 * ex9(i)) * w9<double>(i);
     const double wt[5] = {0.6, 0.1, 0.1, 0.1, 0.1};
-    for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)St<STO>::ld(A + (9 + i) * plane + n) + wt[i] * T0;
+    for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)ldv(A.g + i * plane + n) + wt[i] * T0;
 }
 
 // ------------------------------------------------------------ host runtime --
@@ -521,7 +529,7 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
     o->T0 = 0.5 * (p->T_hot + p->T_cold);
     o->Kbar = p->Da * o->L * o->L;
     const int64_t N = (int64_t)p->nr * p->nz;
-    o->bytes_per_step = N * (28 * (int64_t)elem_size(p->storage) + (int64_t)phi_size(p->storage));
+    o->bytes_per_step = N * (int64_t)(2 * (9 * f_size(p->storage) + 5 * g_size(p->storage)) + phi_size(p->storage));
     if (cd) {
         Consts<double>& c = *cd;
         memset(&c, 0, sizeof(c));
@@ -543,11 +551,18 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         c.gbeta = o->gbeta;
         c.T0 = o->T0;
         c.az = p->body_accel_z;
-        c.nu = o->nu;
-        c.invKbar = p->Da > 0 ? 1.0 / o->Kbar : 0.0;
+        // Eq. 8 coefficients (see porous()): 1/K(phi) = c_k (1 - phi)^2 / phi^3 with
+        // c_k = eps_mean^3 / ((1 - eps_mean)^2 Da L^2), i.e. K(eps_mean) = Da L^2.
         const double em = p->eps_mean;
-        c.c_kappa = (p->Da > 0 && em < 1) ? em * em * em / ((1 - em) * (1 - em) * o->Kbar) : 0.0;
-        c.F_eps = p->F_eps > 0 ? p->F_eps : 0.0;
+        const double F = p->F_eps > 0 ? p->F_eps : 0.0;
+        if (c.porous_mode == 2) {
+            const double ck = em * em * em / ((1 - em) * (1 - em) * o->Kbar);
+            c.lin_coef = o->nu * ck;
+            c.nl_coef = c.ergun ? 1.75 * std::sqrt(ck / 150.0) : F * std::sqrt(ck);
+        } else if (c.porous_mode == 1) {
+            c.lin_coef = o->nu / o->Kbar;
+            c.nl_coef = c.ergun ? 1.75 * std::sqrt(1.0 / (150.0 * o->Kbar)) : F / std::sqrt(o->Kbar);
+        }
         c.T_hot = p->T_hot;
         c.T_cold = p->T_cold;
     }
@@ -560,8 +575,8 @@ static Consts<float> to_float(const Consts<double>& d) {
     f.r0 = (float)d.r0; f.cs2tau = (float)d.cs2tau; f.two_taum = (float)d.two_taum;
     f.s_e = (float)d.s_e; f.s_eps = (float)d.s_eps; f.s_j = (float)d.s_j; f.s_q = (float)d.s_q; f.s_nu = (float)d.s_nu;
     f.tauT = (float)d.tauT; f.wg_den = (float)d.wg_den; f.gbeta = (float)d.gbeta; f.T0 = (float)d.T0;
-    f.az = (float)d.az; f.nu = (float)d.nu; f.invKbar = (float)d.invKbar; f.c_kappa = (float)d.c_kappa;
-    f.F_eps = (float)d.F_eps; f.T_hot = (float)d.T_hot; f.T_cold = (float)d.T_cold;
+    f.az = (float)d.az; f.lin_coef = (float)d.lin_coef; f.nl_coef = (float)d.nl_coef;
+    f.T_hot = (float)d.T_hot; f.T_cold = (float)d.T_cold;
     return f;
 }
 
@@ -577,7 +592,13 @@ static dim3 grid2d(const lbm_handle* h, int threads) {
         default: { constexpr int S_ = LBM_BF16; __VA_ARGS__; } break;      \
     }
 
-template <int STO> using TT = typename St<STO>::T;
+template <int STO> static Buf<STO> bufp(const lbm_handle* h, int which) {
+    Buf<STO> b;
+    char* base = (char*)h->buf[which];
+    b.f = (typename St<STO>::TF*)base;
+    b.g = (typename St<STO>::TG*)(base + 9 * h->plane * f_size(STO));
+    return b;
+}
 template <int STO> using PP = typename St<STO>::P;
 
 extern "C" {
@@ -629,10 +650,9 @@ int lbm_destroy(lbm_handle* h) {
 }
 
 static int launch_init(lbm_handle* h, const float* ur, const float* uz, const float* T) {
-    void* dst = h->buf[0];
     dim3 g = grid2d(h, 128);
     DISPATCH_STO(h->p.storage,
-                 k_init<S_><<<g, 128, 0, h->stream>>>(h->cd, (TT<S_>*)dst, (const PP<S_>*)h->phi, h->plane, ur, uz,
+                 k_init<S_><<<g, 128, 0, h->stream>>>(h->cd, bufp<S_>(h, 0), (const PP<S_>*)h->phi, h->plane, ur, uz,
                                                       T, h->p.init_noise, h->p.seed));
     CK(cudaGetLastError());
     h->cur = 0;
@@ -653,7 +673,6 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     h->N = (int64_t)p->nr * p->nz;
     h->plane = (h->N + 63) / 64 * 64;
     h->mstride = h->plane;
-    const size_t es = elem_size(p->storage);
     h->pblocks = 1024;
 #define ALLOC(ptr, bytes)                                                       \
     do {                                                                        \
@@ -665,8 +684,8 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
                         "cudaMalloc(%zu bytes): %s", (size_t)(bytes), cudaGetErrorString(e_)); \
         }                                                                       \
     } while (0)
-    ALLOC(h->buf[0], 14 * h->plane * es);
-    ALLOC(h->buf[1], 14 * h->plane * es);
+    ALLOC(h->buf[0], state_bytes(p->storage, h->plane));
+    ALLOC(h->buf[1], state_bytes(p->storage, h->plane));
     ALLOC(h->phi, h->plane * phi_size(p->storage));
     ALLOC(h->partials, (size_t)h->pblocks * RES_NV * sizeof(double));
     ALLOC(h->result, 8 * sizeof(double));
@@ -749,8 +768,6 @@ int lbm_init_fields(lbm_handle* h, const float* ur, const float* uz, const float
 }
 
 static int launch_step(lbm_handle* h) {
-    const void* A = h->buf[h->cur];
-    void* B = h->buf[h->cur ^ 1];
     const dim3 g = grid2d(h, BULK_THREADS);
     const int nw = wall_count(h->p.geometry, h->p.nr, h->p.nz);
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -760,13 +777,21 @@ static int launch_step(lbm_handle* h) {
         CK(cudaEventCreate(&e2));
         CK(cudaEventRecord(e0, h->stream));
     }
-    DISPATCH_STO(h->p.storage,
-                 k_bulk<S_><<<g, BULK_THREADS, 0, h->stream>>>(h->cf, (const TT<S_>*)A, (TT<S_>*)B,
-                                                                (const PP<S_>*)h->phi, h->plane));
+    if (14 * h->plane < ((int64_t)1 << 31)) {
+        DISPATCH_STO(h->p.storage,
+                     k_bulk<S_, int><<<g, BULK_THREADS, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur),
+                                                                         bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi,
+                                                                         (int)h->plane));
+    } else {
+        DISPATCH_STO(h->p.storage,
+                     k_bulk<S_, int64_t><<<g, BULK_THREADS, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur),
+                                                                             bufp<S_>(h, h->cur ^ 1),
+                                                                             (const PP<S_>*)h->phi, h->plane));
+    }
     CK(cudaGetLastError());
     if (h->timing) CK(cudaEventRecord(e1, h->stream));
     DISPATCH_STO(h->p.storage,
-                 k_wall<S_><<<(nw + 127) / 128, 128, 0, h->stream>>>(h->cf, (const TT<S_>*)A, (TT<S_>*)B,
+                 k_wall<S_><<<(nw + 127) / 128, 128, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur), bufp<S_>(h, h->cur ^ 1),
                                                                      (const PP<S_>*)h->phi, h->plane, nw));
     CK(cudaGetLastError());
     if (h->timing) {
@@ -794,7 +819,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
 static int launch_moments(lbm_handle* h, int which, float* rho, float* ur, float* uz, float* T) {
     const dim3 g = grid2d(h, 128);
     DISPATCH_STO(h->p.storage,
-                 k_moments<S_><<<g, 128, 0, h->stream>>>(h->cf, (const TT<S_>*)h->buf[which], (const PP<S_>*)h->phi,
+                 k_moments<S_><<<g, 128, 0, h->stream>>>(h->cf, bufp<S_>(h, which), (const PP<S_>*)h->phi,
                                                          h->plane, rho, ur, uz, T));
     CK(cudaGetLastError());
     return LBM_OK;
@@ -828,7 +853,7 @@ int lbm_nusselt(lbm_handle* h, double* nu_inner, double* nu_outer) {
     const double dTw = h->p.T_hot - h->p.T_cold;
     const double ri = h->info.r0, ro = h->info.r0 + (h->p.nr - 1);
     DISPATCH_STO(h->p.storage,
-                 k_nusselt<S_><<<1, 1024, 0, h->stream>>>(h->cf, (const TT<S_>*)h->buf[h->cur], h->plane, ri, ro,
+                 k_nusselt<S_><<<1, 256, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur), h->plane, ri, ro,
                                                           h->info.H, dTw, h->result));
     CK(cudaGetLastError());
     double r[2];
@@ -911,7 +936,7 @@ int lbm_export_populations(lbm_handle* h, int32_t row0, int32_t nrows, double* f
     double* d = nullptr;
     CK(cudaMallocAsync((void**)&d, 14 * P * sizeof(double), h->stream));
     dim3 grid((unsigned)((h->p.nz + 127) / 128), (unsigned)nrows);
-    DISPATCH_STO(h->p.storage, k_export<S_><<<grid, 128, 0, h->stream>>>(h->cf, (const TT<S_>*)h->buf[h->cur], h->plane,
+    DISPATCH_STO(h->p.storage, k_export<S_><<<grid, 128, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur), h->plane,
                                                                           row0, nrows, h->info.r0, h->info.T0, d));
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, 9 * P * sizeof(double), cudaMemcpyDeviceToHost, h->stream);

@@ -2,15 +2,19 @@
 // (Liu, He & Li, arXiv 1409.5929, Sec. 3.1-3.2 and Sec. 4), device side.
 //
 // Variables.  The populations of Eq. 17 carry a factor r.  Between steps they are
-// stored as deviations from the rest state (rho0 = 1, T0):
-//     fh_i = f_i - r w_i          (w_i of Eq. 32)
-//     gh_i = g_i - wT_i T0        (wT_i of Eq. 36)
-// so that every quantity handled is small and FP32 (or FP16/BF16 storage) keeps
-// its relative precision.  Pulling a population across a row changes r by -e_ir,
-// so the pulled deviation is the stored one minus e_ir w_i (Eq. 22).  The moments
-// are taken of the deviations, mh = M fh = m - r (1, -2, 1, 0, ..., 0) (Eq. 16, 18),
-// and the collision of Eq. 21 is applied to mh: m - m_eq = mh - mh_eq because the
-// rest part cancels.  M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
+// stored as deviations from the exact post-collision rest state (rho = 1, u = 0):
+//     ft_i = f+_i - (r w_i + c_i),   c_i = e_ir w_i / 2,
+//     gh_i = g+_i - wT_i T0,
+// where r w_i + c_i = M^-1 (m_eq + S/2) at rest (S_3 = rho c_s^2 from a_r of Eq. 25).
+// Streaming maps that rest state onto the pre-collision rest state r w_i - c_i
+// (because r - e_ir + e_ir/2 = r - e_ir/2), so the pulled pre-collision deviation
+//     fv_i(x) = f_i(x) - (r w_i - c_i) = ft_i(x - e_i)
+// is a plain copy (Eq. 22), also through the specular image of the axis row.  The
+// moments of the deviations are mv = M fv = m - r (1, -2, 1, 0, ...) + (0, 0, 0, c_s^2/2,
+// -c_s^2/2, 0, ...).  Eq. 21 applied to mv, with the constant c_s^2 of S_3 (and -c_s^2
+// of S_4) removed from the source, gives exactly M ft+: the rest constants cancel.  All
+// handled values are small, so FP32 (and FP16/BF16 storage) keep their precision.
+// M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,10 +37,8 @@ struct Consts {
     R s_e, s_eps, s_j, s_q, s_nu;   // Eq. 23 with the rates of Sec. 4
     R tauT, wg_den;    // tau_T and 1 / (tau_T + 1/2)
     R gbeta, T0, az;   // buoyancy, reference temperature, external acceleration (z)
-    R nu;              // fluid viscosity nu = nu_e / J
-    R invKbar;         // 1 / (Da L^2)
-    R c_kappa;         // 1/K(phi) = c_kappa (1 - phi)^2 / phi^3 (porous_mode 2)
-    R F_eps;           // constant F_phi (ergun = 0)
+    R lin_coef;        // nu / K = lin_coef (mode 1) or lin_coef (1 - phi)^2 / phi^3 (mode 2)
+    R nl_coef;         // F_phi / sqrt(K), see porous()
     R T_hot, T_cold;
 };
 
@@ -44,6 +46,22 @@ template <typename R> __host__ __device__ constexpr R cs2() { return R(1) / R(3)
 
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+
+// Reciprocals.  rcp_fast: hardware approximation (a few ulp), used only where an
+// error of that size perturbs a parameter-like quantity (geometry, porous
+// coefficients, small corrections).  rcp_acc: one Newton step on top (error well
+// below one ulp, unbiased rounding), used wherever the result scales the conserved
+// momentum that the next step reads back (1/rho and the Eq. 28 denominators): a
+// biased factor there would act as a spurious force every step.
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_acc(float x) {
+    const float y = __fdividef(1.0f, x);
+    return fmaf(y, fmaf(-x, y, 1.0f), y);
+}
+__device__ __forceinline__ double rcp_acc(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
 
 // Node class (Fig. 1, Fig. 3): walls on the outermost nodes, corners on the side walls.
 __host__ __device__ __forceinline__ int node_class(int geometry, int nr, int nz, int kr, int kz) {
@@ -72,45 +90,57 @@ __device__ __forceinline__ void fluid_neighbour(int geometry, int nr, int nz, in
     }
 }
 
-// Eq. 8 per node: nu / K and F_phi / sqrt(K).
+// Eq. 8 per node, in closed form.  With d_p fixed from Da and the mean porosity,
+// 1/K(phi) = c_k (1 - phi)^2 / phi^3 and the Ergun F_phi / sqrt(K) = 1.75 sqrt(c_k / 150)
+// (1 - phi) / phi^3, so one reciprocal 1/phi^3 gives nu / K, F_phi / sqrt(K) and 1/phi.
+// porous_mode 0: no drag; 1: K = Da L^2 everywhere (F_phi from phi, or constant);
+// 2: K(phi) per node.  lin = nu / K, nl = F_phi / sqrt(K).
 template <typename R>
-__device__ __forceinline__ void porous(const Consts<R>& c, R phi, R& lin, R& nl) {
-    R invK;
-    if (c.porous_mode == 0) invK = R(0);
-    else if (c.porous_mode == 1) invK = c.invKbar;
-    else {
+__device__ __forceinline__ void porous(const Consts<R>& c, R phi, R& lin, R& nl, R& inv_phi) {
+    const R ip3 = rcp_fast(phi * phi * phi);
+    inv_phi = phi * phi * ip3;
+    if (c.porous_mode == 2) {
         const R om = R(1) - phi;
-        invK = c.c_kappa * om * om / (phi * phi * phi);
+        lin = c.lin_coef * om * om * ip3;
+        nl = c.ergun ? c.nl_coef * om * ip3 : c.nl_coef * om * sqrt_fast(ip3);
+    } else if (c.porous_mode == 1) {
+        lin = c.lin_coef;
+        nl = c.ergun ? c.nl_coef * sqrt_fast(ip3) : c.nl_coef;
+    } else {
+        lin = R(0);
+        nl = R(0);
     }
-    const R Fphi = c.ergun ? R(1.75) / dsqrt(R(150) * phi * phi * phi) : c.F_eps;
-    lin = c.nu * invK;
-    nl = Fphi * dsqrt(invK);
 }
 
-// Macroscopic fields of a non-wall node from its post-streaming deviations:
+// Macroscopic fields of a non-wall node from its pre-collision deviations fv, gh:
 // T (Eq. 38), rho (Eq. 26), G (Eq. 7), v (Eq. 29), l_j0, l_1 (Eq. 30), u (Eq. 28,
-// literally per component with |v| = sqrt(v_r^2 + v_z^2)).
+// literally per component with |v| = sqrt(v_r^2 + v_z^2)); lin, nl from porous().
 template <typename R>
-__device__ __forceinline__ void recover(const Consts<R>& c, R r, R inv_r, R phi, const R* fh, const R* gh,
-                                        R& m0, R& rho, R& ur, R& uz, R& dT) {
+__device__ __forceinline__ void recover(const Consts<R>& c, R r, R inv_r, R phi, R lin, R nl, const R* fh,
+                                        const R* gh, R& m0, R& rho, R& ur, R& uz, R& dT) {
     dT = gh[0] + gh[1] + gh[2] + gh[3] + gh[4];
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
     rho = R(1) + m0 * inv_r;
     const R jr = (fh[1] - fh[3]) + (fh[5] - fh[6]) + (fh[8] - fh[7]);
     const R jz = (fh[2] - fh[4]) + (fh[5] + fh[6]) - (fh[7] + fh[8]);
     const R Gz = c.gbeta * dT + c.az;
-    const R inv_rho = R(1) / rho;
-    const R vr = jr * inv_rho + R(0.5) * cs2<R>();
+    const R inv_rho = rcp_acc(rho);
+    // sum_i e_ir f_i = jr - c_s^2 / 2, so v_r = (jr - c_s^2/2) / rho + c_s^2 / 2 (Eq. 29)
+    const R vr = (jr + R(0.5) * cs2<R>() * m0 * inv_r) * inv_rho;
     const R vz = jz * inv_rho + R(0.5) * r * phi * Gz;
-    R lin, nl;
-    porous(c, phi, lin, nl);
     const R hd = R(0.25) * r * phi * lin;
     const R lr0 = R(0.5) * (r + c.cs2tau * inv_r) + hd;
     const R lz0 = R(0.5) * r + hd;
-    const R l1 = R(0.5) * r * phi * nl;
-    const R vm = dsqrt(vr * vr + vz * vz);
-    ur = vr / (lr0 + dsqrt(lr0 * lr0 + l1 * vm));
-    uz = vz / (lz0 + dsqrt(lz0 * lz0 + l1 * vm));
+    // Eq. 28: u_j = v_j / D_j, D_j = l_j0 + sqrt(l_j0^2 + x) = 2 l_j0 + x / D_j with
+    // x = l_1 |v|; the small Forchheimer part x / D_j is evaluated with fast operations.
+    R Dr = R(2) * lr0, Dz = R(2) * lz0;
+    if (nl != R(0)) {
+        const R x = R(0.5) * r * phi * nl * sqrt_fast(vr * vr + vz * vz);
+        Dr += x * rcp_fast(lr0 + sqrt_fast(lr0 * lr0 + x));
+        Dz += x * rcp_fast(lz0 + sqrt_fast(lz0 * lz0 + x));
+    }
+    ur = vr * rcp_acc(Dr);
+    uz = vz * rcp_acc(Dz);
 }
 
 // f = M^-1 m with M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
@@ -134,27 +164,27 @@ __device__ __forceinline__ void minv(const R* m, R* f) {
     f[8] = b58 + y3 - y5 - a8;
 }
 
-// Collision of one node (in place on fh, gh): forces (Eq. 6, 25), source (Eq. 24),
+// Collision of one node (in place: pre-collision deviations in, stored
+// post-collision deviations out): forces (Eq. 6, 25), source (Eq. 24),
 // MRT relaxation (Eq. 21) and f+ = M^-1 m+ (Eq. 22); D2Q5 update (Eq. 33, 35-37)
 // with omega_g,i = (1 + e_ir tau_T / r) / (tau_T + 1/2).  rho, u, T are given so
 // that wall nodes can impose u = 0 and their temperature; m0 = sum_i fh_i.
 template <typename R>
-__device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi, R* fh, R* gh, R m0, R rho,
-                                        R ur, R uz, R dT) {
-    R lin, nl;
-    porous(c, phi, lin, nl);
+__device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi, R lin, R nl, R inv_phi, R* fh,
+                                        R* gh, R m0, R rho, R ur, R uz, R dT) {
     const R T = c.T0 + dT;
     const R u2 = ur * ur + uz * uz;
-    const R um = dsqrt(u2);
+    const R um = sqrt_fast(u2);
     const R Gz = c.gbeta * dT + c.az;
     const R drag = lin + nl * um;
-    const R Ftr = -phi * drag * ur + cs2<R>() * (R(1) - c.two_taum * ur * inv_r) * inv_r;
+    const R Fr = -phi * drag * ur;
+    const R Ftr = Fr + cs2<R>() * (R(1) - c.two_taum * ur * inv_r) * inv_r;   // Eq. 25
     const R Ftz = -phi * drag * uz + phi * Gz;
-    const R inv_phi = R(1) / phi;
     const R rr = r * rho;
-    // Eq. 24
+    // Eq. 24; S_3 = r rho F~_r = c_s^2 + S3, the constant c_s^2 cancelling against
+    // the rest offsets of the stored deviations
     const R S1 = R(6) * rr * (ur * Ftr + uz * Ftz) * inv_phi;
-    const R S3 = rr * Ftr;
+    const R S3 = cs2<R>() * m0 * inv_r + rr * Fr - rho * cs2<R>() * c.two_taum * ur * inv_r;
     const R S5 = rr * Ftz;
     const R S7 = R(2) * rr * (ur * Ftr - uz * Ftz) * inv_phi;
     const R S8 = rr * (ur * Ftz + uz * Ftr) * inv_phi;
@@ -176,26 +206,35 @@ __device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi,
     const R e1 = R(-2) * m0 + q, e2 = m0 - q;
     const R e3 = rr * ur, e5 = rr * uz;
     const R e7 = rr * (ur * ur - uz * uz) * inv_phi, e8 = rr * ur * uz * inv_phi;
-    // Eq. 21 with Lambda = diag(1, s_e, s_eps, s_j, s_q, s_j, s_q, s_nu, s_nu)
-    const R p1 = m1 - c.s_e * (m1 - e1) + (R(1) - R(0.5) * c.s_e) * S1;
-    const R p2 = m2 - c.s_eps * (m2 - e2) - (R(1) - R(0.5) * c.s_eps) * S1;
-    const R p3 = m3 - c.s_j * (m3 - e3) + (R(1) - R(0.5) * c.s_j) * S3;
-    const R p4 = m4 - c.s_q * (m4 + e3) - (R(1) - R(0.5) * c.s_q) * S3;
-    const R p5 = m5 - c.s_j * (m5 - e5) + (R(1) - R(0.5) * c.s_j) * S5;
-    const R p6 = m6 - c.s_q * (m6 + e5) - (R(1) - R(0.5) * c.s_q) * S5;
-    const R p7 = m7 - c.s_nu * (m7 - e7) + (R(1) - R(0.5) * c.s_nu) * S7;
-    const R p8 = m8 - c.s_nu * (m8 - e8) + (R(1) - R(0.5) * c.s_nu) * S8;
-    // Eq. 22: f+ = M^-1 m+
-    const R mp[9] = {m0, p1, p2, p3, p4, p5, p6, p7, p8};
-    minv(mp, fh);
+    // Eq. 21 with Lambda = diag(1, s_e, s_eps, s_j, s_q, s_j, s_q, s_nu, s_nu), as the
+    // change dm = m+ - m (dm_0 = 0).  Eq. 22 is applied to the change only,
+    // f+ = f + M^-1 dm, so the inexact float reciprocals of M^-1 scale the small
+    // collision increment and not the conserved moments themselves (a factor like
+    // 6 fl(1/6) = 1 + 3e-8 on the momentum every step would act as a spurious force).
+    const R dm[9] = {R(0),
+                     -c.s_e * (m1 - e1) + (R(1) - R(0.5) * c.s_e) * S1,
+                     -c.s_eps * (m2 - e2) - (R(1) - R(0.5) * c.s_eps) * S1,
+                     -c.s_j * (m3 - e3) + (R(1) - R(0.5) * c.s_j) * S3,
+                     -c.s_q * (m4 + e3) - (R(1) - R(0.5) * c.s_q) * S3,
+                     -c.s_j * (m5 - e5) + (R(1) - R(0.5) * c.s_j) * S5,
+                     -c.s_q * (m6 + e5) - (R(1) - R(0.5) * c.s_q) * S5,
+                     -c.s_nu * (m7 - e7) + (R(1) - R(0.5) * c.s_nu) * S7,
+                     -c.s_nu * (m8 - e8) + (R(1) - R(0.5) * c.s_nu) * S8};
+    R df[9];
+    minv(dm, df);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fh[i] += df[i];
     // D2Q5 (Eq. 33, 35-37)
     const R k = c.tauT * inv_r;
     const R wd = c.wg_den;
     const R cu = -ur * inv_r;
     const R Tr = R(0.5) * T * ur, Tz = R(0.5) * T * uz;
-    const R g0e = R(0.6) * dT;                     // g_eq - wT T0
-    const R g1e = R(0.1) * dT + Tr, g3e = R(0.1) * dT - Tr;
-    const R g2e = R(0.1) * dT + Tz, g4e = R(0.1) * dT - Tz;
+    // g_eq - wT T0 (Eq. 35-36); the rest component is dT minus the other four so that
+    // sum_i g_eq,i = T holds to rounding (0.6f + 4 * 0.1f is not 1)
+    const R t1 = R(0.1) * dT;
+    const R g1e = t1 + Tr, g3e = t1 - Tr;
+    const R g2e = t1 + Tz, g4e = t1 - Tz;
+    const R g0e = dT - R(4) * t1;
     const R wT0 = R(0.6) * c.T0, wT1 = R(0.1) * c.T0;
     gh[0] = gh[0] - wd * (gh[0] - g0e) + cu * (g0e + wT0);
     gh[1] = gh[1] - (R(1) + k) * wd * (gh[1] - g1e) + cu * (g1e + wT1);
@@ -211,16 +250,15 @@ __host__ __device__ constexpr int mirror9(int i) { return i == 1 ? 3 : i == 3 ? 
 template <typename R> __host__ __device__ constexpr R w9(int i) { return i == 0 ? R(4) / R(9) : i < 5 ? R(1) / R(9) : R(1) / R(36); }
 
 // Wall node rebuild by non-equilibrium extrapolation (Sec. 4, ref. [47]) from the
-// interior neighbour's post-streaming deviations (fhf at radius rf):
+// interior neighbour's pre-collision deviations (fhf at radius rf; iphi = 1/phi_f):
 //   f_b = f_eq(r_b, rho_f, 0) + [f_f - f_eq(r_f, rho_f, u_f)]      (Eq. 32)
 // In deviations: fh_b,i = r_b w_i drho_f + fh_f,i - r_f w_i [drho_f + rho_f (3 eu
 // + 4.5 eu^2 / phi_f - 1.5 u^2 / phi_f)], drho_f = m0f / r_f.
 template <typename R>
-__device__ __forceinline__ void rebuild_flow(R rb, R rf, R phif, R m0f, R rhof, R urf, R uzf, const R* fhf,
+__device__ __forceinline__ void rebuild_flow(R rb, R rf, R iphi, R m0f, R rhof, R urf, R uzf, const R* fhf,
                                              R* fh) {
-    const R drho = m0f / rf;
+    const R drho = m0f * rcp_acc(rf);
     const R u2 = urf * urf + uzf * uzf;
-    const R iphi = R(1) / phif;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const R eu = R(ex9(i)) * urf + R(ez9(i)) * uzf;
@@ -235,11 +273,13 @@ template <typename R>
 __device__ __forceinline__ void rebuild_thermal(R T0, R dTf, R dTb, R urf, R uzf, const R* ghf, R* gh) {
     const R Tf = T0 + dTf;
     const R tr = R(0.5) * Tf * urf, tz = R(0.5) * Tf * uzf;
-    gh[0] = R(0.6) * dTb + ghf[0] - R(0.6) * dTf;
-    gh[1] = R(0.1) * dTb + ghf[1] - (R(0.1) * dTf + tr);
-    gh[2] = R(0.1) * dTb + ghf[2] - (R(0.1) * dTf + tz);
-    gh[3] = R(0.1) * dTb + ghf[3] - (R(0.1) * dTf - tr);
-    gh[4] = R(0.1) * dTb + ghf[4] - (R(0.1) * dTf - tz);
+    const R d = dTb - dTf;
+    const R t1 = R(0.1) * d;
+    gh[0] = ghf[0] + (d - R(4) * t1);
+    gh[1] = ghf[1] + (t1 - tr);
+    gh[2] = ghf[2] + (t1 - tz);
+    gh[3] = ghf[3] + (t1 + tr);
+    gh[4] = ghf[4] + (t1 + tz);
 }
 
 }  // namespace lbm

@@ -60,8 +60,8 @@ def test_derivation_matches_oracle(lbm, oracle, kw):
     for k_lib, k_ref in (("L", "L"), ("H", "H"), ("r0", "r0"), ("tau_nu", "tau"), ("tau_T", "tauT"),
                          ("nu_e", "nu_e"), ("nu", "nu"), ("gbeta", "gbeta"), ("T0", "T0"), ("Kbar", "Kbar")):
         assert np.isclose(getattr(info, k_lib), ref[k_ref], rtol=1e-14, atol=0), k_lib
-    es = 4 if p.storage == 0 else 2
-    assert info.bytes_per_step == p.nr * p.nz * (28 * es + es)
+    ef = 4 if p.storage == 0 else 2           # flow populations; temperature populations stay FP32
+    assert info.bytes_per_step == p.nr * p.nz * (2 * (9 * ef + 5 * 4) + ef)
 
 
 @pytest.mark.parametrize("bad", [
