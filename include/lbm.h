@@ -155,9 +155,13 @@ int lbm_nusselt(lbm_handle *h, double *nu_inner, double *nu_outer);
  * Returns LBM_ERR_DIVERGED if a field holds NaN or Inf.  Synchronises. */
 int lbm_residual(lbm_handle *h, double *res, double *mass);
 
-/* Step until the residual is <= tol, checking every check_every steps, or until
- * max_steps.  *steps_done and *res (either may be NULL) receive the steps taken
- * and the last residual.  LBM_ERR_DIVERGED on NaN/Inf. */
+/* Step until steady or max_steps.  Every check_every steps the mean change per step
+ * over the interval, max(|u^n - u^(n-k)|_2 / |u^n|_2, |T^n - T^(n-k)|_2 / |T^n|_2) / k
+ * over non-wall nodes (FP64), is compared with tol; it averages out the rounding
+ * jitter of an FP32 or 16-bit state, which keeps the consecutive-step residual of
+ * lbm_residual near 1e-8 - 1e-7 however long the run.  *steps_done and *res (either
+ * may be NULL) receive the steps taken and the last value.  LBM_ERR_DIVERGED on
+ * NaN/Inf.  Synchronises at every check. */
 int lbm_run(lbm_handle *h, int64_t max_steps, int64_t check_every, double tol, int64_t *steps_done,
             double *res);
 
