@@ -186,6 +186,29 @@ int lbm_set_timing(lbm_handle *h, int enable);
 int lbm_kernel_times(lbm_handle *h, double *bulk_ms, int64_t *bulk_launches, double *wall_ms,
                      int64_t *wall_launches);
 
+/* Allocation-free residual (the paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory when they need the check, e.g. a host
+ * framework whose own allocator owns all device memory, or a monitoring path that
+ * must not trigger the device-wide synchronisation cudaMalloc / cudaFree can cause).
+ * Same result as lbm_residual, computed from two field snapshots the caller supplies:
+ *   cur:  device floats, 4 planes of nr*nz at stride field_stride: rho, u_r, u_z, T
+ *         of state n (the layout lbm_moments writes when given plane pointers);
+ *   prev: the same 4 planes of state n - 1 (its rho plane is not read);
+ *   geometry, nr, nz: as in lbm_params; r0 = r(kr = 0) (lbm_info.r0);
+ *   *res, *mass: host doubles receiving the residual and sum of r * rho (FP64).
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the reduction's
+ * partial sums live in a file-scope static device array of 1025 x 6 doubles (49 KB),
+ * held by every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls share the
+ * array and each overwrites it: calls that overlap on the GPU (other streams, other
+ * threads) race.  Limits: 3 <= nr, nz <= 65535 and nr*nz < 2^31 (LBM_ERR_INVALID
+ * beyond), current device index < 64.  Work runs on `stream` (NULL = legacy default)
+ * and the call synchronises it.  LBM_ERR_DIVERGED if cur holds NaN or Inf. */
+int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t nz, double r0, const float *cur,
+                               const float *prev, int64_t field_stride, double *res, double *mass,
+                               void *stream);
+
 /* Free everything h owns.  h may be NULL. */
 int lbm_destroy(lbm_handle *h);
 

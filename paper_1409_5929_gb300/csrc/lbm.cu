@@ -27,6 +27,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1002,3 +1003,58 @@ int lbm_kernel_times(lbm_handle* h, double* bulk_ms, int64_t* bulk_launches, dou
 const char* lbm_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+// ----------------------------------------------- allocation-free residual --
+// Scratch for lbm_field_residual_noalloc: LBM_NOALLOC_ROWS partial rows of RES_NV
+// doubles (one per reduction block) and one result row, 49 KB in total.  Every GPU
+// that loads this library holds the array until the process exits.  Host code only
+// ever passes the address obtained from cudaGetSymbolAddress; the symbol itself is a
+// host-side stand-in there.
+constexpr int LBM_NOALLOC_ROWS = 1024;
+static __device__ __align__(256) double g_noalloc_scratch[(LBM_NOALLOC_ROWS + 1) * RES_NV];
+
+constexpr int LBM_NOALLOC_MAX_DEVICES = 64;
+static double* g_noalloc_ptr[LBM_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+extern "C" int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t nz, double r0, const float* cur,
+                                          const float* prev, int64_t field_stride, double* res, double* mass,
+                                          void* stream) {
+    if (!cur || !prev || !res || !mass) return fail(LBM_ERR_INVALID, "NULL argument");
+    if (geometry < 0 || geometry > 2) return fail(LBM_ERR_INVALID, "unknown geometry %d", geometry);
+    if (nr < 3 || nz < 3 || nr > 65535 || nz > 65535 || (int64_t)nr * nz >= ((int64_t)1 << 31))
+        return fail(LBM_ERR_INVALID, "grid %d x %d outside 3..65535 per side with nr*nz < 2^31", nr, nz);
+    const int64_t N = (int64_t)nr * nz;
+    if (field_stride < N) return fail(LBM_ERR_INVALID, "field_stride %lld < nr*nz", (long long)field_stride);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= LBM_NOALLOC_MAX_DEVICES)
+        return fail(LBM_ERR_INVALID, "device %d beyond the %d supported", dev, LBM_NOALLOC_MAX_DEVICES);
+    double* scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = (double*)p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)std::min<int64_t>(LBM_NOALLOC_ROWS, (N + 255) / 256);
+    double* result = scratch + LBM_NOALLOC_ROWS * RES_NV;
+    // every partial row the final sum reads is written by this call: nothing to clear
+    k_resid_partial<<<blocks, 256, 0, s>>>(geometry, nr, nz, r0, cur, prev, field_stride, scratch);
+    CK(cudaGetLastError());
+    k_sum_rows<<<1, 256, 0, s>>>(scratch, blocks, result);
+    CK(cudaGetLastError());
+    double sum[RES_NV];
+    CK(cudaMemcpyAsync(sum, result, sizeof(sum), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (sum[5] > 0) return fail(LBM_ERR_DIVERGED, "%.0f nodes hold NaN or Inf", sum[5]);
+    const double ru = sum[1] > 0 ? std::sqrt(sum[0] / sum[1]) : (sum[0] > 0 ? INFINITY : 0.0);
+    const double rt = sum[3] > 0 ? std::sqrt(sum[2] / sum[3]) : (sum[2] > 0 ? INFINITY : 0.0);
+    *res = ru > rt ? ru : rt;
+    *mass = sum[4];
+    return LBM_OK;
+}

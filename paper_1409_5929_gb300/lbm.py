@@ -71,6 +71,8 @@ _SIGS = {
     "lbm_set_timing": (C.c_int, [_vp, C.c_int]),
     "lbm_kernel_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]),
+    "lbm_field_residual_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, _vp, _vp, C.c_int64,
+                                             C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "lbm_destroy": (C.c_int, [_vp]),
     "lbm_last_error": (C.c_char_p, []),
 }
@@ -200,6 +202,15 @@ def lbm_kernel_times(h):
     a, b, c, d = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
     _check(load().lbm_kernel_times(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
     return a.value, b.value, c.value, d.value
+
+
+def lbm_field_residual_noalloc(geometry: int, nr: int, nz: int, r0: float, cur, prev, field_stride: int,
+                               stream=None):
+    """Residual and mass from device field snapshots without any device allocation."""
+    a, b = C.c_double(), C.c_double()
+    _check(load().lbm_field_residual_noalloc(int(geometry), int(nr), int(nz), float(r0), _ptr(cur), _ptr(prev),
+                                             int(field_stride), C.byref(a), C.byref(b), stream))
+    return a.value, b.value
 
 
 def lbm_destroy(h):
