@@ -209,6 +209,45 @@ int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t nz, double 
                                const float *prev, int64_t field_stride, double *res, double *mass,
                                void *stream);
 
+/* ------------------------------------------------------------------ batches --
+ * Many independent problems of uneven size advanced by the same kernel launches.
+ * Every step of every active instance is the step of lbm_step (same kernels, same
+ * arithmetic); the batch only shares launches, a CUDA graph and the checks.  All
+ * instances must use the same storage type.  Instance indices are 0 .. n-1.  The
+ * batch owns one stream (lbm_batch_set_stream replaces it; the legacy default stream
+ * cannot be captured and is rejected).  Not thread-safe. */
+typedef struct lbm_batch lbm_batch;
+
+/* Allocate and cold-start n instances with parameters p[0..n-1] (validated as in
+ * lbm_create); each gets uniform porosity eps_mean. */
+int lbm_batch_create(const lbm_params *p, int32_t n, lbm_batch **out);
+int lbm_batch_set_stream(lbm_batch *b, void *stream);
+/* Porosity field of instance i (nr_i * nz_i values in (0, 1], copied). */
+int lbm_batch_set_porosity(lbm_batch *b, int32_t i, const float *phi, int on_device);
+/* (Re)initialise instance i as lbm_init_fields does; a stopped instance becomes
+ * active again. */
+int lbm_batch_init_fields(lbm_batch *b, int32_t i, const float *ur, const float *uz, const float *T, int on_device);
+/* nsteps steps of every active instance (two launches per step for the whole batch). */
+int lbm_batch_step(lbm_batch *b, int64_t nsteps);
+/* Step until every instance is steady (criterion of lbm_run, per instance, checked
+ * every check_every steps; check_every must be even) or max_steps.  The steps of one
+ * check interval are captured once in a CUDA graph and replayed; instances that meet
+ * tol stop stepping.  steps[n], res[n] (either may be NULL) receive the steps each
+ * instance took and its last criterion value.  LBM_ERR_DIVERGED names an instance that
+ * produced NaN or Inf (it is stopped; the others have run to that check). */
+int lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t check_every, double tol, int64_t *steps, double *res);
+/* Eq. 42 of every instance: nu_inner[n], nu_outer[n] (host). */
+int lbm_batch_nusselt(lbm_batch *b, double *nu_inner, double *nu_outer);
+/* Fields of instance i, as lbm_moments. */
+int lbm_batch_moments(lbm_batch *b, int32_t i, float *rho, float *ur, float *uz, float *T, int on_device);
+/* Autotuner: times `steps` steps for each bulk block shape (columns x rows per block:
+ * 64x1, 128x1, 256x1, 64x2, 128x2, 64x4, 32x8) and keeps the fastest; returns it and
+ * its time per step.  The state advances by the steps the tuning ran. */
+int lbm_batch_tune(lbm_batch *b, int32_t steps, int32_t *cols, int32_t *rows, float *ms_per_step);
+/* Derived constants of instance i; steps = steps taken by the batch. */
+int lbm_batch_get_info(lbm_batch *b, int32_t i, lbm_info *out);
+int lbm_batch_destroy(lbm_batch *b);
+
 /* Free everything h owns.  h may be NULL. */
 int lbm_destroy(lbm_handle *h);
 

@@ -1058,3 +1058,650 @@ extern "C" int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t 
     *mass = sum[4];
     return LBM_OK;
 }
+
+// ======================================================================= batch ==
+// Many independent problems of uneven size advanced by the same launches.
+//
+// Layout: one pooled device allocation holds, per instance, state A, state B and the
+// porosity plane (each instance's own nr*nz, plane stride padded to 64 elements), and
+// a second pool holds two field snapshots (4 planes each) per instance.  A device
+// table of InstDesc carries each instance's lattice constants and pool offsets.
+// A step is two launches covering every active instance: k_batch_bulk over a
+// flattened list of tiles (instance, first row, first column; block shape chosen by
+// lbm_batch_tune) and k_batch_wall over the concatenated wall-node lists.  lbm_batch_run
+// captures check_every steps (an even number, so every instance's A/B parity is the
+// same at each check) in a CUDA graph and replays it; instances that reach the
+// steady criterion leave the tile lists at the next check.
+struct InstDesc {
+    Consts<float> c;
+    int64_t off_state[2];   // byte offsets of state buffers A and B in the state pool
+    int64_t off_phi;        // byte offset of the porosity plane
+    int64_t off_mac;        // float offset of the two field snapshots in the snapshot pool
+    int64_t plane;          // elements per plane
+    double r0, H, dTw;
+};
+
+template <int STO>
+__device__ __forceinline__ Buf<STO> inst_buf(const InstDesc& d, char* pool, int which) {
+    Buf<STO> b;
+    b.f = (typename St<STO>::TF*)(pool + d.off_state[which]);
+    b.g = (typename St<STO>::TG*)(pool + d.off_state[which] + 9 * d.plane * (int64_t)sizeof(typename St<STO>::TF));
+    return b;
+}
+
+// Tile = (instance, first row, first column); block = (bz, rows).
+template <int STO>
+__global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__ desc, char* __restrict__ pool,
+                                                    int parity, const int4* __restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const InstDesc& d = desc[t.x];
+    const Consts<float> c = d.c;
+    const int kz = t.z + threadIdx.x;
+    const int kr = t.y + threadIdx.y;
+    if (kz >= c.nz || kr >= c.nr) return;
+    if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) return;
+    const Buf<STO> A = inst_buf<STO>(d, pool, parity), B = inst_buf<STO>(d, pool, parity ^ 1);
+    const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
+    const int plane = (int)d.plane;
+    float fh[9], gh[5];
+    pull<STO, float, int>(c, A, plane, kr, kz, fh, gh);
+    const int n = kr * c.nz + kz;
+    const float r = c.r0 + float(kr), inv_r = rcp_acc(r);
+    const float ph = ldv(phi + n);
+    float m0, rho, ur, uz, dT, lin, nl, iph;
+    porous(c, ph, lin, nl, iph);
+    recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+    collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
+    store<STO, float, int>(B, plane, n, fh, gh);
+}
+
+// Wall nodes of all active instances: prefix[k] = first wall thread of active instance k.
+__device__ __forceinline__ int find_slot(const int* __restrict__ prefix, int n, int t) {
+    int lo = 0, hi = n;   // prefix[lo] <= t < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int STO>
+__global__ void k_batch_wall(const InstDesc* __restrict__ desc, char* __restrict__ pool, int parity,
+                             const int* __restrict__ active, const int* __restrict__ prefix, int nactive) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= prefix[nactive]) return;
+    const int k = find_slot(prefix, nactive, t);
+    const InstDesc& d = desc[active[k]];
+    const Consts<float> c = d.c;
+    int kr, kz;
+    wall_node(c.geometry, c.nr, c.nz, t - prefix[k], kr, kz);
+    const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
+    const Buf<STO> A = inst_buf<STO>(d, pool, parity), B = inst_buf<STO>(d, pool, parity ^ 1);
+    const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
+    float fh[9], gh[5], m0, rho, dTb;
+    wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dTb);
+    const int64_t n = (int64_t)kr * c.nz + kz;
+    const float r = c.r0 + float(kr), ph = ldv(phi + n);
+    float lin, nl, iph;
+    porous(c, ph, lin, nl, iph);
+    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, m0, rho, 0.0f, 0.0f, dTb);
+    store<STO>(B, d.plane, n, fh, gh);
+}
+
+// Field snapshot `slot` (0 or 1) of every instance the tiles cover, all nodes.
+template <int STO>
+__global__ void __launch_bounds__(256) k_batch_moments(const InstDesc* __restrict__ desc, char* __restrict__ pool,
+                                                       float* __restrict__ macpool, int parity, int slot,
+                                                       const int4* __restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const InstDesc& d = desc[t.x];
+    const Consts<float> c = d.c;
+    const int kz = t.z + threadIdx.x;
+    const int kr = t.y + threadIdx.y;
+    if (kz >= c.nz || kr >= c.nr) return;
+    const Buf<STO> A = inst_buf<STO>(d, pool, parity);
+    const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
+    const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
+    const int64_t n = (int64_t)kr * c.nz + kz;
+    float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT;
+    if (is_wall(cls)) {
+        wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dT);
+    } else {
+        pull<STO>(c, A, d.plane, kr, kz, fh, gh);
+        const float r = c.r0 + float(kr), ph = ldv(phi + n);
+        float lin, nl, iph;
+        porous(c, ph, lin, nl, iph);
+        recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+    }
+    float* m = macpool + d.off_mac + (int64_t)slot * 4 * d.plane;
+    m[n] = rho;
+    m[d.plane + n] = ur;
+    m[2 * d.plane + n] = uz;
+    m[3 * d.plane + n] = c.T0 + dT;
+}
+
+// Per-instance residual sums between the two snapshots (cur = slot `cur`): grid
+// (RB, nactive); partial rows [k][block][RES_NV].
+constexpr int BATCH_RB = 16;
+__global__ void k_batch_resid(const InstDesc* __restrict__ desc, const float* __restrict__ macpool, int cur,
+                              const int* __restrict__ active, double* __restrict__ partials) {
+    const int k = blockIdx.y;
+    const InstDesc& d = desc[active[k]];
+    const int nr = d.c.nr, nz = d.c.nz, geometry = d.c.geometry;
+    const float* C = macpool + d.off_mac + (int64_t)cur * 4 * d.plane;
+    const float* P = macpool + d.off_mac + (int64_t)(cur ^ 1) * 4 * d.plane;
+    const int64_t fs = d.plane;
+    double v[RES_NV] = {0, 0, 0, 0, 0, 0};
+    const int64_t N = (int64_t)nr * nz;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const int kr = (int)(n / nz), kz = (int)(n - (int64_t)kr * nz);
+        const float rho = C[n], ur = C[fs + n], uz = C[2 * fs + n], T = C[3 * fs + n];
+        if (!isfinite(rho) || !isfinite(ur) || !isfinite(uz) || !isfinite(T)) v[5] += 1;
+        v[4] += (d.r0 + kr) * (double)rho;
+        if (is_wall(node_class(geometry, nr, nz, kr, kz))) continue;
+        const double a = (double)ur - P[fs + n], b = (double)uz - P[2 * fs + n], e = (double)T - P[3 * fs + n];
+        v[0] += a * a + b * b;
+        v[1] += (double)ur * ur + (double)uz * uz;
+        v[2] += e * e;
+        v[3] += (double)T * T;
+    }
+    double out[RES_NV];
+    block_sum<RES_NV>(v, out);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < RES_NV; ++j) partials[((int64_t)k * gridDim.x + blockIdx.x) * RES_NV + j] = out[j];
+}
+
+__global__ void k_batch_resid_final(const double* __restrict__ partials, int rb, double* __restrict__ result) {
+    const int k = blockIdx.x;
+    double v[RES_NV] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < rb; b += blockDim.x)
+        for (int j = 0; j < RES_NV; ++j) v[j] += partials[((int64_t)k * rb + b) * RES_NV + j];
+    double out[RES_NV];
+    block_sum<RES_NV>(v, out);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < RES_NV; ++j) result[(int64_t)k * RES_NV + j] = out[j];
+}
+
+// Eq. 42 for every instance (one block each).
+template <int STO>
+__global__ void __launch_bounds__(256) k_batch_nusselt(const InstDesc* __restrict__ desc, char* __restrict__ pool,
+                                                       const int* __restrict__ parity, double* __restrict__ result) {
+    const InstDesc& d = desc[blockIdx.x];
+    const Consts<float> c = d.c;
+    const Buf<STO> A = inst_buf<STO>(d, pool, parity[blockIdx.x]);
+    double v[2] = {0, 0};
+    for (int kz = threadIdx.x; kz < c.nz; kz += blockDim.x) {
+        const double wz = (kz == 0 || kz == c.nz - 1) ? 0.5 : 1.0;
+        const double t0 = node_T<STO>(c, A, d.plane, 0, kz), t1 = node_T<STO>(c, A, d.plane, 1, kz);
+        const double t2 = node_T<STO>(c, A, d.plane, 2, kz);
+        const double u0 = node_T<STO>(c, A, d.plane, c.nr - 1, kz), u1 = node_T<STO>(c, A, d.plane, c.nr - 2, kz);
+        const double u2 = node_T<STO>(c, A, d.plane, c.nr - 3, kz);
+        v[0] += wz * (-3 * t0 + 4 * t1 - t2) * 0.5;
+        v[1] += wz * (3 * u0 - 4 * u1 + u2) * 0.5;
+    }
+    double out[2];
+    block_sum<2>(v, out);
+    if (threadIdx.x == 0) {
+        const double ro = d.r0 + (c.nr - 1);
+        result[2 * blockIdx.x] = -d.r0 * out[0] / (d.H * d.dTw);
+        result[2 * blockIdx.x + 1] = -ro * out[1] / (d.H * d.dTw);
+    }
+}
+
+struct lbm_batch {
+    int n = 0;
+    int storage = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<lbm_params> p;
+    std::vector<lbm_info> info;
+    std::vector<Consts<double>> cd;
+    std::vector<InstDesc> desc;       // host copy
+    InstDesc* d_desc = nullptr;
+    char* pool = nullptr;
+    float* macpool = nullptr;
+    float* fstage = nullptr;          // largest instance: 3 planes (porosity or warm-start upload)
+    int64_t max_plane = 0;
+    int parity = 0;
+    int64_t steps = 0;
+    std::vector<char> active;         // 1 = still stepping
+    // tiles and wall lists of the active set
+    int bz = 128, rows = 1;           // bulk block shape
+    int4* d_tiles = nullptr;          // active instances, all rows
+    int ntiles = 0;
+    int* d_active = nullptr;
+    int* d_prefix = nullptr;
+    int nactive = 0;
+    int nwall = 0;
+    size_t cap_tiles = 0;
+    double* partials = nullptr;
+    double* result = nullptr;
+    std::vector<int> iparity;         // buffer holding the state of an instance that stopped
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_steps = 0;
+    int graph_parity = 0;             // batch parity the graph was captured at
+    bool graph_dirty = true;
+    int cur_parity(int i) const { return active[i] ? parity : iparity[i]; }
+};
+
+static void batch_free_graph(lbm_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_dirty = true;
+}
+
+// Rebuild the tile list, the active list and the wall prefix for the current active
+// set and block shape.
+static int batch_rebuild(lbm_batch* b) {
+    std::vector<int4> tiles;
+    std::vector<int> act, prefix(1, 0);
+    for (int i = 0; i < b->n; ++i) {
+        if (!b->active[i]) continue;
+        act.push_back(i);
+        prefix.push_back(prefix.back() + wall_count(b->p[i].geometry, b->p[i].nr, b->p[i].nz));
+        for (int kr = 0; kr < b->p[i].nr; kr += b->rows)
+            for (int z0 = 0; z0 < b->p[i].nz; z0 += b->bz) tiles.push_back(make_int4(i, kr, z0, 0));
+    }
+    b->ntiles = (int)tiles.size();
+    b->nactive = (int)act.size();
+    b->nwall = prefix.back();
+    if ((size_t)b->ntiles > b->cap_tiles) {
+        cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        CK(cudaMalloc((void**)&b->d_tiles, tiles.size() * sizeof(int4)));
+        b->cap_tiles = tiles.size();
+    }
+    if (b->ntiles)
+        CK(cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+    if (b->nactive) {
+        CK(cudaMemcpyAsync(b->d_active, act.data(), act.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    }
+    CK(cudaMemcpyAsync(b->d_prefix, prefix.data(), prefix.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    batch_free_graph(b);
+    return LBM_OK;
+}
+
+template <int STO> static Buf<STO> batch_buf(const lbm_batch* b, int i, int which) {
+    const InstDesc& d = b->desc[i];
+    Buf<STO> r;
+    r.f = (typename St<STO>::TF*)(b->pool + d.off_state[which]);
+    r.g = (typename St<STO>::TG*)(b->pool + d.off_state[which] + 9 * d.plane * (int64_t)sizeof(typename St<STO>::TF));
+    return r;
+}
+
+static int batch_launch_step(lbm_batch* b) {
+    if (!b->nactive) return LBM_OK;
+    const dim3 blk(b->bz, b->rows);
+    DISPATCH_STO(b->storage, k_batch_bulk<S_><<<b->ntiles, blk, 0, b->stream>>>(b->d_desc, b->pool, b->parity,
+                                                                                 b->d_tiles));
+    CK(cudaGetLastError());
+    DISPATCH_STO(b->storage, k_batch_wall<S_><<<(b->nwall + 127) / 128, 128, 0, b->stream>>>(
+                                 b->d_desc, b->pool, b->parity, b->d_active, b->d_prefix, b->nactive));
+    CK(cudaGetLastError());
+    b->parity ^= 1;
+    return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free_graph(b);
+    cudaFree(b->d_desc);
+    cudaFree(b->pool);
+    cudaFree(b->macpool);
+    cudaFree(b->fstage);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_active);
+    cudaFree(b->d_prefix);
+    cudaFree(b->partials);
+    cudaFree(b->result);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LBM_OK;
+}
+
+int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
+    if (!p || !out || n < 1) return fail(LBM_ERR_INVALID, "need params[n], n >= 1 and an output pointer");
+    *out = nullptr;
+    lbm_batch* b = new lbm_batch();
+    b->n = n;
+    b->storage = p[0].storage;
+    b->p.assign(p, p + n);
+    b->info.resize(n);
+    b->cd.resize(n);
+    b->desc.resize(n);
+    int64_t state_off = 0, mac_off = 0;
+    for (int i = 0; i < n; ++i) {
+        int rc = derive(&p[i], &b->info[i], &b->cd[i]);
+        if (rc) { delete b; return fail(rc, "instance %d: %s", i, g_err.c_str()); }
+        if (p[i].storage != b->storage) { delete b; return fail(LBM_ERR_INVALID, "instance %d: storage differs", i); }
+        const int64_t N = (int64_t)p[i].nr * p[i].nz, plane = (N + 63) / 64 * 64;
+        if (14 * plane >= ((int64_t)1 << 31)) { delete b; return fail(LBM_ERR_INVALID, "instance %d too large", i); }
+        InstDesc& d = b->desc[i];
+        d.c = to_float(b->cd[i]);
+        d.plane = plane;
+        d.off_state[0] = state_off;
+        state_off += (int64_t)state_bytes(b->storage, plane);
+        d.off_state[1] = state_off;
+        state_off += (int64_t)state_bytes(b->storage, plane);
+        d.off_phi = state_off;
+        state_off += (plane * (int64_t)phi_size(b->storage) + 255) / 256 * 256;
+        d.off_mac = mac_off;
+        mac_off += 8 * plane;
+        d.r0 = b->info[i].r0;
+        d.H = b->info[i].H;
+        d.dTw = p[i].T_hot - p[i].T_cold;
+        b->max_plane = std::max(b->max_plane, plane);
+    }
+    b->active.assign(n, 1);
+    b->iparity.assign(n, 0);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = e == cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->pool, state_off);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->macpool, mac_off * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, n * sizeof(InstDesc));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_active, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_prefix, (n + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->partials, (size_t)n * BATCH_RB * RES_NV * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->result, (size_t)n * RES_NV * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice,
+                                              b->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        lbm_batch_destroy(b);
+        return fail(e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "batch allocation: %s",
+                    cudaGetErrorString(e));
+    }
+    // uniform porosity and the cold start of every instance
+    for (int i = 0; i < n; ++i) {
+        const InstDesc& d = b->desc[i];
+        const int64_t N = (int64_t)p[i].nr * p[i].nz;
+        const dim3 g((unsigned)((p[i].nz + 127) / 128), (unsigned)p[i].nr);
+        DISPATCH_STO(b->storage, {
+            k_phi_fill<S_><<<(unsigned)((N + 255) / 256), 256, 0, b->stream>>>((PP<S_>*)(b->pool + d.off_phi), N,
+                                                                                (float)p[i].eps_mean);
+            k_init<S_><<<g, 128, 0, b->stream>>>(b->cd[i], batch_buf<S_>(b, i, 0), (const PP<S_>*)(b->pool + d.off_phi),
+                                                 d.plane, nullptr, nullptr, nullptr, p[i].init_noise, p[i].seed);
+        });
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return fail(LBM_ERR_CUDA, "batch initialisation: %s", cudaGetErrorString(e));
+    }
+    int rc = batch_rebuild(b);
+    if (rc) { lbm_batch_destroy(b); return rc; }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_stream(lbm_batch* b, void* stream) {
+    if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+    if (!stream) return fail(LBM_ERR_INVALID, "a batch needs a created stream (graph capture)");
+    CK(cudaSetDevice(b->device));
+    CK(cudaStreamSynchronize(b->stream));
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    b->own_stream = false;
+    b->stream = (cudaStream_t)stream;
+    batch_free_graph(b);
+    return LBM_OK;
+}
+
+static int batch_upload(lbm_batch* b, const float* src, int64_t N, int slot, const float** dev) {
+    if (!b->fstage) CK(cudaMalloc((void**)&b->fstage, 3 * b->max_plane * sizeof(float)));
+    CK(cudaMemcpyAsync(b->fstage + slot * b->max_plane, src, N * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+    *dev = b->fstage + slot * b->max_plane;
+    return LBM_OK;
+}
+
+int lbm_batch_set_porosity(lbm_batch* b, int32_t i, const float* phi, int on_device) {
+    if (!b || !phi || i < 0 || i >= b->n) return fail(LBM_ERR_INVALID, "bad batch, instance or pointer");
+    CK(cudaSetDevice(b->device));
+    const int64_t N = (int64_t)b->p[i].nr * b->p[i].nz;
+    const float* src = phi;
+    int rc;
+    if (!on_device && (rc = batch_upload(b, phi, N, 0, &src))) return rc;
+    unsigned int* bad = (unsigned int*)b->result;   // scratch word
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned int), b->stream));
+    DISPATCH_STO(b->storage, k_phi<S_><<<(unsigned)((N + 255) / 256), 256, 0, b->stream>>>(
+                                 src, (PP<S_>*)(b->pool + b->desc[i].off_phi), N, bad));
+    CK(cudaGetLastError());
+    unsigned int nb = 0;
+    CK(cudaMemcpyAsync(&nb, bad, sizeof(nb), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (nb) return fail(LBM_ERR_INVALID, "instance %d: %u porosity values outside (0, 1]", i, nb);
+    return LBM_OK;
+}
+
+int lbm_batch_init_fields(lbm_batch* b, int32_t i, const float* ur, const float* uz, const float* T, int on_device) {
+    if (!b || i < 0 || i >= b->n) return fail(LBM_ERR_INVALID, "bad batch or instance");
+    if ((ur == nullptr) != (uz == nullptr)) return fail(LBM_ERR_INVALID, "give both u_r and u_z or neither");
+    CK(cudaSetDevice(b->device));
+    const int64_t N = (int64_t)b->p[i].nr * b->p[i].nz;
+    const float *dur = ur, *duz = uz, *dT = T;
+    int rc;
+    if (!on_device) {
+        if (ur && ((rc = batch_upload(b, ur, N, 0, &dur)) || (rc = batch_upload(b, uz, N, 1, &duz)))) return rc;
+        if (T && (rc = batch_upload(b, T, N, 2, &dT))) return rc;
+    }
+    const InstDesc& d = b->desc[i];
+    const dim3 g((unsigned)((b->p[i].nz + 127) / 128), (unsigned)b->p[i].nr);
+    // the instance's current buffer is the batch parity
+    DISPATCH_STO(b->storage, k_init<S_><<<g, 128, 0, b->stream>>>(b->cd[i], batch_buf<S_>(b, i, b->parity),
+                                                                   (const PP<S_>*)(b->pool + d.off_phi), d.plane, dur,
+                                                                   duz, dT, b->p[i].init_noise, b->p[i].seed));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(b->stream));
+    if (!b->active[i]) {
+        b->active[i] = 1;
+        return batch_rebuild(b);
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return fail(LBM_ERR_INVALID, "bad batch or nsteps");
+    CK(cudaSetDevice(b->device));
+    for (int64_t s = 0; s < nsteps; ++s) {
+        int rc = batch_launch_step(b);
+        if (rc) return rc;
+    }
+    b->steps += nsteps;
+    return LBM_OK;
+}
+
+// Snapshot `slot` of every active instance.
+static int batch_snapshot(lbm_batch* b, int slot) {
+    // moments use all rows of the active instances: the bulk tiles cover them
+    const dim3 blk(b->bz, b->rows);
+    DISPATCH_STO(b->storage, k_batch_moments<S_><<<b->ntiles, blk, 0, b->stream>>>(b->d_desc, b->pool, b->macpool,
+                                                                                    b->parity, slot, b->d_tiles));
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_batch_run(lbm_batch* b, int64_t max_steps, int64_t check_every, double tol, int64_t* steps_out,
+                  double* res_out) {
+    if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+    if (max_steps < 0 || check_every < 2 || (check_every & 1))
+        return fail(LBM_ERR_INVALID, "max_steps >= 0 and an even check_every >= 2 required");
+    CK(cudaSetDevice(b->device));
+    std::vector<int64_t> done(b->n, 0);
+    std::vector<double> res(b->n, INFINITY);
+    int slot = 0;
+    int rc = batch_snapshot(b, slot ^ 1);
+    if (rc) return rc;
+    int64_t total = 0;
+    while (total < max_steps && b->nactive > 0) {
+        const int64_t k = std::min(check_every, max_steps - total);
+        if (k == check_every) {
+            if (b->graph_dirty || b->graph_steps != k || b->graph_parity != b->parity) {
+                batch_free_graph(b);
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                const int p0 = b->parity;
+                for (int64_t s = 0; s < k; ++s) {
+                    rc = batch_launch_step(b);
+                    if (rc) break;
+                }
+                b->parity = p0;   // replays start from the same parity (k is even)
+                cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+                if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+                if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+                e = cudaGraphInstantiate(&b->graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+                b->graph_steps = k;
+                b->graph_parity = p0;
+                b->graph_dirty = false;
+            }
+            CK(cudaGraphLaunch(b->graph, b->stream));
+        } else {
+            for (int64_t s = 0; s < k; ++s)
+                if ((rc = batch_launch_step(b))) return rc;
+            // an odd tail leaves the parity flipped, which the launches already track
+        }
+        total += k;
+        b->steps += k;
+        for (int i = 0; i < b->n; ++i)
+            if (b->active[i]) done[i] += k;
+        if ((rc = batch_snapshot(b, slot))) return rc;
+        const dim3 grid(BATCH_RB, b->nactive);
+        k_batch_resid<<<grid, 256, 0, b->stream>>>(b->d_desc, b->macpool, slot, b->d_active, b->partials);
+        CK(cudaGetLastError());
+        k_batch_resid_final<<<b->nactive, 256, 0, b->stream>>>(b->partials, BATCH_RB, b->result);
+        CK(cudaGetLastError());
+        std::vector<double> s((size_t)b->nactive * RES_NV);
+        CK(cudaMemcpyAsync(s.data(), b->result, s.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        std::vector<int> act;
+        for (int i = 0; i < b->n; ++i)
+            if (b->active[i]) act.push_back(i);
+        bool changed = false;
+        int diverged = -1;
+        for (int j = 0; j < b->nactive; ++j) {
+            const double* q = &s[(size_t)j * RES_NV];
+            const int i = act[j];
+            if (q[5] > 0) {
+                diverged = i;
+                b->active[i] = 0;
+                b->iparity[i] = b->parity;
+                changed = true;
+                continue;
+            }
+            const double ru = q[1] > 0 ? std::sqrt(q[0] / q[1]) : (q[0] > 0 ? INFINITY : 0.0);
+            const double rt = q[3] > 0 ? std::sqrt(q[2] / q[3]) : (q[2] > 0 ? INFINITY : 0.0);
+            res[i] = (ru > rt ? ru : rt) / (double)k;
+            if (res[i] <= tol) {
+                b->active[i] = 0;
+                b->iparity[i] = b->parity;
+                changed = true;
+            }
+        }
+        slot ^= 1;
+        if (changed && (rc = batch_rebuild(b))) return rc;
+        if (diverged >= 0) {
+            if (steps_out) std::copy(done.begin(), done.end(), steps_out);
+            if (res_out) std::copy(res.begin(), res.end(), res_out);
+            return fail(LBM_ERR_DIVERGED, "instance %d holds NaN or Inf", diverged);
+        }
+    }
+    if (steps_out) std::copy(done.begin(), done.end(), steps_out);
+    if (res_out) std::copy(res.begin(), res.end(), res_out);
+    return LBM_OK;
+}
+
+int lbm_batch_nusselt(lbm_batch* b, double* nu_inner, double* nu_outer) {
+    if (!b || !nu_inner || !nu_outer) return fail(LBM_ERR_INVALID, "NULL argument");
+    CK(cudaSetDevice(b->device));
+    std::vector<int> par(b->n);
+    for (int i = 0; i < b->n; ++i) par[i] = b->cur_parity(i);
+    int* d_par = (int*)(b->partials);   // scratch: n ints fit in the partial rows
+    CK(cudaMemcpyAsync(d_par, par.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    DISPATCH_STO(b->storage, k_batch_nusselt<S_><<<b->n, 256, 0, b->stream>>>(b->d_desc, b->pool, d_par, b->result));
+    CK(cudaGetLastError());
+    std::vector<double> r(2 * (size_t)b->n);
+    CK(cudaMemcpyAsync(r.data(), b->result, r.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        nu_inner[i] = b->p[i].geometry == LBM_PIPE_PERIODIC_Z ? NAN : r[2 * i];
+        nu_outer[i] = r[2 * i + 1];
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch* b, int32_t i, float* rho, float* ur, float* uz, float* T, int on_device) {
+    if (!b || i < 0 || i >= b->n) return fail(LBM_ERR_INVALID, "bad batch or instance");
+    CK(cudaSetDevice(b->device));
+    const InstDesc& d = b->desc[i];
+    const int64_t N = (int64_t)b->p[i].nr * b->p[i].nz;
+    float* m = b->macpool + d.off_mac;   // snapshot slot 0 of this instance as staging
+    const dim3 g((unsigned)((b->p[i].nz + 127) / 128), (unsigned)b->p[i].nr);
+    float* outs[4] = {rho, ur, uz, T};
+    float* dst[4];
+    for (int j = 0; j < 4; ++j) dst[j] = on_device ? outs[j] : (outs[j] ? m + j * d.plane : nullptr);
+    DISPATCH_STO(b->storage, k_moments<S_><<<g, 128, 0, b->stream>>>(d.c, batch_buf<S_>(b, i, b->cur_parity(i)),
+                                                                      (const PP<S_>*)(b->pool + d.off_phi), d.plane,
+                                                                      dst[0], dst[1], dst[2], dst[3]));
+    CK(cudaGetLastError());
+    if (!on_device)
+        for (int j = 0; j < 4; ++j)
+            if (outs[j]) CK(cudaMemcpyAsync(outs[j], dst[j], N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+// Autotuner: time `steps` batched steps for each bulk block shape (columns x rows
+// per block, at most 256 threads) and keep the fastest.  Leaves the state advanced
+// by the steps it ran.
+int lbm_batch_tune(lbm_batch* b, int32_t steps, int32_t* bz_out, int32_t* rows_out, float* ms_out) {
+    if (!b || steps < 1) return fail(LBM_ERR_INVALID, "bad batch or steps");
+    CK(cudaSetDevice(b->device));
+    static const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2}, {64, 4}, {32, 8}};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = INFINITY;
+    int bb = b->bz, br = b->rows;
+    int rc = LBM_OK;
+    for (const auto& s : shapes) {
+        b->bz = s[0];
+        b->rows = s[1];
+        if ((rc = batch_rebuild(b))) break;
+        if ((rc = lbm_batch_step(b, 2))) break;   // warm-up
+        cudaEventRecord(e0, b->stream);
+        if ((rc = lbm_batch_step(b, steps))) break;
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bb = s[0]; br = s[1]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    b->bz = bb;
+    b->rows = br;
+    if ((rc = batch_rebuild(b))) return rc;
+    if (bz_out) *bz_out = bb;
+    if (rows_out) *rows_out = br;
+    if (ms_out) *ms_out = best / (float)steps;
+    return LBM_OK;
+}
+
+int lbm_batch_get_info(lbm_batch* b, int32_t i, lbm_info* out) {
+    if (!b || !out || i < 0 || i >= b->n) return fail(LBM_ERR_INVALID, "bad batch, instance or pointer");
+    *out = b->info[i];
+    out->steps = b->steps;
+    return LBM_OK;
+}
+
+}  // extern "C"

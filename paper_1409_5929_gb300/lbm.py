@@ -73,6 +73,18 @@ _SIGS = {
                                    C.POINTER(C.c_int64)]),
     "lbm_field_residual_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, _vp, _vp, C.c_int64,
                                              C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
+    "lbm_batch_create": (C.c_int, [C.POINTER(lbm_params), C.c_int32, C.POINTER(_vp)]),
+    "lbm_batch_set_stream": (C.c_int, [_vp, _vp]),
+    "lbm_batch_set_porosity": (C.c_int, [_vp, C.c_int32, _vp, C.c_int]),
+    "lbm_batch_init_fields": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, C.c_int]),
+    "lbm_batch_step": (C.c_int, [_vp, C.c_int64]),
+    "lbm_batch_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, _vp, _vp]),
+    "lbm_batch_nusselt": (C.c_int, [_vp, _vp, _vp]),
+    "lbm_batch_moments": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int]),
+    "lbm_batch_tune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_float)]),
+    "lbm_batch_get_info": (C.c_int, [_vp, C.c_int32, C.POINTER(lbm_info)]),
+    "lbm_batch_destroy": (C.c_int, [_vp]),
     "lbm_destroy": (C.c_int, [_vp]),
     "lbm_last_error": (C.c_char_p, []),
 }
@@ -280,3 +292,109 @@ class Solver:
 
     def info(self) -> lbm_info:
         return lbm_get_info(self.h)
+
+
+# ---- batches ----------------------------------------------------------------
+def lbm_batch_create(params) -> int:
+    arr = (lbm_params * len(params))(*params)
+    h = _vp()
+    _check(load().lbm_batch_create(arr, len(params), C.byref(h)))
+    return h.value
+
+
+def lbm_batch_set_stream(b, stream):
+    _check(load().lbm_batch_set_stream(b, stream))
+
+
+def lbm_batch_set_porosity(b, i: int, phi, on_device: bool):
+    _check(load().lbm_batch_set_porosity(b, int(i), _ptr(phi), int(on_device)))
+
+
+def lbm_batch_init_fields(b, i: int, ur, uz, T, on_device: bool):
+    _check(load().lbm_batch_init_fields(b, int(i), _ptr(ur), _ptr(uz), _ptr(T), int(on_device)))
+
+
+def lbm_batch_step(b, nsteps: int):
+    _check(load().lbm_batch_step(b, int(nsteps)))
+
+
+def lbm_batch_run(b, n: int, max_steps: int, check_every: int, tol: float):
+    steps = np.zeros(n, np.int64)
+    res = np.zeros(n, np.float64)
+    _check(load().lbm_batch_run(b, int(max_steps), int(check_every), float(tol), steps.ctypes.data, res.ctypes.data))
+    return steps, res
+
+
+def lbm_batch_nusselt(b, n: int):
+    a = np.zeros(n, np.float64)
+    c = np.zeros(n, np.float64)
+    _check(load().lbm_batch_nusselt(b, a.ctypes.data, c.ctypes.data))
+    return a, c
+
+
+def lbm_batch_moments(b, i: int, rho, ur, uz, T, on_device: bool):
+    _check(load().lbm_batch_moments(b, int(i), _ptr(rho), _ptr(ur), _ptr(uz), _ptr(T), int(on_device)))
+
+
+def lbm_batch_tune(b, steps: int):
+    cz, rw, ms = C.c_int32(), C.c_int32(), C.c_float()
+    _check(load().lbm_batch_tune(b, int(steps), C.byref(cz), C.byref(rw), C.byref(ms)))
+    return cz.value, rw.value, ms.value
+
+
+def lbm_batch_get_info(b, i: int) -> lbm_info:
+    info = lbm_info()
+    _check(load().lbm_batch_get_info(b, int(i), C.byref(info)))
+    return info
+
+
+def lbm_batch_destroy(b):
+    _check(load().lbm_batch_destroy(b))
+
+
+class Batch:
+    """Independent problems advanced together on the current CUDA device."""
+
+    def __init__(self, params):
+        self.params = list(params)
+        self.n = len(self.params)
+        self.b = lbm_batch_create(self.params)
+
+    def close(self):
+        if self.b:
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_porosity(self, i, phi):
+        lbm_batch_set_porosity(self.b, i, np.ascontiguousarray(phi, dtype=np.float32), False)
+
+    def init_fields(self, i, ur=None, uz=None, T=None):
+        ur, uz, T = (None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (ur, uz, T))
+        lbm_batch_init_fields(self.b, i, ur, uz, T, False)
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+
+    def run(self, max_steps, check_every=1000, tol=1e-8):
+        return lbm_batch_run(self.b, self.n, max_steps, check_every, tol)
+
+    def nusselt(self):
+        return lbm_batch_nusselt(self.b, self.n)
+
+    def moments(self, i):
+        p = self.params[i]
+        out = [np.empty((p.nr, p.nz), np.float32) for _ in range(4)]
+        lbm_batch_moments(self.b, i, *out, False)
+        return out
+
+    def tune(self, steps=10):
+        return lbm_batch_tune(self.b, steps)
+
+    def info(self, i) -> lbm_info:
+        return lbm_batch_get_info(self.b, i)
