@@ -206,6 +206,85 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def _sweep_params(lbm, n, seed, storage, nr_lo=64, nr_hi=512):
+    from paper_1409_5929_gb300 import inputs
+
+    return [lbm.lbm_params_default(nr=d["nr"], nz=d["nz"], Ra=d["Ra"], Da=d["Da"], eps_mean=d["eps"], Pr=d["Pr"],
+                                   radius_ratio=d["radius_ratio"], storage=storage)
+            for d in inputs.sweep_instances(n, seed=seed, nr_lo=nr_lo, nr_hi=nr_hi)]
+
+
+def sweep_throughput(steps: int):
+    """Batched sweep (256 annulus instances, Nr ~ U{64..512}, Nz = 2 Nr, Ra log-U[1e3, 1e6],
+    Da log-U[1e-5, 1e-1], eps ~ U[0.3, 0.9], Pr in {0.71, 1, 7}, R* ~ U[1.5, 4], seed 3,
+    FP16 storage): node updates per second of the batched launches vs the same
+    instances stepped one at a time."""
+    import torch
+
+    from paper_1409_5929_gb300 import lbm
+
+    params = _sweep_params(lbm, 256, 3, "f16")
+    nodes = sum(p.nr * p.nz for p in params)
+    b = lbm.Batch(params)
+    cols, rows, _ = b.tune(10)
+    b.step(10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.run(steps, steps if steps % 2 == 0 else steps + 1, -1.0)   # graph-replayed steps
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / (2 * steps)
+    b.close()
+    singles = [lbm.Solver(p) for p in params]
+    for s in singles:
+        s.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in singles:
+        s.step(steps)
+    torch.cuda.synchronize()
+    ts = (time.perf_counter() - t0) / steps
+    for s in singles:
+        s.close()
+    return {"workload": "256 annulus instances of the sweep draws (seed 3), 48.6 M nodes, FP16 storage",
+            "batched_mlups": round(nodes / tb / 1e6, 1), "one_at_a_time_mlups": round(nodes / ts / 1e6, 1),
+            "speedup": round(ts / tb, 2), "tile": f"{cols}x{rows}", "steps": 2 * steps}
+
+
+def time_to_steady(max_steps: int = 300000, check: int = 1000, tol: float = 1e-8):
+    """Time to the steady criterion (mean change per step over a check interval <= tol)
+    for a bounded sweep: 16 instances with the sweep's parameter ranges at
+    Nr ~ U{24..48}, Nz = 2 Nr (seed 4).  Plain: each instance alone in FP32 (lbm_run);
+    batched FP32; batched FP16 storage.  |dNu| against the plain FP32 results."""
+    from paper_1409_5929_gb300 import lbm
+
+    out = {"workload": "16 annulus instances, sweep parameter ranges, Nr ~ U{24..48}, Nz = 2 Nr, seed 4",
+           "criterion": f"interval residual <= {tol:g} (checked every {check} steps)"}
+    p32 = _sweep_params(lbm, 16, 4, "f32", 24, 48)
+    t0 = time.perf_counter()
+    nu_ref, steps_ref = [], []
+    for p in p32:
+        s = lbm.Solver(p)
+        n, r = s.run(max_steps, check, tol)
+        nu_ref.append(s.nusselt())
+        steps_ref.append(n)
+        s.close()
+    out["plain_fp32_s"] = round(time.perf_counter() - t0, 3)
+    out["plain_fp32_steps_max"] = int(max(steps_ref))
+    nu_ref = np.array(nu_ref)
+    for name, sto in (("batched_fp32", "f32"), ("batched_fp16", "f16")):
+        b = lbm.Batch(_sweep_params(lbm, 16, 4, sto, 24, 48))
+        t0 = time.perf_counter()
+        steps, res = b.run(max_steps, check, tol)
+        dt = time.perf_counter() - t0
+        nu = np.stack(b.nusselt(), axis=1)
+        b.close()
+        out[name] = {"s": round(dt, 3), "speedup_vs_plain": round(out["plain_fp32_s"] / dt, 2),
+                     "converged": int((res <= tol).sum()), "of": 16, "steps_max": int(steps.max()),
+                     "max_abs_dNu": float(np.abs(nu - nu_ref).max())}
+    return out
+
+
 def cpu_sample(seconds: float):
     """The oracle as it stands on a bounded sample: the same recipe on a 256 x 512
     annulus, all host cores, timed for about `seconds`."""
@@ -269,6 +348,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the sweep and time-to-steady sections")
     ap.add_argument("--nr", type=int, default=NR, help="override the grid (profiling of small cases only)")
     ap.add_argument("--nz", type=int, default=NZ)
     args = ap.parse_args()
@@ -300,6 +380,9 @@ def main():
 
         dist.barrier()
     line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["sweep"] = sweep_throughput(100)
+        line["time_to_steady"] = time_to_steady()
     if rank == 0:
         line["cpu_baseline"] = cpu_sample(args.cpu_seconds) if world == 1 else None
         print(json.dumps(line), flush=True)
