@@ -37,6 +37,27 @@ METRIC = "MLUPS & % HBM roofline; time-to-steady vs plain FP32 GPU at |ΔNu|≤1
 SAMPLE_NR, SAMPLE_NZ = 256, 512   # bounded CPU sample: the same recipe on a 256 x 512 annulus
 
 
+# DRAM traffic of one k_bulk launch on the 4096 x 8192 workload (dram__bytes_read.sum +
+# dram__bytes_write.sum, one single-pass ncu capture; profiles/k_bulk_f32_4096x8192_traffic.md),
+# valid only for the kernel sources it was taken on (hash of csrc/lbm.cu + lbm_physics.cuh).
+TRAFFIC = {("f32", 4096, 8192): ("a77a2d2a785ddc41", 2.02e9 + 1.83e9)}
+
+
+def _kernel_hash() -> str:
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_1409_5929_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("lbm.cu", "lbm_physics.cuh"):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(storage: str):
+    rec = TRAFFIC.get((storage, NR, NZ))
+    return rec[1] if rec and rec[0] == _kernel_hash() else None
+
+
 def _set_grid(nr: int, nz: int):
     global NR, NZ
     NR, NZ = nr, nz
@@ -105,6 +126,25 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(local_ms: float, local_units: float, device=None) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: the units all ranks processed
+    divided by the slowest rank's time (MAX over ranks).  Returns (units per second,
+    max milliseconds).  Works with any initialised process group (NCCL or gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([local_ms, local_units], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tu = t[1:].clone()
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        ms, units = float(tm.item()), float(tu.item())
+    else:
+        ms, units = local_ms, local_units
+    return units / (ms * 1e-3), ms
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -145,13 +185,8 @@ def run_ours(args, rank, world, local_rank):
     bulk_ms, bulk_n, wall_ms, wall_n = lbm.lbm_kernel_times(s.h)
     lbm.lbm_set_timing(s.h, False)
     ck = clocks.stop()
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        if world > 1:
-            dist.barrier()
-    ms_max = float(t.item())
-    value = world * nodes * args.steps / (ms_max * 1e-3) / 1e6
+    ups, ms_max = aggregate(ms, float(nodes) * args.steps, device="cuda")
+    value = ups / 1e6
 
     # end to end through the C ABI with host buffers: upload the porosity field from
     # pinned host memory, one step, read the Nusselt numbers back (synchronising)
@@ -165,10 +200,8 @@ def run_ours(args, rank, world, local_rank):
         s.step(1)
         nu = s.nusselt()
     t1 = time.perf_counter()
-    te = torch.tensor([t1 - t0], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = world * nodes * ke / float(te.item()) / 1e6
+    e2e_ups, _ = aggregate((t1 - t0) * 1e3, float(nodes) * ke, device="cuda")
+    e2e_val = e2e_ups / 1e6
     s.close()
     if rank != 0:
         return None
@@ -194,7 +227,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "state larger than L2 (no flush)",
                    "bytes_per_step": info.bytes_per_step},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4), "traffic": _traffic(args.storage),
                      "kernel": f"k_bulk<{args.storage}>", "peak_source": f"{peak_kind} hbm_gbs",
                      "avg_launch_ms": round(bulk_avg, 5), "bytes_per_launch": bulk_bytes,
                      "wall_kernel_avg_ms": round(wall_ms / max(wall_n, 1), 5)},
