@@ -1,0 +1,365 @@
+"""Learned warm start: a 2-D Fourier neural operator (FNO) trained on steady fields of the
+lattice Boltzmann solver, mapping the porosity field and the problem parameters to an
+initial (u_r, u_z, T).  The paper has no counterpart; the solver always runs to
+convergence from the proposed field, and the cold start remains the fallback.
+
+Network (channels-last activations [batch, nr, nz, channels], FP32 in memory; every
+contraction runs in the BF16 tensor-core GEMM of libfno.so with FP32 accumulation):
+  lift      h = x P + p                        8 -> width
+  layers    pre = h W + b + K(h);  h = GELU(pre)   (no GELU after the last layer)
+  project   q = GELU(h Q1 + q1);  y = q Q2 + q2      width -> hidden -> 3
+K is the truncated spectral convolution: rfft2, keep kr in [0, m) U [nr - m, nr) and
+kz in [0, m), multiply by complex weights per mode, irfft2 -- evaluated as dense
+GEMMs against truncated DFT matrices (z: real -> complex, r: complex), the per-mode
+channel mixing, then the inverse pair, all in fno.h kernels.  Torch is used for device
+buffers only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+FNO_LIB_PATH = os.path.join(HERE, "libfno.so")
+
+_lock = threading.Lock()
+_lib = None
+_vp = C.c_void_p
+_i64 = C.c_int64
+_SIGS = {
+    "fno_gemm": [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, _vp, _i64, _i64, _vp, _i64, _i64, C.c_float,
+                 _vp, _i64, _i64, C.c_int, _vp, _vp],
+    "fno_gelu_fwd": [_vp, _vp, _i64, _vp],
+    "fno_gelu_bwd": [_vp, _vp, _vp, _i64, C.c_int, _vp],
+    "fno_mix_fwd": [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp],
+    "fno_mix_bwd": [_vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp],
+    "fno_colsum": [_vp, _i64, C.c_int, _i64, _vp, C.c_int, _vp],
+    "fno_mse": [_vp, _vp, _vp, _vp, _i64, _vp],
+    "fno_adam": [_vp, _vp, _vp, _vp, _i64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, _vp],
+}
+
+
+def load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(FNO_LIB_PATH):
+                from . import build as _b
+
+                _b.build()
+            lib = C.CDLL(FNO_LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = C.c_int
+                fn.argtypes = args
+            lib.fno_last_error.restype = C.c_char_p
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError(f"fno error {rc}: {load().fno_last_error().decode()}")
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream():
+    import torch
+
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ---- C-named wrappers (argument marshalling only) ---------------------------
+def fno_gemm(transA, transB, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, Cm, ldc, sC, batch=1, bias=None,
+             a_off=0, b_off=0, c_off=0):
+    """Pointers may be offset by a_off / b_off / c_off elements (views into a buffer)."""
+    _check(load().fno_gemm(int(transA), int(transB), int(M), int(N), int(K), float(alpha), _p(A) + 4 * a_off,
+                           int(lda), int(sA), _p(B) + 4 * b_off, int(ldb), int(sB), float(beta), _p(Cm) + 4 * c_off,
+                           int(ldc), int(sC), int(batch), _p(bias), _stream()))
+
+
+def fno_gelu_fwd(x, y):
+    _check(load().fno_gelu_fwd(_p(x), _p(y), x.numel(), _stream()))
+
+
+def fno_gelu_bwd(x, dy, dx, accumulate=False):
+    _check(load().fno_gelu_bwd(_p(x), _p(dy), _p(dx), x.numel(), int(accumulate), _stream()))
+
+
+def fno_mix_fwd(X, R, Y, batch, nkr, nkz, Cin, O):
+    _check(load().fno_mix_fwd(_p(X), _p(R), _p(Y), batch, nkr, nkz, Cin, O, _stream()))
+
+
+def fno_mix_bwd(X, R, dY, dX, dR, batch, nkr, nkz, Cin, O, accumulate=False):
+    _check(load().fno_mix_bwd(_p(X), _p(R), _p(dY), _p(dX), _p(dR), batch, nkr, nkz, Cin, O, int(accumulate),
+                              _stream()))
+
+
+def fno_colsum(X, rows, N, ldx, out, accumulate=False):
+    _check(load().fno_colsum(_p(X), int(rows), int(N), int(ldx), _p(out), int(accumulate), _stream()))
+
+
+def fno_mse(y, t, dy, loss):
+    _check(load().fno_mse(_p(y), _p(t), _p(dy), _p(loss), y.numel(), _stream()))
+
+
+def fno_adam(w, g, m, v, lr, b1, b2, eps, step):
+    _check(load().fno_adam(_p(w), _p(g), _p(m), _p(v), w.numel(), float(lr), float(b1), float(b2), float(eps),
+                           int(step), _stream()))
+
+
+# ---- the operator -------------------------------------------------------------
+PARAM_ORDER = ["P", "p"] + [f"{n}{l}" for l in range(4) for n in ("R", "W", "b")] + ["Q1", "q1", "Q2", "q2"]
+
+
+def kr_values(nr: int, m: int):
+    """Retained radial wavenumbers: 0..m-1 and nr-m..nr-1."""
+    return list(range(m)) + list(range(nr - m, nr))
+
+
+def init_params(nr, nz, width=32, modes=16, layers=4, in_ch=8, out_ch=3, hidden=128, seed=0):
+    """FP32 parameters (numpy) in the layout of the kernels: matrices [in, out], spectral
+    weights [nkr, nkz, in, out, 2]."""
+    rng = np.random.default_rng(seed)
+    nkr, nkz = 2 * modes, modes
+
+    def lin(i, o):
+        a = 1.0 / math.sqrt(i)
+        return rng.uniform(-a, a, (i, o)).astype(np.float32), rng.uniform(-a, a, o).astype(np.float32)
+
+    P = {}
+    P["P"], P["p"] = lin(in_ch, width)
+    for l in range(layers):
+        P[f"R{l}"] = (rng.uniform(0, 1, (nkr, nkz, width, width, 2)) / (width * width)).astype(np.float32)
+        P[f"W{l}"], P[f"b{l}"] = lin(width, width)
+    P["Q1"], P["q1"] = lin(width, hidden)
+    P["Q2"], P["q2"] = lin(hidden, out_ch)
+    return P
+
+
+def dft_matrices(nr, nz, modes):
+    """Truncated DFT matrices (float64 numpy): Fz [nz, 2m] (cos | -sin) for the z
+    transform, Cr, Sr [2m, nr] for the r transform, Gz [2m, nz] for the inverse z
+    transform with the one-sided weights (1 for kz = 0, 2 otherwise) and 1/(nr nz)."""
+    m = modes
+    z = np.arange(nz)[:, None]
+    kz = np.arange(m)[None, :]
+    ang = 2 * np.pi * z * kz / nz
+    Fz = np.concatenate([np.cos(ang), -np.sin(ang)], axis=1)
+    kr = np.array(kr_values(nr, m))[:, None]
+    r = np.arange(nr)[None, :]
+    angr = 2 * np.pi * kr * r / nr
+    Cr, Sr = np.cos(angr), np.sin(angr)
+    w = np.where(np.arange(m) == 0, 1.0, 2.0)[:, None] / (nr * nz)
+    angz = 2 * np.pi * np.arange(m)[:, None] * np.arange(nz)[None, :] / nz
+    Gz = np.concatenate([w * np.cos(angz), -w * np.sin(angz)], axis=0)
+    return Fz, Cr, Sr, Gz
+
+
+class FNO2d:
+    """Forward, backward and Adam on the GPU through libfno.so."""
+
+    def __init__(self, nr, nz, width=32, modes=16, layers=4, in_ch=8, out_ch=3, hidden=128, seed=0, params=None):
+        import torch
+
+        self.nr, self.nz, self.width, self.m, self.L = nr, nz, width, modes, layers
+        self.in_ch, self.out_ch, self.hidden = in_ch, out_ch, hidden
+        self.nkr, self.nkz = 2 * modes, modes
+        P = params if params is not None else init_params(nr, nz, width, modes, layers, in_ch, out_ch, hidden, seed)
+        dev = "cuda"
+        self.w = {k: torch.tensor(np.ascontiguousarray(v, dtype=np.float32), device=dev) for k, v in P.items()}
+        self.g = {k: torch.zeros_like(v) for k, v in self.w.items()}
+        self.adam_m = {k: torch.zeros_like(v) for k, v in self.w.items()}
+        self.adam_v = {k: torch.zeros_like(v) for k, v in self.w.items()}
+        self.step_count = 0
+        Fz, Cr, Sr, Gz = dft_matrices(nr, nz, modes)
+        f32 = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+        self.Fz, self.Cr, self.Sr, self.Gz = f32(Fz), f32(Cr), f32(Sr), f32(Gz)
+        self.Ci, self.Si = f32(Cr.T), f32(Sr.T)
+        self._buf = {}
+        load()
+
+    # -- buffers ------------------------------------------------------------
+    def _b(self, name, shape):
+        import torch
+
+        t = self._buf.get(name)
+        if t is None or tuple(t.shape) != tuple(shape):
+            t = torch.empty(shape, dtype=torch.float32, device="cuda")
+            self._buf[name] = t
+        return t
+
+    def params_numpy(self):
+        return {k: v.detach().cpu().numpy() for k, v in self.w.items()}
+
+    # -- spectral convolution pieces (B = batch) -------------------------------
+    def _zdft(self, v, Z, B, Cc):
+        """Z[b, r, kz2, c] = sum_z Fz[z, kz2] v[b, r, z, c]."""
+        nz, m2 = self.nz, 2 * self.m
+        fno_gemm(1, 0, m2, Cc, nz, 1.0, self.Fz, m2, 0, v, Cc, nz * Cc, 0.0, Z, Cc, m2 * Cc, B * self.nr)
+
+    def _zdft_T(self, dZ, dv, B, Cc):
+        """dv[b, r, z, c] += sum_kz2 Fz[z, kz2] dZ[b, r, kz2, c]."""
+        nz, m2 = self.nz, 2 * self.m
+        fno_gemm(0, 0, nz, Cc, m2, 1.0, self.Fz, m2, 0, dZ, Cc, m2 * Cc, 1.0, dv, Cc, nz * Cc, B * self.nr)
+
+    def _rdft(self, Z, W, B, Cc, M1, M2, rows_in, rows_out):
+        """W_re = M1 Z_re + M2 Z_im, W_im = M1 Z_im - M2 Z_re, per batch; Z [rows_in, 2 m C],
+        W [rows_out, 2 m C]; M1, M2 [rows_out, rows_in]."""
+        mc = self.m * Cc
+        sz, sw = rows_in * 2 * mc, rows_out * 2 * mc
+        K = rows_in
+        fno_gemm(0, 0, rows_out, mc, K, 1.0, M1, K, 0, Z, 2 * mc, sz, 0.0, W, 2 * mc, sw, B)
+        fno_gemm(0, 0, rows_out, mc, K, 1.0, M2, K, 0, Z, 2 * mc, sz, 1.0, W, 2 * mc, sw, B, b_off=mc)
+        fno_gemm(0, 0, rows_out, mc, K, 1.0, M1, K, 0, Z, 2 * mc, sz, 0.0, W, 2 * mc, sw, B, b_off=mc, c_off=mc)
+        fno_gemm(0, 0, rows_out, mc, K, -1.0, M2, K, 0, Z, 2 * mc, sz, 1.0, W, 2 * mc, sw, B, c_off=mc)
+
+    def _irdft(self, Y, V, B, Cc, M1, M2, rows_in, rows_out):
+        """V_re = M1 Y_re - M2 Y_im, V_im = M2 Y_re + M1 Y_im."""
+        mc = self.m * Cc
+        sy, sv = rows_in * 2 * mc, rows_out * 2 * mc
+        K = rows_in
+        fno_gemm(0, 0, rows_out, mc, K, 1.0, M1, K, 0, Y, 2 * mc, sy, 0.0, V, 2 * mc, sv, B)
+        fno_gemm(0, 0, rows_out, mc, K, -1.0, M2, K, 0, Y, 2 * mc, sy, 1.0, V, 2 * mc, sv, B, b_off=mc)
+        fno_gemm(0, 0, rows_out, mc, K, 1.0, M2, K, 0, Y, 2 * mc, sy, 0.0, V, 2 * mc, sv, B, c_off=mc)
+        fno_gemm(0, 0, rows_out, mc, K, 1.0, M1, K, 0, Y, 2 * mc, sy, 1.0, V, 2 * mc, sv, B, b_off=mc, c_off=mc)
+
+    def _izdft(self, V, out, B, Cc):
+        """out[b, r, z, c] += sum_kz2 Gz[kz2, z] V[b, r, kz2, c]."""
+        nz, m2 = self.nz, 2 * self.m
+        fno_gemm(1, 0, nz, Cc, m2, 1.0, self.Gz, nz, 0, V, Cc, m2 * Cc, 1.0, out, Cc, nz * Cc, B * self.nr)
+
+    def _izdft_T(self, dout, dV, B, Cc):
+        """dV[b, r, kz2, c] = sum_z Gz[kz2, z] dout[b, r, z, c]."""
+        nz, m2 = self.nz, 2 * self.m
+        fno_gemm(0, 0, m2, Cc, nz, 1.0, self.Gz, nz, 0, dout, Cc, nz * Cc, 0.0, dV, Cc, m2 * Cc, B * self.nr)
+
+    def _wgrad(self, X, dY, K, Min, Nout, dW):
+        """dW [Min, Nout] = X^T dY with X [K, Min], dY [K, Nout]; split over K."""
+        S = max(1, min(64, K // 4096))
+        while K % S:
+            S -= 1
+        tmp = self._b(f"wg_{Min}_{Nout}_{S}", (S, Min, Nout))
+        ks = K // S
+        fno_gemm(1, 0, Min, Nout, ks, 1.0, X, Min, ks * Min, dY, Nout, ks * Nout, 0.0, tmp, Nout, Min * Nout, S)
+        fno_colsum(tmp, S, Min * Nout, Min * Nout, dW, accumulate=True)
+
+    # -- forward / backward -------------------------------------------------
+    def forward(self, x, train=False):
+        """x: [B, nr, nz, in_ch] float32 CUDA tensor -> [B, nr, nz, out_ch]."""
+        B = x.shape[0]
+        px = B * self.nr * self.nz
+        Wd, m = self.width, self.m
+        w = self.w
+        h = self._b("h0", (B, self.nr, self.nz, Wd))
+        fno_gemm(0, 0, px, Wd, self.in_ch, 1.0, x, self.in_ch, 0, w["P"], Wd, 0, 0.0, h, Wd, 0, 1, bias=w["p"])
+        self._x = x
+        self._hs = [h]
+        for l in range(self.L):
+            Z = self._b(f"Z{l}", (B, self.nr, 2 * m, Wd))
+            Wm = self._b(f"Wm{l}", (B, self.nkr, 2 * m, Wd))
+            Y = self._b(f"Y{l}", (B, self.nkr, 2 * m, Wd))
+            V = self._b(f"V{l}", (B, self.nr, 2 * m, Wd))
+            pre = self._b(f"pre{l}", (B, self.nr, self.nz, Wd))
+            self._zdft(h, Z, B, Wd)
+            self._rdft(Z, Wm, B, Wd, self.Cr, self.Sr, self.nr, self.nkr)
+            fno_mix_fwd(Wm, w[f"R{l}"], Y, B, self.nkr, self.nkz, Wd, Wd)
+            self._irdft(Y, V, B, Wd, self.Ci, self.Si, self.nkr, self.nr)
+            fno_gemm(0, 0, px, Wd, Wd, 1.0, h, Wd, 0, w[f"W{l}"], Wd, 0, 0.0, pre, Wd, 0, 1, bias=w[f"b{l}"])
+            self._izdft(V, pre, B, Wd)
+            if l < self.L - 1:
+                h = self._b(f"h{l + 1}", (B, self.nr, self.nz, Wd))
+                fno_gelu_fwd(pre, h)
+            else:
+                h = pre
+            self._hs.append(h)
+        qp = self._b("qpre", (B, self.nr, self.nz, self.hidden))
+        q = self._b("q", (B, self.nr, self.nz, self.hidden))
+        y = self._b("y", (B, self.nr, self.nz, self.out_ch))
+        fno_gemm(0, 0, px, self.hidden, Wd, 1.0, h, Wd, 0, w["Q1"], self.hidden, 0, 0.0, qp, self.hidden, 0, 1,
+                 bias=w["q1"])
+        fno_gelu_fwd(qp, q)
+        fno_gemm(0, 0, px, self.out_ch, self.hidden, 1.0, q, self.hidden, 0, w["Q2"], self.out_ch, 0, 0.0, y,
+                 self.out_ch, 0, 1, bias=w["q2"])
+        return y
+
+    def zero_grad(self):
+        for g in self.g.values():
+            g.zero_()
+
+    def backward(self, dy):
+        """Accumulate parameter gradients for dL/dy of the last forward."""
+        B = dy.shape[0]
+        px = B * self.nr * self.nz
+        Wd, m, hid = self.width, self.m, self.hidden
+        w, g = self.w, self.g
+        q, qp = self._buf["q"], self._buf["qpre"]
+        h = self._hs[-1]
+        # projection
+        self._wgrad(q, dy, px, hid, self.out_ch, g["Q2"])
+        fno_colsum(dy, px, self.out_ch, self.out_ch, g["q2"], accumulate=True)
+        dq = self._b("dq", (B, self.nr, self.nz, hid))
+        fno_gemm(0, 1, px, hid, self.out_ch, 1.0, dy, self.out_ch, 0, w["Q2"], self.out_ch, 0, 0.0, dq, hid, 0, 1)
+        fno_gelu_bwd(qp, dq, dq)
+        self._wgrad(h, dq, px, Wd, hid, g["Q1"])
+        fno_colsum(dq, px, hid, hid, g["q1"], accumulate=True)
+        dh = self._b("dh_a", (B, self.nr, self.nz, Wd))
+        fno_gemm(0, 1, px, Wd, hid, 1.0, dq, hid, 0, w["Q1"], hid, 0, 0.0, dh, Wd, 0, 1)
+        other = "dh_b"
+        for l in reversed(range(self.L)):
+            pre = self._buf[f"pre{l}"]
+            hin = self._hs[l]
+            dpre = self._b("dpre", (B, self.nr, self.nz, Wd))
+            if l < self.L - 1:
+                fno_gelu_bwd(pre, dh, dpre)
+            else:
+                dpre.copy_(dh)
+            # pointwise path
+            self._wgrad(hin, dpre, px, Wd, Wd, g[f"W{l}"])
+            fno_colsum(dpre, px, Wd, Wd, g[f"b{l}"], accumulate=True)
+            dhin = self._b(other, (B, self.nr, self.nz, Wd))
+            fno_gemm(0, 1, px, Wd, Wd, 1.0, dpre, Wd, 0, w[f"W{l}"], Wd, 0, 0.0, dhin, Wd, 0, 1)
+            # spectral path
+            dV = self._b("dV", (B, self.nr, 2 * m, Wd))
+            dY = self._b("dY", (B, self.nkr, 2 * m, Wd))
+            dWm = self._b("dWm", (B, self.nkr, 2 * m, Wd))
+            dZ = self._b("dZ", (B, self.nr, 2 * m, Wd))
+            self._izdft_T(dpre, dV, B, Wd)
+            # V = irdft(Y) with (Ci, Si): dY_re = Cr dV_re + Sr dV_im, dY_im = Cr dV_im - Sr dV_re
+            self._rdft(dV, dY, B, Wd, self.Cr, self.Sr, self.nr, self.nkr)
+            fno_mix_bwd(self._buf[f"Wm{l}"], w[f"R{l}"], dY, dWm, g[f"R{l}"], B, self.nkr, self.nkz, Wd, Wd,
+                        accumulate=True)
+            # Wm = rdft(Z) with (Cr, Sr): dZ_re = Ci dW_re - Si dW_im, dZ_im = Si dW_re + Ci dW_im
+            self._irdft(dWm, dZ, B, Wd, self.Ci, self.Si, self.nkr, self.nr)
+            self._zdft_T(dZ, dhin, B, Wd)
+            dh, other = dhin, ("dh_a" if other == "dh_b" else "dh_b")
+        # lift
+        self._wgrad(self._x, dh, px, self.in_ch, Wd, g["P"])
+        fno_colsum(dh, px, Wd, Wd, g["p"], accumulate=True)
+
+    def loss_and_grad(self, x, t):
+        """MSE loss (device double, accumulated) and parameter gradients for one batch."""
+        import torch
+
+        y = self.forward(x, train=True)
+        dy = self._b("dy", tuple(y.shape))
+        lbuf = self._buf.get("lossd")
+        if lbuf is None:
+            lbuf = torch.zeros(1, dtype=torch.float64, device="cuda")
+            self._buf["lossd"] = lbuf
+        lbuf.zero_()
+        fno_mse(y, t, dy, lbuf)
+        self.backward(dy)
+        return lbuf
+
+    def adam_step(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        self.step_count += 1
+        for k in self.w:
+            fno_adam(self.w[k], self.g[k], self.adam_m[k], self.adam_v[k], lr, b1, b2, eps, self.step_count)

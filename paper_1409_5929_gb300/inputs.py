@@ -30,6 +30,15 @@ def porosity_field(nr: int, nz: int, lo: float, hi: float, sigma: float, seed: i
     return np.ascontiguousarray(white, dtype=np.float32)
 
 
+def porosity_field_around(nr: int, nz: int, mean: float, amp: float, sigma: float, seed: int) -> np.ndarray:
+    """Smoothed porosity field with a prescribed mean and standard deviation: white
+    noise smoothed by a Gaussian of sigma cells (as porosity_field), standardised,
+    scaled to standard deviation `amp` around `mean`, clipped to [0.05, 0.99]."""
+    s = porosity_field(nr, nz, 0.0, 1.0, sigma, seed).astype(np.float64)
+    s = (s - s.mean()) / max(s.std(), 1e-12)
+    return np.ascontiguousarray(np.clip(mean + amp * s, 0.05, 0.99), dtype=np.float32)
+
+
 def uniform_field(nr: int, nz: int, value: float) -> np.ndarray:
     return np.full((nr, nz), value, dtype=np.float32)
 

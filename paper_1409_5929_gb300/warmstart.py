@@ -1,0 +1,228 @@
+"""Learned warm start of the steady-state iteration.
+
+Pipeline (all compute on the GPU: the lattice Boltzmann step in liblbm.so, the network
+in libfno.so):
+  1. instances: parameter draws of the batched sweep (Ra log-U[1e3, 1e6], Da log-U[1e-5,
+     1e-1], eps ~ U[0.3, 0.9], Pr in {0.71, 1, 7}, R* ~ U[1.5, 4]) on an nr x nz annulus,
+     each with a smoothed porosity field of mean eps (inputs.porosity_field_around);
+  2. targets: the solver's own steady fields (lbm_batch_run to the steady criterion,
+     capped at max_steps);
+  3. training: the FNO (4 Fourier layers, width 32, 16 modes) on normalised inputs
+     (porosity, five parameter planes, r, z) and outputs (u_r / U, u_z / U, 2 (T - T0) / dT
+     with U = Ma c_s), MSE, Adam, BF16 tensor-core GEMMs with FP32 accumulation;
+  4. warm start of held-out instances: the network's fields through lbm_init_fields,
+     then the iteration to the same criterion; it decides the result.  An instance whose
+     warm run diverges, or ends more than dNu_tol away from its cold-start Nusselt
+     numbers, falls back to the cold start.
+
+    python -m paper_1409_5929_gb300.warmstart [--ntrain 2000] [--nheld 256] ...
+prints one JSON line with the measurements.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import inputs, lbm
+from . import fno as F
+
+U_LATTICE = 0.1 / math.sqrt(3.0)   # U = Ma c_s with the Ma = 0.1 of Eq. 39
+
+
+def make_instances(n: int, seed: int, nr: int, nz: int, amp: float = 0.05, sigma: float = 8.0):
+    draws = inputs.sweep_instances(n, seed=seed, nr_lo=nr, nr_hi=nr)
+    out = []
+    for k, d in enumerate(draws):
+        phi = inputs.porosity_field_around(nr, nz, d["eps"], amp, sigma, seed * 100003 + k)
+        p = lbm.lbm_params_default(nr=nr, nz=nz, Ra=d["Ra"], Da=d["Da"], Pr=d["Pr"],
+                                   radius_ratio=d["radius_ratio"], eps_mean=float(phi.mean(dtype=np.float64)))
+        out.append((p, phi, d))
+    return out
+
+
+def features(inst, nr: int, nz: int) -> np.ndarray:
+    """[n, nr, nz, 8] float32: porosity, log Ra, log Da, eps, log Pr, R*, r, z (scaled to ~[-1, 1])."""
+    X = np.empty((len(inst), nr, nz, 8), np.float32)
+    rr = np.linspace(-1, 1, nr, dtype=np.float32)[:, None]
+    zz = np.linspace(-1, 1, nz, dtype=np.float32)[None, :]
+    for i, (p, phi, d) in enumerate(inst):
+        X[i, :, :, 0] = (phi - 0.6) / 0.3
+        X[i, :, :, 1] = (math.log10(d["Ra"]) - 4.5) / 1.5
+        X[i, :, :, 2] = (math.log10(d["Da"]) + 3.0) / 2.0
+        X[i, :, :, 3] = (d["eps"] - 0.6) / 0.3
+        X[i, :, :, 4] = math.log10(d["Pr"]) / 0.85
+        X[i, :, :, 5] = (d["radius_ratio"] - 2.75) / 1.25
+        X[i, :, :, 6] = rr
+        X[i, :, :, 7] = zz
+    return X
+
+
+def targets_from_fields(ur, uz, T, T0=0.5, dT=1.0):
+    return np.stack([ur / U_LATTICE, uz / U_LATTICE, 2.0 * (T - T0) / dT], axis=-1).astype(np.float32)
+
+
+def fields_from_targets(Y, T0=0.5, dT=1.0):
+    return Y[..., 0] * U_LATTICE, Y[..., 1] * U_LATTICE, T0 + 0.5 * dT * Y[..., 2]
+
+
+def run_batch(inst, max_steps, check, tol, warm=None):
+    """Batched run of instances to the criterion; returns steps, criterion values, Nu
+    (inner, outer), the fields and the wall time.  warm: optional (ur, uz, T) arrays
+    [n, nr, nz] as start fields."""
+    import torch
+
+    b = lbm.Batch([p for p, _, _ in inst])
+    for i, (p, phi, _) in enumerate(inst):
+        b.set_porosity(i, phi)
+        if warm is None:
+            b.init_fields(i)
+        else:
+            b.init_fields(i, warm[0][i], warm[1][i], warm[2][i])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps, res = b.run(max_steps, check, tol)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nu = np.stack(b.nusselt(), axis=1)
+    fields = [b.moments(i) for i in range(len(inst))]
+    b.close()
+    return steps, res, nu, fields, dt
+
+
+def train(net, X, Y, epochs, batch, lr, seed=0, log=None):
+    import torch
+
+    n = X.shape[0]
+    rng = np.random.default_rng(seed)
+    steps_per_epoch = n // batch
+    total = epochs * steps_per_epoch
+    losses = []
+    it = 0
+    for ep in range(epochs):
+        perm = torch.tensor(rng.permutation(n)[: steps_per_epoch * batch], device="cuda").view(steps_per_epoch, batch)
+        acc = torch.zeros((), dtype=torch.float64, device="cuda")
+        for s in range(steps_per_epoch):
+            idx = perm[s]
+            xb = X.index_select(0, idx).contiguous()
+            yb = Y.index_select(0, idx).contiguous()
+            net.zero_grad()
+            l = net.loss_and_grad(xb, yb)
+            acc += l[0]
+            cur_lr = lr * 0.5 * (1 + math.cos(math.pi * it / total))
+            net.adam_step(cur_lr)
+            it += 1
+        losses.append(float(acc.item()) / steps_per_epoch)
+        if log:
+            log(f"epoch {ep} loss {losses[-1]:.4e}")
+    return losses
+
+
+def predict(net, X, batch=8):
+    import torch
+
+    out = []
+    for s in range(0, X.shape[0], batch):
+        xb = X[s:s + batch].contiguous()
+        out.append(net.forward(xb).clone())
+    torch.cuda.synchronize()
+    return torch.cat(out).cpu().numpy()
+
+
+def compare(cold_steps, cold_res, cold_nu, cold_fields, cold_dt, warm_steps, warm_res, warm_nu, warm_fields, warm_dt,
+            pred, tol, dnu_tol):
+    """Cold against warm start.  The iteration decides: where both runs reach the
+    criterion their Nusselt numbers must agree within dnu_tol, else the instance falls
+    back to the cold start (its cost then counts both runs); a warm run that fails to
+    converge where the cold one converges also falls back."""
+    ok_c = cold_res <= tol
+    ok_w = (warm_res <= tol) & np.isfinite(warm_nu).all(axis=1)
+    dnu = np.abs(warm_nu - cold_nu).max(axis=1)
+    both = ok_c & ok_w
+    agree = both & (dnu <= dnu_tol)
+    fallback = (both & ~agree) | (ok_c & ~ok_w)
+    rel = []
+    for i in np.nonzero(both)[0]:
+        g, c = warm_fields[i], cold_fields[i]
+        rel.append(max(np.linalg.norm(g[3] - c[3]) / np.linalg.norm(c[3]),
+                       np.linalg.norm(np.stack(g[1:3]) - np.stack(c[1:3])) / max(np.linalg.norm(np.stack(c[1:3])), 1e-30)))
+    Yc = np.stack([targets_from_fields(f[1], f[2], f[3]) for f in cold_fields])
+    steps_w = np.where(fallback, warm_steps + cold_steps, warm_steps)
+    return {
+        "cold": {"s": round(cold_dt, 2), "converged": int(ok_c.sum()), "steps_median": int(np.median(cold_steps))},
+        "warm": {"s": round(warm_dt, 2), "converged": int(ok_w.sum()), "steps_median": int(np.median(warm_steps)),
+                 "fallback_to_cold": int(fallback.sum()), "converged_only_warm": int((ok_w & ~ok_c).sum())},
+        "both_converged": {
+            "instances": int(both.sum()), "agree_within_dNu_tol": int(agree.sum()),
+            "cold_steps_median": int(np.median(cold_steps[both])) if both.any() else None,
+            "warm_steps_median": int(np.median(steps_w[both])) if both.any() else None,
+            "steps_ratio_cold_over_warm": round(float(cold_steps[both].sum()) / max(float(steps_w[both].sum()), 1.0), 3)
+            if both.any() else None,
+            "max_abs_dNu": float(dnu[both].max()) if both.any() else None,
+            "max_rel_l2_fields": float(max(rel)) if rel else None},
+        "batch_time_ratio_cold_over_warm": round(cold_dt / warm_dt, 3) if warm_dt > 0 else None,
+        "start_field_rms_error": {"trained_network": float(np.sqrt(((pred - Yc) ** 2).mean())),
+                                  "rest_state": float(np.sqrt((Yc ** 2).mean()))},
+    }
+
+
+def main():
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nr", type=int, default=128)
+    ap.add_argument("--nz", type=int, default=256)
+    ap.add_argument("--ntrain", type=int, default=2000)
+    ap.add_argument("--nheld", type=int, default=256)
+    ap.add_argument("--max-steps", type=int, default=200000)
+    ap.add_argument("--check", type=int, default=1000)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--width", type=int, default=32)
+    ap.add_argument("--modes", type=int, default=16)
+    ap.add_argument("--dnu-tol", type=float, default=1e-3)
+    ap.add_argument("--held-max-steps", type=int, default=400000)
+    ap.add_argument("--verbose", action="store_true")
+    a = ap.parse_args()
+    log = (lambda s: print(s, flush=True)) if a.verbose else None
+    nr, nz = a.nr, a.nz
+    out = {"workload": f"warm start, {nr}x{nz} annulus, sweep parameter ranges, smoothed porosity (sigma 8)",
+           "ntrain": a.ntrain, "nheld": a.nheld, "criterion": f"interval residual <= {a.tol:g}",
+           "max_steps": a.max_steps}
+    t0 = time.perf_counter()
+    train_inst = make_instances(a.ntrain, 40000, nr, nz)
+    held = make_instances(a.nheld, 50000, nr, nz)
+    steps, res, nu, fields, dt = run_batch(train_inst, a.max_steps, a.check, a.tol)
+    out["data_generation_s"] = round(dt, 2)
+    out["train_converged"] = int((res <= a.tol).sum())
+    Y = np.stack([targets_from_fields(f[1], f[2], f[3]) for f in fields])
+    X = features(train_inst, nr, nz)
+    Xd, Yd = torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda")
+    net = F.FNO2d(nr, nz, width=a.width, modes=a.modes, seed=1)
+    t1 = time.perf_counter()
+    losses = train(net, Xd, Yd, a.epochs, a.batch, a.lr, log=log)
+    torch.cuda.synchronize()
+    out["train_s"] = round(time.perf_counter() - t1, 2)
+    out["train_loss_first_last"] = [losses[0], losses[-1]]
+    Xh = torch.tensor(features(held, nr, nz), device="cuda")
+    pred = predict(net, Xh)
+    warm = fields_from_targets(pred)
+    hm = a.held_max_steps
+    cold_steps, cold_res, cold_nu, cold_fields, cold_dt = run_batch(held, hm, a.check, a.tol)
+    warm_steps, warm_res, warm_nu, warm_fields, warm_dt = run_batch(held, hm, a.check, a.tol, warm=warm)
+    out.update(compare(cold_steps, cold_res, cold_nu, cold_fields, cold_dt, warm_steps, warm_res, warm_nu,
+                       warm_fields, warm_dt, pred, a.tol, a.dnu_tol))
+    out["held_max_steps"] = hm
+    out.update({
+        "total_s": round(time.perf_counter() - t0, 1),
+    })
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

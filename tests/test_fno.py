@@ -1,0 +1,92 @@
+"""Warm-start network: the GPU kernels (BF16 tensor-core GEMM, FP32 accumulation)
+against FP64 references.  GEMM against an FP64 matmul; the whole operator's output
+and every parameter gradient against the FP64 autograd oracle (oracle/fno_oracle.py),
+which evaluates the spectral layers with FFTs instead of DFT GEMMs."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fno():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1409_5929_gb300 import build, fno as F
+
+    build.build()
+    F.load()
+    return F
+
+
+def _bf16_tol(a, b):
+    """BF16 operands (8-bit significand): relative rounding 2^-9 per operand."""
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("shape", [(1, 64, 64, 32), (3, 77, 45, 130), (2, 300, 3, 8), (1, 5, 200, 513)])
+def test_gemm_against_fp64(fno, ta, tb, shape):
+    import torch
+
+    batch, M, N, K = shape
+    rng = np.random.default_rng(M * 7 + N)
+    A = rng.normal(size=(batch, K, M) if ta else (batch, M, K)).astype(np.float32)
+    B = rng.normal(size=(batch, N, K) if tb else (batch, K, N)).astype(np.float32)
+    C0 = rng.normal(size=(batch, M, N)).astype(np.float32)
+    bias = rng.normal(size=N).astype(np.float32)
+    Ad, Bd, Cd, bd = (torch.tensor(v, device="cuda") for v in (A, B, C0, bias))
+    lda = M if ta else K
+    ldb = K if tb else N
+    fno.fno_gemm(ta, tb, M, N, K, 0.5, Ad, lda, A[0].size, Bd, ldb, B[0].size, 2.0, Cd, N, M * N, batch, bias=bd)
+    torch.cuda.synchronize()
+    opA = np.swapaxes(A, 1, 2) if ta else A
+    opB = np.swapaxes(B, 1, 2) if tb else B
+    ref = 0.5 * np.einsum("bmk,bkn->bmn", opA.astype(np.float64), opB.astype(np.float64)) + 2.0 * C0 + bias
+    # bound: |sum a b| error <= K * 2 * 2^-9 * max|a b| per element; L2-relative check
+    assert _bf16_tol(Cd.cpu().numpy(), ref) < 2e-2
+
+
+def test_operator_and_gradients_against_fp64_oracle(fno):
+    import torch
+
+    from oracle import fno_oracle
+
+    nr, nz, width, modes, layers, hidden = 16, 32, 8, 4, 4, 16
+    P = fno.init_params(nr, nz, width, modes, layers, in_ch=8, out_ch=3, hidden=hidden, seed=3)
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(2, nr, nz, 8)).astype(np.float32)
+    t = rng.normal(size=(2, nr, nz, 3)).astype(np.float32)
+    # larger spectral weights so the spectral path carries a visible share of the output
+    for l in range(layers):
+        P[f"R{l}"] = (P[f"R{l}"] * width).astype(np.float32)
+    net = fno.FNO2d(nr, nz, width, modes, layers, 8, 3, hidden, params=P)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    net.zero_grad()
+    loss = net.loss_and_grad(xd, td)
+    torch.cuda.synchronize()
+    y_ref, loss_ref, g_ref = fno_oracle.loss_and_grads(P, x, t, modes, layers)
+    y = net._buf["y"].cpu().numpy()
+    assert _bf16_tol(y, y_ref) < 2e-2
+    assert abs(float(loss.item()) - loss_ref) < 2e-2 * loss_ref
+    for k in P:
+        g = net.g[k].cpu().numpy()
+        assert _bf16_tol(g, g_ref[k]) < 5e-2, (k, _bf16_tol(g, g_ref[k]))
+
+
+def test_adam_step_matches_formula(fno):
+    import torch
+
+    rng = np.random.default_rng(1)
+    w, g = rng.normal(size=100).astype(np.float32), rng.normal(size=100).astype(np.float32)
+    m, v = np.zeros(100, np.float32), np.zeros(100, np.float32)
+    wd, gd, md, vd = (torch.tensor(a, device="cuda") for a in (w, g, m, v))
+    for step in (1, 2):
+        fno.fno_adam(wd, gd, md, vd, 1e-2, 0.9, 0.999, 1e-8, step)
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g * g
+        w = w - 1e-2 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
+    torch.cuda.synchronize()
+    assert np.allclose(wd.cpu().numpy(), w, rtol=1e-5, atol=1e-6)
