@@ -62,6 +62,13 @@ int fno_mse(const float *y, const float *t, float *dy, double *loss, int64_t n, 
 int fno_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, float beta1, float beta2, float eps,
              int t, void *stream);
 
+/* Tensor-core path of fno_gemm: 0 = mma.sync m16n8k16 (default), 1 = tcgen05.mma with
+ * the accumulator in tensor memory (128 x N tiles, N <= 256 per CTA).  Process-wide. */
+int fno_set_tensor_path(int path);
+/* 1 if a tcgen05 GEMM gave up a bounded wait since the last clear (its output is then
+ * invalid), 0 otherwise, -1 on a CUDA error; clear = 1 resets the flag.  Synchronous. */
+int fno_tensor_path_status(int clear);
+
 const char *fno_last_error(void);
 
 #ifdef __cplusplus

@@ -132,6 +132,188 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, float alpha, 
             }
 }
 
+
+// ------------------------------------------------------- tcgen05 GEMM path --
+// One CTA (four warps) computes a 128 x ntile tile of C (ntile <= 256, a multiple of
+// 16) on the 5th-generation tensor cores: operands are staged from FP32 global memory
+// as BF16 into shared memory in the canonical K-major layout without swizzle (core
+// matrices of 8 rows x 16 bytes; LBO = 128 B between core matrices along K, SBO =
+// 1024 B between 8-row groups for a 64-wide K chunk), thread 0 issues four
+// tcgen05.mma (K = 16 each) per chunk into an FP32 accumulator in tensor memory and
+// commits them to an mbarrier, and each warp reads its 32 accumulator lanes back with
+// tcgen05.ld.  Every wait is bounded: on timeout the kernel records an error, waits
+// once more (bounded) for the tensor core, frees its tensor memory and returns.
+constexpr int TC_BM = 128, TC_BK = 64;
+__device__ int g_tc_error;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    const uint64_t lbo = 128, sbo = 1024;
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// byte offset of element (row, k) of a [rows x 64] K-major tile in the canonical layout
+__device__ __forceinline__ uint32_t tc_off(int row, int k) {
+    return (uint32_t)((((row >> 3) * 8 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile, float alpha,
+                                                 const float* __restrict__ A, int64_t lda, int64_t sA,
+                                                 const float* __restrict__ B, int64_t ldb, int64_t sB, float beta,
+                                                 float* __restrict__ C, int64_t ldc, int64_t sC,
+                                                 const float* __restrict__ bias) {
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_sh;
+    uint8_t* As = tc_smem;
+    uint8_t* Bs = tc_smem + TC_BM * TC_BK * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * ntile;
+    A += (int64_t)blockIdx.z * sA;
+    B += (int64_t)blockIdx.z * sB;
+    C += (int64_t)blockIdx.z * sC;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)ntile) ncols <<= 1;
+    const uint32_t mbar_a = smem_u32(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_sh;
+    // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, N, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = 0; k0 < K && ok; k0 += TC_BK) {
+        for (int i = tid; i < TC_BM * TC_BK; i += 128) {
+            int m, k;
+            if (TA) { k = i / TC_BM; m = i % TC_BM; } else { m = i / TC_BK; k = i % TC_BK; }
+            const int gm = m0 + m, gk = k0 + k;
+            float v = 0.f;
+            if (gm < M && gk < K) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
+            *reinterpret_cast<__nv_bfloat16*>(As + tc_off(m, k)) = __float2bfloat16_rn(v);
+        }
+        for (int i = tid; i < ntile * TC_BK; i += 128) {
+            int n, k;
+            if (TB) { n = i / TC_BK; k = i % TC_BK; } else { k = i / ntile; n = i % ntile; }
+            const int gn = n0 + n, gk = k0 + k;
+            float v = 0.f;
+            if (gn < N && gk < K) v = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
+            *reinterpret_cast<__nv_bfloat16*>(Bs + tc_off(n, k)) = __float2bfloat16_rn(v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < TC_BK / 16; ++j) {
+                const uint64_t ad = tc_desc(smem_u32(As) + j * 256), bd = tc_desc(smem_u32(Bs) + j * 256);
+                const uint32_t acc = (k0 > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+                         : "memory");
+        }
+        ok = tc_wait(mbar_a, phase);
+        phase ^= 1;
+        __syncthreads();
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_tc_error, 1);
+        tc_wait(mbar_a, phase ^ 1);   // one more bounded wait for the tensor core
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = m0 + warp * 32 + lane;
+        for (int c = 0; c < ntile; c += 8) {
+            uint32_t r[8];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                           "=r"(r[7])
+                         : "r"(taddr)
+                         : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int col = n0 + c + q;
+                    if (col < N && c + q < ntile) {
+                        float* cp = C + (int64_t)row * ldc + col;
+                        float v = alpha * __uint_as_float(r[q]);
+                        if (beta != 0.f) v += beta * *cp;
+                        if (bias) v += bias[col];
+                        *cp = v;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+static int g_tc_path = 0;   // 1: route fno_gemm through the tcgen05 kernel
+
+static int gemm_tc(int transA, int transB, int M, int N, int K, float alpha, const float* A, int64_t lda,
+                   int64_t strideA, const float* B, int64_t ldb, int64_t strideB, float beta, float* C, int64_t ldc,
+                   int64_t strideC, int batch, const float* bias, cudaStream_t s) {
+    int ntile = ((N + 15) / 16) * 16;
+    if (ntile > 256) ntile = 256;
+    const dim3 grid((unsigned)((N + ntile - 1) / ntile), (unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)batch);
+    if (grid.y > 65535) return fno_fail(FNO_ERR_INVALID, "GEMM grid too large");
+    const size_t smem = (size_t)(TC_BM + ntile) * TC_BK * 2;
+    static bool attr_done = false;
+    if (!attr_done) {
+        const int lim = (TC_BM + 256) * TC_BK * 2;
+        FCK(cudaFuncSetAttribute(k_gemm_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        attr_done = true;
+    }
+    if (!transA && !transB)
+        k_gemm_tc<false, false><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
+    else if (!transA && transB)
+        k_gemm_tc<false, true><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
+    else if (transA && !transB)
+        k_gemm_tc<true, false><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
+    else
+        k_gemm_tc<true, true><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
+    FCK(cudaGetLastError());
+    return FNO_OK;
+}
+
 // ---------------------------------------------------------------- elementwise --
 __global__ void k_gelu_fwd(const float* __restrict__ x, float* __restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -286,6 +468,9 @@ int fno_gemm(int transA, int transB, int M, int N, int K, float alpha, const flo
     if (M < 0 || N < 0 || K < 0 || batch < 0 || !A || !B || !C) return fno_fail(FNO_ERR_INVALID, "bad GEMM argument");
     if (M == 0 || N == 0 || batch == 0) return FNO_OK;
     if (batch > 65535 || (M + GBM - 1) / GBM > 65535) return fno_fail(FNO_ERR_INVALID, "GEMM grid too large");
+    if (g_tc_path)
+        return gemm_tc(transA, transB, M, N, K, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, batch,
+                       bias, (cudaStream_t)stream);
     const dim3 grid((unsigned)((N + GBN - 1) / GBN), (unsigned)((M + GBM - 1) / GBM), (unsigned)batch);
     cudaStream_t s = (cudaStream_t)stream;
     if (!transA && !transB)
@@ -364,6 +549,22 @@ int fno_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr, 
     k_adam<<<grid1d(n, 256), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, n, lr, beta1, beta2, eps, c1, c2);
     FCK(cudaGetLastError());
     return FNO_OK;
+}
+
+int fno_set_tensor_path(int path) {
+    if (path != 0 && path != 1) return fno_fail(FNO_ERR_INVALID, "path must be 0 (mma.sync) or 1 (tcgen05)");
+    g_tc_path = path;
+    return FNO_OK;
+}
+
+int fno_tensor_path_status(int clear) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess) return -1;
+    if (clear) {
+        const int z = 0;
+        if (cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int)) != cudaSuccess) return -1;
+    }
+    return v;
 }
 
 const char* fno_last_error(void) { return g_fno_err.c_str(); }

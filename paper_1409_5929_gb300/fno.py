@@ -40,6 +40,8 @@ _SIGS = {
     "fno_colsum": [_vp, _i64, C.c_int, _i64, _vp, C.c_int, _vp],
     "fno_mse": [_vp, _vp, _vp, _vp, _i64, _vp],
     "fno_adam": [_vp, _vp, _vp, _vp, _i64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, _vp],
+    "fno_set_tensor_path": [C.c_int],
+    "fno_tensor_path_status": [C.c_int],
 }
 
 
@@ -113,6 +115,15 @@ def fno_mse(y, t, dy, loss):
 def fno_adam(w, g, m, v, lr, b1, b2, eps, step):
     _check(load().fno_adam(_p(w), _p(g), _p(m), _p(v), w.numel(), float(lr), float(b1), float(b2), float(eps),
                            int(step), _stream()))
+
+
+def fno_set_tensor_path(path: int):
+    """0: mma.sync m16n8k16; 1: tcgen05.mma with the accumulator in tensor memory."""
+    _check(load().fno_set_tensor_path(int(path)))
+
+
+def fno_tensor_path_status(clear: bool = True) -> int:
+    return int(load().fno_tensor_path_status(int(clear)))
 
 
 # ---- the operator -------------------------------------------------------------

@@ -26,11 +26,15 @@ def _bf16_tol(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
-@pytest.mark.parametrize("shape", [(1, 64, 64, 32), (3, 77, 45, 130), (2, 300, 3, 8), (1, 5, 200, 513)])
-def test_gemm_against_fp64(fno, ta, tb, shape):
+@pytest.mark.parametrize("shape", [(1, 64, 64, 32), (3, 77, 45, 130), (2, 300, 3, 8), (1, 5, 200, 513),
+                                   (1, 1000, 300, 96)])
+def test_gemm_against_fp64(fno, path, ta, tb, shape):
+    """Both tensor-core paths: mma.sync (0) and tcgen05 with a tensor-memory accumulator (1)."""
     import torch
 
+    fno.fno_set_tensor_path(path)
     batch, M, N, K = shape
     rng = np.random.default_rng(M * 7 + N)
     A = rng.normal(size=(batch, K, M) if ta else (batch, M, K)).astype(np.float32)
@@ -46,10 +50,14 @@ def test_gemm_against_fp64(fno, ta, tb, shape):
     opB = np.swapaxes(B, 1, 2) if tb else B
     ref = 0.5 * np.einsum("bmk,bkn->bmn", opA.astype(np.float64), opB.astype(np.float64)) + 2.0 * C0 + bias
     # bound: |sum a b| error <= K * 2 * 2^-9 * max|a b| per element; L2-relative check
-    assert _bf16_tol(Cd.cpu().numpy(), ref) < 2e-2
+    got = Cd.cpu().numpy()
+    fno.fno_set_tensor_path(0)
+    assert fno.fno_tensor_path_status(True) == 0
+    assert _bf16_tol(got, ref) < 2e-2
 
 
-def test_operator_and_gradients_against_fp64_oracle(fno):
+@pytest.mark.parametrize("path", [0, 1])
+def test_operator_and_gradients_against_fp64_oracle(fno, path):
     import torch
 
     from oracle import fno_oracle
@@ -62,6 +70,7 @@ def test_operator_and_gradients_against_fp64_oracle(fno):
     # larger spectral weights so the spectral path carries a visible share of the output
     for l in range(layers):
         P[f"R{l}"] = (P[f"R{l}"] * width).astype(np.float32)
+    fno.fno_set_tensor_path(path)
     net = fno.FNO2d(nr, nz, width, modes, layers, 8, 3, hidden, params=P)
     xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
     net.zero_grad()
@@ -71,6 +80,8 @@ def test_operator_and_gradients_against_fp64_oracle(fno):
     y = net._buf["y"].cpu().numpy()
     assert _bf16_tol(y, y_ref) < 2e-2
     assert abs(float(loss.item()) - loss_ref) < 2e-2 * loss_ref
+    fno.fno_set_tensor_path(0)
+    assert fno.fno_tensor_path_status(True) == 0
     for k in P:
         g = net.g[k].cpu().numpy()
         assert _bf16_tol(g, g_ref[k]) < 5e-2, (k, _bf16_tol(g, g_ref[k]))
