@@ -93,6 +93,42 @@ def run_batch(inst, max_steps, check, tol, warm=None):
     return steps, res, nu, fields, dt
 
 
+def nu_trajectory(inst, total, chunk, warm=None):
+    """Advance every instance `total` steps (batched, graph-replayed chunks, no early
+    stop) and record both Nusselt numbers after each chunk: [nchunks, n, 2]."""
+    import torch
+
+    b = lbm.Batch([p for p, _, _ in inst])
+    for i, (p, phi, _) in enumerate(inst):
+        b.set_porosity(i, phi)
+        if warm is None:
+            b.init_fields(i)
+        else:
+            b.init_fields(i, warm[0][i], warm[1][i], warm[2][i])
+    torch.cuda.synchronize()
+    traj, done = [], 0
+    t0 = time.perf_counter()
+    while done < total:
+        b.run(chunk, chunk, -1.0)
+        done += chunk
+        traj.append(np.stack(b.nusselt(), axis=1))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    fields = [b.moments(i) for i in range(len(inst))]
+    b.close()
+    return np.stack(traj), dt, fields
+
+
+def steps_to_nu(traj, ref, tol, chunk):
+    """First step count after which |Nu - ref| <= tol (both walls) holds to the end of the
+    trajectory; -1 where it never settles."""
+    err = np.abs(traj - ref[None]).max(axis=2)          # [nchunks, n]
+    ok = err <= tol
+    settled = np.flip(np.logical_and.accumulate(np.flip(ok, 0), 0), 0)   # ok from t to the end
+    first = np.where(settled.any(0), settled.argmax(0), -1)
+    return np.where(first >= 0, (first + 1) * chunk, -1)
+
+
 def train(net, X, Y, epochs, batch, lr, seed=0, log=None):
     import torch
 
@@ -186,10 +222,8 @@ def main():
     ap.add_argument("--width", type=int, default=32)
     ap.add_argument("--modes", type=int, default=16)
     ap.add_argument("--dnu-tol", type=float, default=1e-3)
-    ap.add_argument("--held-max-steps", type=int, default=1000000)
-    ap.add_argument("--held-tol", type=float, default=1e-10,
-                    help="criterion of the cold/warm comparison (tighter than the data's, so that the stopping "
-                         "distance to the steady state stays below the Nusselt tolerance)")
+    ap.add_argument("--held-max-steps", type=int, default=800000)
+    ap.add_argument("--nu-chunk", type=int, default=5000)
     ap.add_argument("--verbose", action="store_true")
     a = ap.parse_args()
     log = (lambda s: print(s, flush=True)) if a.verbose else None
@@ -215,14 +249,42 @@ def main():
     Xh = torch.tensor(features(held, nr, nz), device="cuda")
     pred = predict(net, Xh)
     warm = fields_from_targets(pred)
-    hm = a.held_max_steps
-    cold_steps, cold_res, cold_nu, cold_fields, cold_dt = run_batch(held, hm, a.check, a.held_tol)
-    warm_steps, warm_res, warm_nu, warm_fields, warm_dt = run_batch(held, hm, a.check, a.held_tol, warm=warm)
-    out.update(compare(cold_steps, cold_res, cold_nu, cold_fields, cold_dt, warm_steps, warm_res, warm_nu,
-                       warm_fields, warm_dt, pred, a.held_tol, a.dnu_tol))
-    out["held_max_steps"] = hm
-    out["held_criterion"] = f"interval residual <= {a.held_tol:g}"
+    hm, ch = a.held_max_steps, a.nu_chunk
+    traj_c, dt_c, f_c = nu_trajectory(held, hm, ch)
+    traj_w, dt_w, f_w = nu_trajectory(held, hm, ch, warm=warm)
+    ref = traj_c[-1]                                    # cold start, end of the long run
+    s_c = steps_to_nu(traj_c, ref, a.dnu_tol, ch)
+    s_w = steps_to_nu(traj_w, ref, a.dnu_tol, ch)
+    agree = np.abs(traj_w[-1] - ref).max(axis=1) <= a.dnu_tol
+    both = (s_c > 0) & (s_w > 0) & agree
+    # fallback: a warm run that ends away from the cold answer is replaced by the cold run
+    s_w_fb = np.where(agree, s_w, hm + s_c)
+    rel = [max(np.linalg.norm(f_w[i][3] - f_c[i][3]) / np.linalg.norm(f_c[i][3]),
+               np.linalg.norm(np.stack(f_w[i][1:3]) - np.stack(f_c[i][1:3]))
+               / max(np.linalg.norm(np.stack(f_c[i][1:3])), 1e-30)) for i in np.nonzero(agree)[0]]
+    Yc = np.stack([targets_from_fields(f[1], f[2], f[3]) for f in f_c])
+    ms_step = dt_c / hm * 1e3
     out.update({
+        "time_to_steady_definition": f"steps until |Nu - Nu_ref| <= {a.dnu_tol:g} on both walls for the rest "
+                                     f"of a {hm}-step run; Nu_ref = cold start at {hm} steps; checked every {ch}",
+        "batched_ms_per_step": round(ms_step, 4),
+        "cold": {"settled": int((s_c > 0).sum()), "steps_median": int(np.median(s_c[s_c > 0])) if (s_c > 0).any() else None},
+        "warm": {"settled": int((s_w > 0).sum()), "agree_with_cold_at_end": int(agree.sum()),
+                 "fallback_to_cold": int((~agree).sum()),
+                 "steps_median": int(np.median(s_w[s_w > 0])) if (s_w > 0).any() else None},
+        "both_settled": {"instances": int(both.sum()),
+                         "cold_steps_median": int(np.median(s_c[both])) if both.any() else None,
+                         "warm_steps_median": int(np.median(s_w[both])) if both.any() else None,
+                         "steps_ratio_cold_over_warm": round(float(s_c[both].sum()) / float(s_w[both].sum()), 3)
+                         if both.any() else None,
+                         "time_to_steady_cold_s": round(float(s_c[both].max()) * ms_step / 1e3, 2) if both.any() else None,
+                         "time_to_steady_warm_s": round(float(s_w[both].max()) * ms_step / 1e3, 2) if both.any() else None},
+        "all_instances_steps_ratio_with_fallback": round(float(np.where(s_c > 0, s_c, hm).sum())
+                                                         / float(np.where(s_w_fb > 0, s_w_fb, hm).sum()), 3),
+        "max_rel_l2_fields_warm_vs_cold_at_end": float(max(rel)) if rel else None,
+        "start_field_rms_error": {"trained_network": float(np.sqrt(((pred - Yc) ** 2).mean())),
+                                  "rest_state": float(np.sqrt((Yc ** 2).mean()))},
+        "held_steps": hm,
         "total_s": round(time.perf_counter() - t0, 1),
     })
     print(json.dumps(out), flush=True)
