@@ -240,9 +240,11 @@ int lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t check_every, double t
 int lbm_batch_nusselt(lbm_batch *b, double *nu_inner, double *nu_outer);
 /* Fields of instance i, as lbm_moments. */
 int lbm_batch_moments(lbm_batch *b, int32_t i, float *rho, float *ur, float *uz, float *T, int on_device);
-/* Autotuner: times `steps` steps for each bulk block shape (columns x rows per block:
- * 64x1, 128x1, 256x1, 64x2, 128x2, 64x4, 32x8) and keeps the fastest; returns it and
- * its time per step.  The state advances by the steps the tuning ran. */
+/* Autotuner: times `steps` steps for each bulk tile shape (columns x rows per block x
+ * rows per thread; twelve shapes of at most 256 threads) and keeps the fastest; *cols and
+ * *rows receive the tile's columns and rows, *ms_per_step its time per step.  The state
+ * advances by the steps the tuning ran (2 warm-up steps + `steps` per shape; the batch's
+ * step count in lbm_batch_get_info includes them). */
 int lbm_batch_tune(lbm_batch *b, int32_t steps, int32_t *cols, int32_t *rows, float *ms_per_step);
 /* Derived constants of instance i; steps = steps taken by the batch. */
 int lbm_batch_get_info(lbm_batch *b, int32_t i, lbm_info *out);

@@ -65,6 +65,15 @@ static size_t phi_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
 static size_t state_bytes(int sto, int64_t plane) { return (size_t)plane * (9 * f_size(sto) + 5 * g_size(sto)); }
 
 constexpr int BULK_THREADS = 128;
+#ifndef LBM_BULK_RPT
+#define LBM_BULK_RPT 4
+#endif
+constexpr int BULK_RPT = LBM_BULK_RPT;  // rows per thread of the bulk kernel (32-bit indexing)
+#ifndef LBM_BULK_RPT_MIN_BLOCKS
+#define LBM_BULK_RPT_MIN_BLOCKS 16
+#endif
+// BULK_RPT rows per thread only where the grid keeps at least this many blocks per SM
+constexpr int BULK_RPT_MIN_BLOCKS = LBM_BULK_RPT_MIN_BLOCKS;
 
 // ------------------------------------------------------------- pull (Eq. 22) --
 // Pre-collision deviations at (kr, kz) from the post-collision buffer A: a plain
@@ -153,24 +162,40 @@ static int wall_count(int geometry, int nr, int nz) {
 }
 
 // ------------------------------------------------------------------ kernels --
-// I: index type; 32-bit when the state buffer holds fewer than 2^31 elements.
+// Update `rows` consecutive non-wall nodes of column kz from row kr0 on (rows past the
+// last row are skipped); shared by the single-problem and the batched bulk kernels.
+// I: index type.
 template <int STO, typename I>
+__device__ __forceinline__ void update_column(const Consts<float>& c, const Buf<STO>& A, const Buf<STO>& B,
+                                              const typename St<STO>::P* __restrict__ phi, I plane, int kr0,
+                                              int rows, int kz) {
+#pragma unroll 1
+    for (int j = 0; j < rows; ++j) {
+        const int kr = kr0 + j;
+        if (kr >= c.nr) break;
+        if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) continue;
+        float fh[9], gh[5];
+        pull<STO, float, I>(c, A, plane, kr, kz, fh, gh);
+        const I n = (I)kr * c.nz + kz;
+        const float r = c.r0 + float(kr), inv_r = rcp_acc(r);
+        const float ph = ldv(phi + n);
+        float m0, rho, ur, uz, dT, lin, nl, iph;
+        porous(c, ph, lin, nl, iph);
+        recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+        collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
+        store<STO, float, I>(B, plane, n, fh, gh);
+    }
+}
+
+// One thread per column segment of RPT rows: the column's index arithmetic, the
+// kernel-argument loads and the class checks are shared by RPT nodes.
+// I: index type; 32-bit when the state buffer holds fewer than 2^31 elements.
+template <int STO, typename I, int RPT>
 __global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
                                                        const typename St<STO>::P* __restrict__ phi, I plane) {
     const int kz = blockIdx.x * BULK_THREADS + threadIdx.x;
-    const int kr = blockIdx.y;
     if (kz >= c.nz) return;
-    if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) return;
-    float fh[9], gh[5];
-    pull<STO, float, I>(c, A, plane, kr, kz, fh, gh);
-    const I n = (I)kr * c.nz + kz;
-    const float r = c.r0 + float(kr), inv_r = rcp_acc(r);
-    const float ph = ldv(phi + n);
-    float m0, rho, ur, uz, dT, lin, nl, iph;
-    porous(c, ph, lin, nl, iph);
-    recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
-    collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
-    store<STO, float, I>(B, plane, n, fh, gh);
+    update_column<STO, I>(c, A, B, phi, plane, blockIdx.y * RPT, RPT, kz);
 }
 
 template <int STO>
@@ -471,6 +496,7 @@ struct lbm_handle {
     Consts<float> cf;
     Consts<double> cd;
     int device = 0;
+    int sms = 0;             // multiprocessors of the device
     cudaStream_t stream = nullptr;
     int64_t plane = 0;       // elements per plane (padded)
     int64_t N = 0;           // nr * nz
@@ -592,6 +618,13 @@ static dim3 grid2d(const lbm_handle* h, int threads) {
         case LBM_F16: { constexpr int S_ = LBM_F16; __VA_ARGS__; } break;  \
         default: { constexpr int S_ = LBM_BF16; __VA_ARGS__; } break;      \
     }
+// rows per thread of the batched kernels: 1, 2 or 4 (the values the tuner tries)
+#define DISPATCH_RPT(rpt, ...)                                             \
+    switch (rpt) {                                                         \
+        case 4: { constexpr int R_ = 4; __VA_ARGS__; } break;              \
+        case 2: { constexpr int R_ = 2; __VA_ARGS__; } break;              \
+        default: { constexpr int R_ = 1; __VA_ARGS__; } break;             \
+    }
 
 template <int STO> static Buf<STO> bufp(const lbm_handle* h, int which) {
     Buf<STO> b;
@@ -671,6 +704,8 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     h->cf = to_float(h->cd);
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) { delete h; return fail(LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
+    e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { delete h; return fail(LBM_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); }
     h->N = (int64_t)p->nr * p->nz;
     h->plane = (h->N + 63) / 64 * 64;
     h->mstride = h->plane;
@@ -769,7 +804,6 @@ int lbm_init_fields(lbm_handle* h, const float* ur, const float* uz, const float
 }
 
 static int launch_step(lbm_handle* h) {
-    const dim3 g = grid2d(h, BULK_THREADS);
     const int nw = wall_count(h->p.geometry, h->p.nr, h->p.nz);
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (h->timing) {
@@ -778,16 +812,25 @@ static int launch_step(lbm_handle* h) {
         CK(cudaEventCreate(&e2));
         CK(cudaEventRecord(e0, h->stream));
     }
-    if (14 * h->plane < ((int64_t)1 << 31)) {
+    // BULK_RPT rows per thread where the grid keeps BULK_RPT_MIN_BLOCKS blocks per SM
+    // (9 blocks of 128 threads are resident per SM), else one row per thread so that small
+    // grids still fill the device
+    const bool i32 = 14 * h->plane < ((int64_t)1 << 31);
+    const int64_t zblocks = (h->p.nz + BULK_THREADS - 1) / BULK_THREADS;
+    const int rpt = (i32 && zblocks * ((h->p.nr + BULK_RPT - 1) / BULK_RPT) >= (int64_t)BULK_RPT_MIN_BLOCKS * h->sms) ? BULK_RPT : 1;
+    const dim3 gb((unsigned)((h->p.nz + BULK_THREADS - 1) / BULK_THREADS), (unsigned)((h->p.nr + rpt - 1) / rpt));
+    if (rpt > 1) {
         DISPATCH_STO(h->p.storage,
-                     k_bulk<S_, int><<<g, BULK_THREADS, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur),
-                                                                         bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi,
-                                                                         (int)h->plane));
+                     k_bulk<S_, int, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(
+                         h->cf, bufp<S_>(h, h->cur), bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi, (int)h->plane));
+    } else if (i32) {
+        DISPATCH_STO(h->p.storage,
+                     k_bulk<S_, int, 1><<<gb, BULK_THREADS, 0, h->stream>>>(
+                         h->cf, bufp<S_>(h, h->cur), bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi, (int)h->plane));
     } else {
         DISPATCH_STO(h->p.storage,
-                     k_bulk<S_, int64_t><<<g, BULK_THREADS, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur),
-                                                                             bufp<S_>(h, h->cur ^ 1),
-                                                                             (const PP<S_>*)h->phi, h->plane));
+                     k_bulk<S_, int64_t, 1><<<gb, BULK_THREADS, 0, h->stream>>>(
+                         h->cf, bufp<S_>(h, h->cur), bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi, h->plane));
     }
     CK(cudaGetLastError());
     if (h->timing) CK(cudaEventRecord(e1, h->stream));
@@ -1089,30 +1132,22 @@ __device__ __forceinline__ Buf<STO> inst_buf(const InstDesc& d, char* pool, int 
     return b;
 }
 
-// Tile = (instance, first row, first column); block = (bz, rows).
-template <int STO>
+// Tile = (instance, first row, first column); block = (bz, rows); each thread updates
+// RPT consecutive rows of its column (the instance descriptor is read once per thread).
+// The per-node arithmetic is the single-problem kernel's with the same RPT, so a batch
+// instance stepped with the single kernel's rows per thread follows it bit for bit.
+template <int STO, int RPT>
 __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__ desc, char* __restrict__ pool,
                                                     int parity, const int4* __restrict__ tiles) {
     const int4 t = tiles[blockIdx.x];
     const InstDesc& d = desc[t.x];
     const Consts<float> c = d.c;
     const int kz = t.z + threadIdx.x;
-    const int kr = t.y + threadIdx.y;
-    if (kz >= c.nz || kr >= c.nr) return;
-    if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) return;
+    if (kz >= c.nz) return;
     const Buf<STO> A = inst_buf<STO>(d, pool, parity), B = inst_buf<STO>(d, pool, parity ^ 1);
     const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
     const int plane = (int)d.plane;
-    float fh[9], gh[5];
-    pull<STO, float, int>(c, A, plane, kr, kz, fh, gh);
-    const int n = kr * c.nz + kz;
-    const float r = c.r0 + float(kr), inv_r = rcp_acc(r);
-    const float ph = ldv(phi + n);
-    float m0, rho, ur, uz, dT, lin, nl, iph;
-    porous(c, ph, lin, nl, iph);
-    recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
-    collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
-    store<STO, float, int>(B, plane, n, fh, gh);
+    update_column<STO, int>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
 }
 
 // Wall nodes of all active instances: prefix[k] = first wall thread of active instance k.
@@ -1150,7 +1185,7 @@ __global__ void k_batch_wall(const InstDesc* __restrict__ desc, char* __restrict
 }
 
 // Field snapshot `slot` (0 or 1) of every instance the tiles cover, all nodes.
-template <int STO>
+template <int STO, int RPT>
 __global__ void __launch_bounds__(256) k_batch_moments(const InstDesc* __restrict__ desc, char* __restrict__ pool,
                                                        float* __restrict__ macpool, int parity, int slot,
                                                        const int4* __restrict__ tiles) {
@@ -1158,27 +1193,31 @@ __global__ void __launch_bounds__(256) k_batch_moments(const InstDesc* __restric
     const InstDesc& d = desc[t.x];
     const Consts<float> c = d.c;
     const int kz = t.z + threadIdx.x;
-    const int kr = t.y + threadIdx.y;
-    if (kz >= c.nz || kr >= c.nr) return;
+    if (kz >= c.nz) return;
     const Buf<STO> A = inst_buf<STO>(d, pool, parity);
     const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
-    const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
-    const int64_t n = (int64_t)kr * c.nz + kz;
-    float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT;
-    if (is_wall(cls)) {
-        wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dT);
-    } else {
-        pull<STO>(c, A, d.plane, kr, kz, fh, gh);
-        const float r = c.r0 + float(kr), ph = ldv(phi + n);
-        float lin, nl, iph;
-        porous(c, ph, lin, nl, iph);
-        recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
-    }
     float* m = macpool + d.off_mac + (int64_t)slot * 4 * d.plane;
-    m[n] = rho;
-    m[d.plane + n] = ur;
-    m[2 * d.plane + n] = uz;
-    m[3 * d.plane + n] = c.T0 + dT;
+#pragma unroll 1
+    for (int j = 0; j < RPT; ++j) {
+        const int kr = t.y + threadIdx.y * RPT + j;
+        if (kr >= c.nr) break;
+        const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
+        const int64_t n = (int64_t)kr * c.nz + kz;
+        float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT;
+        if (is_wall(cls)) {
+            wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dT);
+        } else {
+            pull<STO>(c, A, d.plane, kr, kz, fh, gh);
+            const float r = c.r0 + float(kr), ph = ldv(phi + n);
+            float lin, nl, iph;
+            porous(c, ph, lin, nl, iph);
+            recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+        }
+        m[n] = rho;
+        m[d.plane + n] = ur;
+        m[2 * d.plane + n] = uz;
+        m[3 * d.plane + n] = c.T0 + dT;
+    }
 }
 
 // Per-instance residual sums between the two snapshots (cur = slot `cur`): grid
@@ -1268,7 +1307,7 @@ struct lbm_batch {
     int64_t steps = 0;
     std::vector<char> active;         // 1 = still stepping
     // tiles and wall lists of the active set
-    int bz = 128, rows = 1;           // bulk block shape
+    int bz = 128, rows = 1, rpt = 1;  // bulk block shape and rows per thread
     int4* d_tiles = nullptr;          // active instances, all rows
     int ntiles = 0;
     int* d_active = nullptr;
@@ -1301,7 +1340,7 @@ static int batch_rebuild(lbm_batch* b) {
         if (!b->active[i]) continue;
         act.push_back(i);
         prefix.push_back(prefix.back() + wall_count(b->p[i].geometry, b->p[i].nr, b->p[i].nz));
-        for (int kr = 0; kr < b->p[i].nr; kr += b->rows)
+        for (int kr = 0; kr < b->p[i].nr; kr += b->rows * b->rpt)
             for (int z0 = 0; z0 < b->p[i].nz; z0 += b->bz) tiles.push_back(make_int4(i, kr, z0, 0));
     }
     b->ntiles = (int)tiles.size();
@@ -1335,8 +1374,8 @@ template <int STO> static Buf<STO> batch_buf(const lbm_batch* b, int i, int whic
 static int batch_launch_step(lbm_batch* b) {
     if (!b->nactive) return LBM_OK;
     const dim3 blk(b->bz, b->rows);
-    DISPATCH_STO(b->storage, k_batch_bulk<S_><<<b->ntiles, blk, 0, b->stream>>>(b->d_desc, b->pool, b->parity,
-                                                                                 b->d_tiles));
+    DISPATCH_STO(b->storage, DISPATCH_RPT(b->rpt, k_batch_bulk<S_, R_><<<b->ntiles, blk, 0, b->stream>>>(
+                                                       b->d_desc, b->pool, b->parity, b->d_tiles)));
     CK(cudaGetLastError());
     DISPATCH_STO(b->storage, k_batch_wall<S_><<<(b->nwall + 127) / 128, 128, 0, b->stream>>>(
                                  b->d_desc, b->pool, b->parity, b->d_active, b->d_prefix, b->nactive));
@@ -1522,8 +1561,8 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 static int batch_snapshot(lbm_batch* b, int slot) {
     // moments use all rows of the active instances: the bulk tiles cover them
     const dim3 blk(b->bz, b->rows);
-    DISPATCH_STO(b->storage, k_batch_moments<S_><<<b->ntiles, blk, 0, b->stream>>>(b->d_desc, b->pool, b->macpool,
-                                                                                    b->parity, slot, b->d_tiles));
+    DISPATCH_STO(b->storage, DISPATCH_RPT(b->rpt, k_batch_moments<S_, R_><<<b->ntiles, blk, 0, b->stream>>>(
+                                                       b->d_desc, b->pool, b->macpool, b->parity, slot, b->d_tiles)));
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -1659,22 +1698,25 @@ int lbm_batch_moments(lbm_batch* b, int32_t i, float* rho, float* ur, float* uz,
     return LBM_OK;
 }
 
-// Autotuner: time `steps` batched steps for each bulk block shape (columns x rows
-// per block, at most 256 threads) and keep the fastest.  Leaves the state advanced
-// by the steps it ran.
+// Autotuner: time `steps` batched steps for each bulk tile shape (columns x rows per
+// block x rows per thread, at most 256 threads) and keep the fastest.  Leaves the state
+// advanced by the steps it ran (2 warm-up + `steps` per shape).
+static const int kTuneShapes[][3] = {{64, 1, 1}, {128, 1, 1}, {256, 1, 1}, {64, 2, 1}, {128, 2, 1}, {64, 4, 1},
+                                     {32, 8, 1}, {64, 1, 2}, {64, 1, 4}, {128, 1, 2}, {128, 1, 4}, {32, 4, 4}};
+
 int lbm_batch_tune(lbm_batch* b, int32_t steps, int32_t* bz_out, int32_t* rows_out, float* ms_out) {
     if (!b || steps < 1) return fail(LBM_ERR_INVALID, "bad batch or steps");
     CK(cudaSetDevice(b->device));
-    static const int shapes[][2] = {{64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2}, {64, 4}, {32, 8}};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = INFINITY;
-    int bb = b->bz, br = b->rows;
+    int bb = b->bz, br = b->rows, bt = b->rpt;
     int rc = LBM_OK;
-    for (const auto& s : shapes) {
+    for (const auto& s : kTuneShapes) {
         b->bz = s[0];
         b->rows = s[1];
+        b->rpt = s[2];
         if ((rc = batch_rebuild(b))) break;
         if ((rc = lbm_batch_step(b, 2))) break;   // warm-up
         cudaEventRecord(e0, b->stream);
@@ -1683,16 +1725,17 @@ int lbm_batch_tune(lbm_batch* b, int32_t steps, int32_t* bz_out, int32_t* rows_o
         cudaEventSynchronize(e1);
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; bb = s[0]; br = s[1]; }
+        if (ms < best) { best = ms; bb = s[0]; br = s[1]; bt = s[2]; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
     b->bz = bb;
     b->rows = br;
+    b->rpt = bt;
     if ((rc = batch_rebuild(b))) return rc;
     if (bz_out) *bz_out = bb;
-    if (rows_out) *rows_out = br;
+    if (rows_out) *rows_out = br * bt;
     if (ms_out) *ms_out = best / (float)steps;
     return LBM_OK;
 }

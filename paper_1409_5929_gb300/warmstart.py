@@ -11,9 +11,10 @@ in libfno.so):
      (porosity, five parameter planes, r, z) and outputs (u_r / U, u_z / U, 2 (T - T0) / dT
      with U = Ma c_s), MSE, Adam, BF16 tensor-core GEMMs with FP32 accumulation;
   4. warm start of held-out instances: the network's fields through lbm_init_fields,
-     then the iteration to the same criterion; it decides the result.  An instance whose
-     warm run diverges, or ends more than dNu_tol away from its cold-start Nusselt
-     numbers, falls back to the cold start.
+     then the same iteration from them, which decides the result; cold and warm runs
+     record their Nusselt numbers along a long run, and the steps each needs to come
+     within dNu_tol of the cold run's final values are compared on the instances where
+     both runs are stationary (summarize).
 
     python -m paper_1409_5929_gb300.warmstart [--ntrain 2000] [--nheld 256] ...
 prints one JSON line with the measurements.
@@ -129,6 +130,43 @@ def steps_to_nu(traj, ref, tol, chunk):
     return np.where(first >= 0, (first + 1) * chunk, -1)
 
 
+def summarize(traj_c, traj_w, chunk, tol, window, drift, groups=None):
+    """Time-to-steady comparison of cold and warm Nusselt trajectories [nchunks, n, 2]
+    recorded every `chunk` steps.
+
+    An instance is stationary when, over the last `window` steps, both runs' Nusselt
+    numbers stay within `drift` of their final values; only then does "time to steady" mean
+    something.  Among stationary instances, the warm run agrees when its final Nusselt
+    numbers are within `tol` of the cold run's; for those, steps to |Nu - Nu_cold,end| <= tol
+    (held to the end) are compared.  `groups` (optional, one label per instance) splits
+    the three counts by label."""
+    w = max(1, window // chunk)
+    ref = traj_c[-1]
+    d_c = np.abs(traj_c[-w:] - traj_c[-1][None]).max(axis=(0, 2))
+    d_w = np.abs(traj_w[-w:] - traj_w[-1][None]).max(axis=(0, 2))
+    stat = (d_c <= drift) & (d_w <= drift)
+    dnu = np.abs(traj_w[-1] - ref).max(axis=1)
+    agree = dnu <= tol
+    s_c = steps_to_nu(traj_c, ref, tol, chunk)
+    s_w = steps_to_nu(traj_w, ref, tol, chunk)
+    ok = stat & agree & (s_c > 0) & (s_w > 0)
+    dis = stat & ~agree
+    out = {"stationary": int(stat.sum()), "stationary_agree": int(ok.sum()),
+           "stationary_disagree": int(dis.sum()), "nonstationary": int((~stat).sum()),
+           "disagree_dNu_quantiles_50_90_max": [float(np.quantile(dnu[dis], q)) for q in (0.5, 0.9, 1.0)]
+           if dis.any() else None}
+    if ok.any():
+        out.update({"cold_steps_median": int(np.median(s_c[ok])), "warm_steps_median": int(np.median(s_w[ok])),
+                    "cold_steps_max": int(s_c[ok].max()), "warm_steps_max": int(s_w[ok].max()),
+                    "steps_ratio_cold_over_warm_sum": round(float(s_c[ok].sum()) / float(s_w[ok].sum()), 3)})
+    if groups is not None:
+        g = np.asarray(groups)
+        out["by_group"] = {str(v): {"stationary_agree": int((ok & (g == v)).sum()),
+                                    "stationary_disagree": int((dis & (g == v)).sum()),
+                                    "nonstationary": int((~stat & (g == v)).sum())} for v in np.unique(g)}
+    return out, ok
+
+
 def train(net, X, Y, epochs, batch, lr, seed=0, log=None):
     import torch
 
@@ -213,7 +251,7 @@ def main():
     ap.add_argument("--nz", type=int, default=256)
     ap.add_argument("--ntrain", type=int, default=2000)
     ap.add_argument("--nheld", type=int, default=256)
-    ap.add_argument("--max-steps", type=int, default=200000)
+    ap.add_argument("--max-steps", type=int, default=300000)
     ap.add_argument("--check", type=int, default=1000)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--epochs", type=int, default=40)
@@ -224,6 +262,9 @@ def main():
     ap.add_argument("--dnu-tol", type=float, default=1e-3)
     ap.add_argument("--held-max-steps", type=int, default=800000)
     ap.add_argument("--nu-chunk", type=int, default=5000)
+    ap.add_argument("--window", type=int, default=200000, help="stationarity window (steps)")
+    ap.add_argument("--drift", type=float, default=1e-4, help="stationarity bound on |Nu - Nu_end|")
+    ap.add_argument("--save", default="", help="write per-instance trajectories and parameters (npz) here")
     ap.add_argument("--verbose", action="store_true")
     a = ap.parse_args()
     log = (lambda s: print(s, flush=True)) if a.verbose else None
@@ -252,35 +293,28 @@ def main():
     hm, ch = a.held_max_steps, a.nu_chunk
     traj_c, dt_c, f_c = nu_trajectory(held, hm, ch)
     traj_w, dt_w, f_w = nu_trajectory(held, hm, ch, warm=warm)
-    ref = traj_c[-1]                                    # cold start, end of the long run
-    s_c = steps_to_nu(traj_c, ref, a.dnu_tol, ch)
-    s_w = steps_to_nu(traj_w, ref, a.dnu_tol, ch)
-    agree = np.abs(traj_w[-1] - ref).max(axis=1) <= a.dnu_tol
-    both = (s_c > 0) & (s_w > 0) & agree
-    # fallback: a warm run that ends away from the cold answer is replaced by the cold run
-    s_w_fb = np.where(agree, s_w, hm + s_c)
+    pr = np.array([d["Pr"] for _, _, d in held])
+    summ, ok = summarize(traj_c, traj_w, ch, a.dnu_tol, a.window, a.drift, groups=pr)
+    if a.save:
+        np.savez_compressed(a.save, traj_cold=traj_c, traj_warm=traj_w, chunk=ch,
+                            Ra=np.array([d["Ra"] for _, _, d in held]), Da=np.array([d["Da"] for _, _, d in held]),
+                            eps=np.array([d["eps"] for _, _, d in held]), Pr=pr,
+                            Rstar=np.array([d["radius_ratio"] for _, _, d in held]))
     rel = [max(np.linalg.norm(f_w[i][3] - f_c[i][3]) / np.linalg.norm(f_c[i][3]),
                np.linalg.norm(np.stack(f_w[i][1:3]) - np.stack(f_c[i][1:3]))
-               / max(np.linalg.norm(np.stack(f_c[i][1:3])), 1e-30)) for i in np.nonzero(agree)[0]]
+               / max(np.linalg.norm(np.stack(f_c[i][1:3])), 1e-30)) for i in np.nonzero(ok)[0]]
     Yc = np.stack([targets_from_fields(f[1], f[2], f[3]) for f in f_c])
     ms_step = dt_c / hm * 1e3
+    if ok.any():
+        summ["time_to_steady_cold_s"] = round(summ["cold_steps_max"] * ms_step / 1e3, 2)
+        summ["time_to_steady_warm_s"] = round(summ["warm_steps_max"] * ms_step / 1e3, 2)
     out.update({
         "time_to_steady_definition": f"steps until |Nu - Nu_ref| <= {a.dnu_tol:g} on both walls for the rest "
-                                     f"of a {hm}-step run; Nu_ref = cold start at {hm} steps; checked every {ch}",
+                                     f"of a {hm}-step run; Nu_ref = cold start at {hm} steps; checked every {ch}; "
+                                     f"stationary = both runs within {a.drift:g} of their final Nu over the last "
+                                     f"{a.window} steps",
         "batched_ms_per_step": round(ms_step, 4),
-        "cold": {"settled": int((s_c > 0).sum()), "steps_median": int(np.median(s_c[s_c > 0])) if (s_c > 0).any() else None},
-        "warm": {"settled": int((s_w > 0).sum()), "agree_with_cold_at_end": int(agree.sum()),
-                 "fallback_to_cold": int((~agree).sum()),
-                 "steps_median": int(np.median(s_w[s_w > 0])) if (s_w > 0).any() else None},
-        "both_settled": {"instances": int(both.sum()),
-                         "cold_steps_median": int(np.median(s_c[both])) if both.any() else None,
-                         "warm_steps_median": int(np.median(s_w[both])) if both.any() else None,
-                         "steps_ratio_cold_over_warm": round(float(s_c[both].sum()) / float(s_w[both].sum()), 3)
-                         if both.any() else None,
-                         "time_to_steady_cold_s": round(float(s_c[both].max()) * ms_step / 1e3, 2) if both.any() else None,
-                         "time_to_steady_warm_s": round(float(s_w[both].max()) * ms_step / 1e3, 2) if both.any() else None},
-        "all_instances_steps_ratio_with_fallback": round(float(np.where(s_c > 0, s_c, hm).sum())
-                                                         / float(np.where(s_w_fb > 0, s_w_fb, hm).sum()), 3),
+        "held_out": summ,
         "max_rel_l2_fields_warm_vs_cold_at_end": float(max(rel)) if rel else None,
         "start_field_rms_error": {"trained_network": float(np.sqrt(((pred - Yc) ** 2).mean())),
                                   "rest_state": float(np.sqrt((Yc ** 2).mean()))},

@@ -62,8 +62,10 @@ def test_batch_instances_follow_single_path(lbm, storage):
         s.step(300)
     for i, s in enumerate(singles):
         g, o = _fields(b, i), _fields(s)
+        # bit for bit: both bulk kernels run the same per-node code with compile-time
+        # rows per thread, whatever the rows per thread (the single kernel takes 4 at Nr >= 64)
         for a, c in zip(g, o):
-            assert _rel(a, c) <= 1e-6, (i, _rel(a, c))
+            assert np.array_equal(a, c), (i, _rel(a, c))
     nb = b.nusselt()
     for i, s in enumerate(singles):
         nu = s.nusselt()
@@ -125,8 +127,8 @@ def test_batch_autotune(lbm):
     params = _mixed_params(lbm)
     b, c = lbm.Batch(params), lbm.Batch(params)
     cols, rows, ms = b.tune(4)
-    assert cols * rows <= 256 and ms > 0
-    c.step(7 * (4 + 2))                         # the tuner ran 7 shapes x (2 + 4) steps
+    assert cols * rows <= 8 * 256 and ms > 0
+    c.step(b.info(0).steps)                     # the steps the tuner ran
     b.step(10)
     c.step(10)
     for i in range(len(params)):
