@@ -100,7 +100,8 @@ typedef struct lbm_info {
     double Kbar;             /* Da * L^2 */
     int64_t steps;           /* steps taken since the last (re)initialisation */
     int64_t bytes_per_step;  /* algorithmic HBM bytes of one step: read + write of every
-                                population and one porosity read per node */
+                                population, one porosity and one FP16 reference
+                                (lbm_rebase) read per node */
 } lbm_info;
 
 typedef struct lbm_handle lbm_handle;
@@ -159,11 +160,23 @@ int lbm_residual(lbm_handle *h, double *res, double *mass);
  * over the interval, max(|u^n - u^(n-k)|_2 / |u^n|_2, |T^n - T^(n-k)|_2 / |T^n|_2) / k
  * over non-wall nodes (FP64), is compared with tol; it averages out the rounding
  * jitter of an FP32 or 16-bit state, which keeps the consecutive-step residual of
- * lbm_residual near 1e-8 - 1e-7 however long the run.  *steps_done and *res (either
+ * lbm_residual near 1e-8 - 1e-7 however long the run.  Before every interval the
+ * temperature reference is refreshed (lbm_rebase).  *steps_done and *res (either
  * may be NULL) receive the steps taken and the last value.  LBM_ERR_DIVERGED on
  * NaN/Inf.  Synchronises at every check. */
 int lbm_run(lbm_handle *h, int64_t max_steps, int64_t check_every, double tol, int64_t *steps_done,
             double *res);
+
+/* Storage detail with no counterpart in the paper.  The thermal populations are
+ * stored as deviations from w_i (T0 + R(x)), R(x) a per-node FP16 offset set from the
+ * start temperature; this call sets R(x) to the current T(x) - T0 (rounded to FP16)
+ * and re-expresses the stored deviations against it.  Every field and population is
+ * unchanged up to FP32 rounding; what changes is the size of the stored numbers, and
+ * so the rounding of later steps: without refreshes, FP32 rounding stops slow thermal
+ * modes once their change per step drops below the rounding of |T - T0 - R|
+ * (a spread of about 1e-3 in Nu on slowly converging annuli); lbm_run refreshes before
+ * every check interval.  Asynchronous on the handle's stream. */
+int lbm_rebase(lbm_handle *h);
 
 /* Node classes (LBM_FLUID ... LBM_AXIS) into out[nr*nz] (host memory). */
 int lbm_node_class(lbm_handle *h, uint8_t *out);
@@ -236,6 +249,9 @@ int lbm_batch_step(lbm_batch *b, int64_t nsteps);
  * instance took and its last criterion value.  LBM_ERR_DIVERGED names an instance that
  * produced NaN or Inf (it is stopped; the others have run to that check). */
 int lbm_batch_run(lbm_batch *b, int64_t max_steps, int64_t check_every, double tol, int64_t *steps, double *res);
+/* lbm_rebase for every instance (lbm_batch_run refreshes the active instances before
+ * every check interval).  Asynchronous on the batch's stream. */
+int lbm_batch_rebase(lbm_batch *b);
 /* Eq. 42 of every instance: nu_inner[n], nu_outer[n] (host). */
 int lbm_batch_nusselt(lbm_batch *b, double *nu_inner, double *nu_outer);
 /* Fields of instance i, as lbm_moments. */

@@ -81,7 +81,8 @@ constexpr int BULK_RPT_MIN_BLOCKS = LBM_BULK_RPT_MIN_BLOCKS;
 // takes its e_r = +1 populations from the mirror image of itself (the ghost row
 // below the axis, e_r reversed).
 template <int STO, typename R, typename I = int64_t>
-__device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh, R* gh) {
+__device__ __forceinline__ void pull_raw(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh,
+                                         R* gh) {
     const bool pz = c.geometry != ANNULUS;
     const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;       // source column for e_z = +1
     const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;       // source column for e_z = -1
@@ -110,6 +111,34 @@ __device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I pl
     gh[4] = R(ldv(G + 4 * plane + row + zp));
 }
 
+// Re-reference pulled thermal deviations to the node's R(x): gh_i += wT_i (R(x - e_i) - R(x))
+// with r0 = R(x) and rm, zm, rp, zp the offsets of the sources of g_1 .. g_4.
+template <typename R>
+__device__ __forceinline__ void reref(R* gh, R r0, R rm, R zm, R rp, R zp) {
+    gh[1] += R(0.1) * (rm - r0);
+    gh[2] += R(0.1) * (zm - r0);
+    gh[3] += R(0.1) * (rp - r0);
+    gh[4] += R(0.1) * (zp - r0);
+}
+
+template <typename I>
+__device__ __forceinline__ float ref_at(const __half* __restrict__ Rp, I n) { return __half2float(Rp[n]); }
+
+// Pull (Eq. 22) with the thermal deviations re-referenced to R(x), which *rref receives.
+template <int STO, typename R, typename I = int64_t>
+__device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh, R* gh,
+                                     R& rref) {
+    pull_raw<STO, R, I>(c, A, plane, kr, kz, fh, gh);
+    const bool pz = c.geometry != ANNULUS;
+    const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;
+    const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;
+    const I row = (I)kr * c.nz;
+    rref = R(ref_at(c.tref, row + kz));
+    // on the pipe axis row g_1 comes from the node's own mirror image
+    const R rm = kr == 0 ? rref : R(ref_at(c.tref, row - c.nz + kz));
+    reref(gh, rref, rm, R(ref_at(c.tref, row + zm)), R(ref_at(c.tref, row + c.nz + kz)), R(ref_at(c.tref, row + zp)));
+}
+
 template <int STO, typename R, typename I = int64_t>
 __device__ __forceinline__ void store(const Buf<STO>& B, I plane, I n, const R* fh, const R* gh) {
 #pragma unroll
@@ -123,19 +152,21 @@ __device__ __forceinline__ void store(const Buf<STO>& B, I plane, I n, const R* 
 template <int STO, typename R>
 __device__ __forceinline__ void wall_state(const Consts<R>& c, const Buf<STO> A,
                                            const typename St<STO>::P* __restrict__ phi, int64_t plane, int cls,
-                                           int kr, int kz, R* fh, R* gh, R& m0, R& rho, R& dTb) {
+                                           int kr, int kz, R* fh, R* gh, R& m0, R& rho, R& dTb, R& refb) {
     int fr, fz;
     fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
-    R fhf[9], ghf[5];
-    pull<STO>(c, A, plane, fr, fz, fhf, ghf);
+    R fhf[9], ghf[5], reff;
+    pull<STO>(c, A, plane, fr, fz, fhf, ghf, reff);
     const R rf = c.r0 + R(fr), rb = c.r0 + R(kr);
     const R phif = R(ldv(phi + (int64_t)fr * c.nz + fz));
     R m0f, rhof, urf, uzf, dTf, lin, nl, ipf;
     porous(c, phif, lin, nl, ipf);
-    recover(c, rf, rcp_acc(rf), phif, lin, nl, fhf, ghf, m0f, rhof, urf, uzf, dTf);
+    recover(c, rf, rcp_acc(rf), phif, lin, nl, fhf, ghf, reff, m0f, rhof, urf, uzf, dTf);
     rebuild_flow(rb, rf, ipf, m0f, rhof, urf, uzf, fhf, fh);
-    dTb = cls == WALL_IN ? c.T_hot - c.T0 : cls == WALL_OUT ? c.T_cold - c.T0 : dTf;
-    rebuild_thermal(c.T0, dTf, dTb, urf, uzf, ghf, gh);
+    // deviations relative to this wall node's own reference R_b
+    refb = R(__half2float(c.tref[(int64_t)kr * c.nz + kz]));
+    dTb = cls == WALL_IN ? (c.T_hot - c.T0) - refb : cls == WALL_OUT ? (c.T_cold - c.T0) - refb : (dTf + reff) - refb;
+    rebuild_thermal(c.T0 + reff, dTf, dTb, urf, uzf, ghf, gh);
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
     rho = R(1) + m0 * rcp_acc(rb);
 }
@@ -174,15 +205,15 @@ __device__ __forceinline__ void update_column(const Consts<float>& c, const Buf<
         const int kr = kr0 + j;
         if (kr >= c.nr) break;
         if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) continue;
-        float fh[9], gh[5];
-        pull<STO, float, I>(c, A, plane, kr, kz, fh, gh);
+        float fh[9], gh[5], ref;
+        pull<STO, float, I>(c, A, plane, kr, kz, fh, gh, ref);
         const I n = (I)kr * c.nz + kz;
         const float r = c.r0 + float(kr), inv_r = rcp_acc(r);
         const float ph = ldv(phi + n);
         float m0, rho, ur, uz, dT, lin, nl, iph;
         porous(c, ph, lin, nl, iph);
-        recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
-        collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
+        recover(c, r, inv_r, ph, lin, nl, fh, gh, ref, m0, rho, ur, uz, dT);
+        collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, ref, m0, rho, ur, uz, dT);
         store<STO, float, I>(B, plane, n, fh, gh);
     }
 }
@@ -207,13 +238,13 @@ __global__ void k_wall(const Consts<float> c, const Buf<STO> A,
     int kr, kz;
     wall_node(c.geometry, c.nr, c.nz, t, kr, kz);
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
-    float fh[9], gh[5], m0, rho, dTb;
-    wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dTb);
+    float fh[9], gh[5], m0, rho, dTb, refb;
+    wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dTb, refb);
     const int64_t n = (int64_t)kr * c.nz + kz;
     const float r = c.r0 + float(kr), ph = ldv(phi + n);
     float lin, nl, iph;
     porous(c, ph, lin, nl, iph);
-    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, m0, rho, 0.0f, 0.0f, dTb);
+    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, 0.0f, 0.0f, dTb);
     store<STO>(B, plane, n, fh, gh);
 }
 
@@ -227,20 +258,20 @@ __global__ void k_moments(const Consts<float> c, const Buf<STO> A,
     if (kz >= c.nz) return;
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
     const int64_t n = (int64_t)kr * c.nz + kz;
-    float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT;
+    float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT, ref;
     if (is_wall(cls)) {
-        wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dT);
+        wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dT, ref);
     } else {
-        pull<STO>(c, A, plane, kr, kz, fh, gh);
+        pull<STO>(c, A, plane, kr, kz, fh, gh, ref);
         const float r = c.r0 + float(kr), ph = ldv(phi + n);
         float lin, nl, iph;
         porous(c, ph, lin, nl, iph);
-        recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+        recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, ref, m0, rho, ur, uz, dT);
     }
     if (rho_o) rho_o[n] = rho;
     if (ur_o) ur_o[n] = ur;
     if (uz_o) uz_o[n] = uz;
-    if (T_o) T_o[n] = c.T0 + dT;
+    if (T_o) T_o[n] = (c.T0 + ref) + dT;
 }
 
 // Start state (FP64 arithmetic, one launch per initialisation): pre-collision
@@ -263,7 +294,7 @@ __device__ __forceinline__ double start_T(const Consts<double>& c, const float* 
 template <int STO>
 __global__ void k_init(const Consts<double> c, const Buf<STO> B,
                        const typename St<STO>::P* __restrict__ phi, int64_t plane, const float* ur_in,
-                       const float* uz_in, const float* T_in, double noise, uint64_t seed) {
+                       const float* uz_in, const float* T_in, double noise, uint64_t seed, __half* __restrict__ tref) {
     const int kz = blockIdx.x * blockDim.x + threadIdx.x;
     const int kr = blockIdx.y;
     if (kz >= c.nz) return;
@@ -305,7 +336,11 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
                             r * ur * uz * iphi - 0.5 * S8};
     double fh[9], gh[5];
     minv(mpre, fh);
-    const double dTs = T - c.T0;
+    // reference offset R(x) = T - T0 in FP16; gh relative to T0 + R(x)
+    const __half Rh = __float2half_rn(fminf(fmaxf((float)(T - c.T0), -60000.f), 60000.f));
+    tref[n] = Rh;
+    const double ref = (double)__half2float(Rh);
+    const double dTs = T - c.T0 - ref;
     gh[0] = 0.6 * dTs;
     gh[1] = 0.1 * dTs + 0.5 * T * ur;
     gh[2] = 0.1 * dTs + 0.5 * T * uz;
@@ -317,9 +352,9 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
         rho = 1 + m0 * inv_r;
         dT = dTs;
     } else {
-        recover(c, r, inv_r, ph, lin, nl, fh, gh, m0, rho, u_r, u_z, dT);
+        recover(c, r, inv_r, ph, lin, nl, fh, gh, ref, m0, rho, u_r, u_z, dT);
     }
-    collide(c, r, inv_r, ph, lin, nl, iphi, fh, gh, m0, rho, u_r, u_z, dT);
+    collide(c, r, inv_r, ph, lin, nl, iphi, fh, gh, ref, m0, rho, u_r, u_z, dT);
     store<STO>(B, plane, n, fh, gh);
 }
 
@@ -424,9 +459,9 @@ __device__ double node_T(const Consts<float>& c, const Buf<STO> A, int64_t plane
         kr = fr;
         kz = fz;
     }
-    float fh[9], gh[5];
-    pull<STO>(c, A, plane, kr, kz, fh, gh);
-    return (double)c.T0 + (((double)gh[0] + gh[1]) + ((double)gh[2] + gh[3]) + gh[4]);
+    float fh[9], gh[5], ref;
+    pull<STO>(c, A, plane, kr, kz, fh, gh, ref);
+    return (double)c.T0 + (double)ref + (((double)gh[0] + gh[1]) + ((double)gh[2] + gh[3]) + gh[4]);
 }
 
 // Eq. 42 for both walls in one block: one-sided second-order dT/dr, trapezoid in z.
@@ -452,7 +487,7 @@ __global__ void __launch_bounds__(256) k_nusselt(const Consts<float> c, const Bu
 }
 
 // FP64 export of rows [row0, row0 + nrows): raw post-collision populations
-// f_i = ft_i + r w_i + e_ir w_i / 2, g_i = gh_i + wT_i T0.
+// f_i = ft_i + r w_i + e_ir w_i / 2, g_i = gh_i + wT_i (T0 + R(x)).
 template <int STO>
 __global__ void k_export(const Consts<float> c, const Buf<STO> A, int64_t plane, int row0,
                          int nrows, double r0, double T0, double* __restrict__ out) {
@@ -464,7 +499,30 @@ __global__ void k_export(const Consts<float> c, const Buf<STO> A, int64_t plane,
     const double r = r0 + kr;
     for (int i = 0; i < 9; ++i) out[i * P + m] = (double)ldv(A.f + i * plane + n) + (r + 0.5 * ex9(i)) * w9<double>(i);
     const double wt[5] = {0.6, 0.1, 0.1, 0.1, 0.1};
-    for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)ldv(A.g + i * plane + n) + wt[i] * T0;
+    const double Tb = T0 + (double)__half2float(c.tref[n]);
+    for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)ldv(A.g + i * plane + n) + wt[i] * Tb;
+}
+
+// Reference refresh: R(x) <- FP16(R(x) + sum_i gh_i(x)), gh re-expressed against the
+// new reference (gh_0 += d - 4 d/10, gh_1..4 += d/10 with d = R_old - R_new).  The
+// populations, and every field they give, are unchanged up to rounding.
+template <int STO>
+__global__ void k_rebase(const Buf<STO> A, int64_t plane, int64_t N, __half* __restrict__ tref) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        float g[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = ldv(A.g + i * plane + n);
+        const float r_old = __half2float(tref[n]);
+        const float t = r_old + (((g[0] + g[1]) + (g[2] + g[3])) + g[4]);
+        const __half h = __float2half_rn(fminf(fmaxf(t, -60000.f), 60000.f));
+        const float d = r_old - __half2float(h), d1 = 0.1f * d;
+        g[0] += d - 4.f * d1;
+#pragma unroll
+        for (int i = 1; i < 5; ++i) g[i] += d1;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) stv(A.g + i * plane + n, g[i]);
+        tref[n] = h;
+    }
 }
 
 // ------------------------------------------------------------ host runtime --
@@ -503,6 +561,7 @@ struct lbm_handle {
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;             // buffer holding the current state
     void* phi = nullptr;
+    __half* tref = nullptr;  // per-node reference offset R(x) of the thermal deviations
     float* fstage = nullptr; // N floats: porosity / init field upload
     float* mac = nullptr;    // two snapshots of 4 planes: rho, ur, uz, T
     int64_t mstride = 0;
@@ -556,7 +615,8 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
     o->T0 = 0.5 * (p->T_hot + p->T_cold);
     o->Kbar = p->Da * o->L * o->L;
     const int64_t N = (int64_t)p->nr * p->nz;
-    o->bytes_per_step = N * (int64_t)(2 * (9 * f_size(p->storage) + 5 * g_size(p->storage)) + phi_size(p->storage));
+    o->bytes_per_step = N * (int64_t)(2 * (9 * f_size(p->storage) + 5 * g_size(p->storage)) + phi_size(p->storage) +
+                                      sizeof(__half));
     if (cd) {
         Consts<double>& c = *cd;
         memset(&c, 0, sizeof(c));
@@ -604,6 +664,7 @@ static Consts<float> to_float(const Consts<double>& d) {
     f.tauT = (float)d.tauT; f.wg_den = (float)d.wg_den; f.gbeta = (float)d.gbeta; f.T0 = (float)d.T0;
     f.az = (float)d.az; f.lin_coef = (float)d.lin_coef; f.nl_coef = (float)d.nl_coef;
     f.T_hot = (float)d.T_hot; f.T_cold = (float)d.T_cold;
+    f.tref = d.tref;
     return f;
 }
 
@@ -671,6 +732,7 @@ int lbm_destroy(lbm_handle* h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* b : h->buf) cudaFree(b);
+    cudaFree(h->tref);
     cudaFree(h->phi);
     cudaFree(h->fstage);
     cudaFree(h->mac);
@@ -687,7 +749,7 @@ static int launch_init(lbm_handle* h, const float* ur, const float* uz, const fl
     dim3 g = grid2d(h, 128);
     DISPATCH_STO(h->p.storage,
                  k_init<S_><<<g, 128, 0, h->stream>>>(h->cd, bufp<S_>(h, 0), (const PP<S_>*)h->phi, h->plane, ur, uz,
-                                                      T, h->p.init_noise, h->p.seed));
+                                                      T, h->p.init_noise, h->p.seed, h->tref));
     CK(cudaGetLastError());
     h->cur = 0;
     h->info.steps = 0;
@@ -722,6 +784,9 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     } while (0)
     ALLOC(h->buf[0], state_bytes(p->storage, h->plane));
     ALLOC(h->buf[1], state_bytes(p->storage, h->plane));
+    ALLOC(h->tref, h->plane * sizeof(__half));
+    h->cd.tref = h->tref;
+    h->cf.tref = h->tref;
     ALLOC(h->phi, h->plane * phi_size(p->storage));
     ALLOC(h->partials, (size_t)h->pblocks * RES_NV * sizeof(double));
     ALLOC(h->result, 8 * sizeof(double));
@@ -961,6 +1026,7 @@ int lbm_run(lbm_handle* h, int64_t max_steps, int64_t check_every, double tol, i
     double r = INFINITY;
     while (done < max_steps) {
         const int64_t k = std::min(check_every, max_steps - done);
+        if ((rc = lbm_rebase(h))) break;
         if ((rc = lbm_step(h, k))) break;
         done += k;
         if ((rc = snapshot(h, h->cur, a))) break;
@@ -974,6 +1040,15 @@ int lbm_run(lbm_handle* h, int64_t max_steps, int64_t check_every, double tol, i
     if (steps_done) *steps_done = done;
     if (res) *res = r;
     return rc;
+}
+
+int lbm_rebase(lbm_handle* h) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    const unsigned blocks = (unsigned)std::min<int64_t>((h->N + 255) / 256, (int64_t)h->sms * 16);
+    DISPATCH_STO(h->p.storage, k_rebase<S_><<<blocks, 256, 0, h->stream>>>(bufp<S_>(h, h->cur), h->plane, h->N, h->tref));
+    CK(cudaGetLastError());
+    return LBM_OK;
 }
 
 int lbm_node_class(lbm_handle* h, uint8_t* out) {
@@ -1119,6 +1194,7 @@ struct InstDesc {
     Consts<float> c;
     int64_t off_state[2];   // byte offsets of state buffers A and B in the state pool
     int64_t off_phi;        // byte offset of the porosity plane
+    int64_t off_tref;       // byte offset of the reference-offset plane R(x) (FP16)
     int64_t off_mac;        // float offset of the two field snapshots in the snapshot pool
     int64_t plane;          // elements per plane
     double r0, H, dTw;
@@ -1134,8 +1210,8 @@ __device__ __forceinline__ Buf<STO> inst_buf(const InstDesc& d, char* pool, int 
 
 // Tile = (instance, first row, first column); block = (bz, rows); each thread updates
 // RPT consecutive rows of its column (the instance descriptor is read once per thread).
-// The per-node arithmetic is the single-problem kernel's with the same RPT, so a batch
-// instance stepped with the single kernel's rows per thread follows it bit for bit.
+// The per-node source is the single-problem kernel's (update_column); the two kernels
+// agree to rounding (the compiler may fuse multiply-adds differently in each).
 template <int STO, int RPT>
 __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__ desc, char* __restrict__ pool,
                                                     int parity, const int4* __restrict__ tiles) {
@@ -1174,13 +1250,13 @@ __global__ void k_batch_wall(const InstDesc* __restrict__ desc, char* __restrict
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
     const Buf<STO> A = inst_buf<STO>(d, pool, parity), B = inst_buf<STO>(d, pool, parity ^ 1);
     const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
-    float fh[9], gh[5], m0, rho, dTb;
-    wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dTb);
+    float fh[9], gh[5], m0, rho, dTb, refb;
+    wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dTb, refb);
     const int64_t n = (int64_t)kr * c.nz + kz;
     const float r = c.r0 + float(kr), ph = ldv(phi + n);
     float lin, nl, iph;
     porous(c, ph, lin, nl, iph);
-    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, m0, rho, 0.0f, 0.0f, dTb);
+    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, 0.0f, 0.0f, dTb);
     store<STO>(B, d.plane, n, fh, gh);
 }
 
@@ -1203,20 +1279,20 @@ __global__ void __launch_bounds__(256) k_batch_moments(const InstDesc* __restric
         if (kr >= c.nr) break;
         const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
         const int64_t n = (int64_t)kr * c.nz + kz;
-        float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT;
+        float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT, ref;
         if (is_wall(cls)) {
-            wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dT);
+            wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dT, ref);
         } else {
-            pull<STO>(c, A, d.plane, kr, kz, fh, gh);
+            pull<STO>(c, A, d.plane, kr, kz, fh, gh, ref);
             const float r = c.r0 + float(kr), ph = ldv(phi + n);
             float lin, nl, iph;
             porous(c, ph, lin, nl, iph);
-            recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+            recover(c, r, rcp_acc(r), ph, lin, nl, fh, gh, ref, m0, rho, ur, uz, dT);
         }
         m[n] = rho;
         m[d.plane + n] = ur;
         m[2 * d.plane + n] = uz;
-        m[3 * d.plane + n] = c.T0 + dT;
+        m[3 * d.plane + n] = (c.T0 + ref) + dT;
     }
 }
 
@@ -1431,6 +1507,8 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
         state_off += (int64_t)state_bytes(b->storage, plane);
         d.off_phi = state_off;
         state_off += (plane * (int64_t)phi_size(b->storage) + 255) / 256 * 256;
+        d.off_tref = state_off;
+        state_off += (plane * (int64_t)sizeof(__half) + 255) / 256 * 256;
         d.off_mac = mac_off;
         mac_off += 8 * plane;
         d.r0 = b->info[i].r0;
@@ -1444,6 +1522,11 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     b->own_stream = e == cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->pool, state_off);
+    if (e == cudaSuccess)
+        for (int i = 0; i < n; ++i) {
+            b->desc[i].c.tref = (const __half*)(b->pool + b->desc[i].off_tref);
+            b->cd[i].tref = b->desc[i].c.tref;
+        }
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->macpool, mac_off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, n * sizeof(InstDesc));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_active, n * sizeof(int));
@@ -1467,7 +1550,8 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
             k_phi_fill<S_><<<(unsigned)((N + 255) / 256), 256, 0, b->stream>>>((PP<S_>*)(b->pool + d.off_phi), N,
                                                                                 (float)p[i].eps_mean);
             k_init<S_><<<g, 128, 0, b->stream>>>(b->cd[i], batch_buf<S_>(b, i, 0), (const PP<S_>*)(b->pool + d.off_phi),
-                                                 d.plane, nullptr, nullptr, nullptr, p[i].init_noise, p[i].seed);
+                                                 d.plane, nullptr, nullptr, nullptr, p[i].init_noise, p[i].seed,
+                                                 (__half*)(b->pool + d.off_tref));
         });
     }
     e = cudaGetLastError();
@@ -1536,7 +1620,8 @@ int lbm_batch_init_fields(lbm_batch* b, int32_t i, const float* ur, const float*
     // the instance's current buffer is the batch parity
     DISPATCH_STO(b->storage, k_init<S_><<<g, 128, 0, b->stream>>>(b->cd[i], batch_buf<S_>(b, i, b->parity),
                                                                    (const PP<S_>*)(b->pool + d.off_phi), d.plane, dur,
-                                                                   duz, dT, b->p[i].init_noise, b->p[i].seed));
+                                                                   duz, dT, b->p[i].init_noise, b->p[i].seed,
+                                                                   (__half*)(b->pool + d.off_tref)));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(b->stream));
     if (!b->active[i]) {
@@ -1554,6 +1639,28 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
         if (rc) return rc;
     }
     b->steps += nsteps;
+    return LBM_OK;
+}
+
+// Reference refresh of instance i (the kernel of lbm_rebase, on the instance's current
+// buffer).
+static int batch_rebase_one(lbm_batch* b, int i) {
+    const InstDesc& d = b->desc[i];
+    const int64_t N = (int64_t)b->p[i].nr * b->p[i].nz;
+    const unsigned blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 4096);
+    DISPATCH_STO(b->storage, k_rebase<S_><<<blocks, 256, 0, b->stream>>>(batch_buf<S_>(b, i, b->cur_parity(i)), d.plane,
+                                                                          N, (__half*)(b->pool + d.off_tref)));
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_batch_rebase(lbm_batch* b) {
+    if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+    CK(cudaSetDevice(b->device));
+    for (int i = 0; i < b->n; ++i) {
+        int rc = batch_rebase_one(b, i);
+        if (rc) return rc;
+    }
     return LBM_OK;
 }
 
@@ -1581,6 +1688,9 @@ int lbm_batch_run(lbm_batch* b, int64_t max_steps, int64_t check_every, double t
     int64_t total = 0;
     while (total < max_steps && b->nactive > 0) {
         const int64_t k = std::min(check_every, max_steps - total);
+        // reference refresh before every check interval, as lbm_run does
+        for (int i = 0; i < b->n; ++i)
+            if (b->active[i] && (rc = batch_rebase_one(b, i))) return rc;
         if (k == check_every) {
             if (b->graph_dirty || b->graph_steps != k || b->graph_parity != b->parity) {
                 batch_free_graph(b);

@@ -4,18 +4,24 @@
 // Variables.  The populations of Eq. 17 carry a factor r.  Between steps they are
 // stored as deviations from the exact post-collision rest state (rho = 1, u = 0):
 //     ft_i = f+_i - (r w_i + c_i),   c_i = e_ir w_i / 2,
-//     gh_i = g+_i - wT_i T0,
-// where r w_i + c_i = M^-1 (m_eq + S/2) at rest (S_3 = rho c_s^2 from a_r of Eq. 25).
-// Streaming maps that rest state onto the pre-collision rest state r w_i - c_i
+//     gh_i = g+_i - wT_i (T0 + R(x)),
+// where r w_i + c_i = M^-1 (m_eq + S/2) at rest (S_3 = rho c_s^2 from a_r of Eq. 25)
+// and R(x) is a per-node reference temperature offset held in FP16 (a separate plane,
+// refreshed from the current temperature by the rebase kernel).  The reference keeps
+// the stored gh at the size of the temperature change since the last refresh instead
+// of |T - T0|, so FP32 rounding no longer freezes slow thermal modes before they settle.
+// Streaming maps the flow rest state onto the pre-collision rest state r w_i - c_i
 // (because r - e_ir + e_ir/2 = r - e_ir/2), so the pulled pre-collision deviation
 //     fv_i(x) = f_i(x) - (r w_i - c_i) = ft_i(x - e_i)
-// is a plain copy (Eq. 22), also through the specular image of the axis row.  The
+// is a plain copy (Eq. 22), also through the specular image of the axis row; the
+// pulled thermal deviation is gh_i(x - e_i) + wT_i (R(x - e_i) - R(x)).  The
 // moments of the deviations are mv = M fv = m - r (1, -2, 1, 0, ...) + (0, 0, 0, c_s^2/2,
 // -c_s^2/2, 0, ...).  Eq. 21 applied to mv, with the constant c_s^2 of S_3 (and -c_s^2
 // of S_4) removed from the source, gives exactly M ft+: the rest constants cancel.  All
 // handled values are small, so FP32 (and FP16/BF16 storage) keep their precision.
 // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,6 +46,7 @@ struct Consts {
     R lin_coef;        // nu / K = lin_coef (mode 1) or lin_coef (1 - phi)^2 / phi^3 (mode 2)
     R nl_coef;         // F_phi / sqrt(K), see porous()
     R T_hot, T_cold;
+    const __half* tref;   // per-node reference offset R(x) (FP16, one plane)
 };
 
 template <typename R> __host__ __device__ constexpr R cs2() { return R(1) / R(3); }
@@ -117,13 +124,13 @@ __device__ __forceinline__ void porous(const Consts<R>& c, R phi, R& lin, R& nl,
 // literally per component with |v| = sqrt(v_r^2 + v_z^2)); lin, nl from porous().
 template <typename R>
 __device__ __forceinline__ void recover(const Consts<R>& c, R r, R inv_r, R phi, R lin, R nl, const R* fh,
-                                        const R* gh, R& m0, R& rho, R& ur, R& uz, R& dT) {
-    dT = gh[0] + gh[1] + gh[2] + gh[3] + gh[4];
+                                        const R* gh, R rref, R& m0, R& rho, R& ur, R& uz, R& dT) {
+    dT = gh[0] + gh[1] + gh[2] + gh[3] + gh[4];   // T - T0 - R(x)
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
     rho = R(1) + m0 * inv_r;
     const R jr = (fh[1] - fh[3]) + (fh[5] - fh[6]) + (fh[8] - fh[7]);
     const R jz = (fh[2] - fh[4]) + (fh[5] + fh[6]) - (fh[7] + fh[8]);
-    const R Gz = c.gbeta * dT + c.az;
+    const R Gz = c.gbeta * (dT + rref) + c.az;
     const R inv_rho = rcp_acc(rho);
     // sum_i e_ir f_i = jr - c_s^2 / 2, so v_r = (jr - c_s^2/2) / rho + c_s^2 / 2 (Eq. 29)
     const R vr = (jr + R(0.5) * cs2<R>() * m0 * inv_r) * inv_rho;
@@ -171,11 +178,12 @@ __device__ __forceinline__ void minv(const R* m, R* f) {
 // that wall nodes can impose u = 0 and their temperature; m0 = sum_i fh_i.
 template <typename R>
 __device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi, R lin, R nl, R inv_phi, R* fh,
-                                        R* gh, R m0, R rho, R ur, R uz, R dT) {
-    const R T = c.T0 + dT;
+                                        R* gh, R rref, R m0, R rho, R ur, R uz, R dT) {
+    const R Tb = c.T0 + rref;   // the node's reference temperature
+    const R T = Tb + dT;
     const R u2 = ur * ur + uz * uz;
     const R um = sqrt_fast(u2);
-    const R Gz = c.gbeta * dT + c.az;
+    const R Gz = c.gbeta * (dT + rref) + c.az;
     const R drag = lin + nl * um;
     const R Fr = -phi * drag * ur;
     const R Ftr = Fr + cs2<R>() * (R(1) - c.two_taum * ur * inv_r) * inv_r;   // Eq. 25
@@ -229,13 +237,13 @@ __device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi,
     const R wd = c.wg_den;
     const R cu = -ur * inv_r;
     const R Tr = R(0.5) * T * ur, Tz = R(0.5) * T * uz;
-    // g_eq - wT T0 (Eq. 35-36); the rest component is dT minus the other four so that
+    // g_eq - wT (T0 + R) (Eq. 35-36); the rest component is dT minus the other four so that
     // sum_i g_eq,i = T holds to rounding (0.6f + 4 * 0.1f is not 1)
     const R t1 = R(0.1) * dT;
     const R g1e = t1 + Tr, g3e = t1 - Tr;
     const R g2e = t1 + Tz, g4e = t1 - Tz;
     const R g0e = dT - R(4) * t1;
-    const R wT0 = R(0.6) * c.T0, wT1 = R(0.1) * c.T0;
+    const R wT0 = R(0.6) * Tb, wT1 = R(0.1) * Tb;
     gh[0] = gh[0] - wd * (gh[0] - g0e) + cu * (g0e + wT0);
     gh[1] = gh[1] - (R(1) + k) * wd * (gh[1] - g1e) + cu * (g1e + wT1);
     gh[2] = gh[2] - wd * (gh[2] - g2e) + cu * (g2e + wT1);
@@ -268,10 +276,11 @@ __device__ __forceinline__ void rebuild_flow(R rb, R rf, R iphi, R m0f, R rhof, 
 }
 
 // Thermal part of the wall rebuild: g_b = g_eq(T_b, 0) + [g_f - g_eq(T_f, u_f)]
-// (Eq. 35); in deviations gh_b,i = wT_i (T_b - T0) + gh_f,i - (g_eq,i(T_f, u_f) - wT_i T0).
+// (Eq. 35); in deviations gh_b,i = wT_i dTb + gh_f,i - (g_eq,i(T_f, u_f) - wT_i Tf0) with
+// dTb = T_b - T0 - R_b, Tf0 = T0 + R_f the fluid neighbour's reference, dTf = T_f - Tf0.
 template <typename R>
-__device__ __forceinline__ void rebuild_thermal(R T0, R dTf, R dTb, R urf, R uzf, const R* ghf, R* gh) {
-    const R Tf = T0 + dTf;
+__device__ __forceinline__ void rebuild_thermal(R Tf0, R dTf, R dTb, R urf, R uzf, const R* ghf, R* gh) {
+    const R Tf = Tf0 + dTf;
     const R tr = R(0.5) * Tf * urf, tz = R(0.5) * Tf * uzf;
     const R d = dTb - dTf;
     const R t1 = R(0.1) * d;

@@ -65,6 +65,7 @@ _SIGS = {
     "lbm_nusselt": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_residual": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+    "lbm_rebase": (C.c_int, [_vp]),
     "lbm_node_class": (C.c_int, [_vp, _vp]),
     "lbm_export_populations": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp]),
     "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
@@ -79,6 +80,7 @@ _SIGS = {
     "lbm_batch_init_fields": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, C.c_int]),
     "lbm_batch_step": (C.c_int, [_vp, C.c_int64]),
     "lbm_batch_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, _vp, _vp]),
+    "lbm_batch_rebase": (C.c_int, [_vp]),
     "lbm_batch_nusselt": (C.c_int, [_vp, _vp, _vp]),
     "lbm_batch_moments": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int]),
     "lbm_batch_tune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -189,6 +191,10 @@ def lbm_run(h, max_steps: int, check_every: int, tol: float):
     return n.value, r.value
 
 
+def lbm_rebase(h):
+    _check(load().lbm_rebase(h))
+
+
 def lbm_node_class(h, out: np.ndarray):
     _check(load().lbm_node_class(h, _ptr(out)))
 
@@ -282,6 +288,9 @@ class Solver:
     def run(self, max_steps, check_every=100, tol=1e-8):
         return lbm_run(self.h, max_steps, check_every, tol)
 
+    def rebase(self):
+        lbm_rebase(self.h)
+
     def node_class(self):
         out = np.empty((self.nr, self.nz), np.uint8)
         lbm_node_class(self.h, out)
@@ -323,6 +332,10 @@ def lbm_batch_run(b, n: int, max_steps: int, check_every: int, tol: float):
     res = np.zeros(n, np.float64)
     _check(load().lbm_batch_run(b, int(max_steps), int(check_every), float(tol), steps.ctypes.data, res.ctypes.data))
     return steps, res
+
+
+def lbm_batch_rebase(b):
+    _check(load().lbm_batch_rebase(b))
 
 
 def lbm_batch_nusselt(b, n: int):
@@ -383,6 +396,9 @@ class Batch:
 
     def run(self, max_steps, check_every=1000, tol=1e-8):
         return lbm_batch_run(self.b, self.n, max_steps, check_every, tol)
+
+    def rebase(self):
+        lbm_batch_rebase(self.b)
 
     def nusselt(self):
         return lbm_batch_nusselt(self.b, self.n)
