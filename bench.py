@@ -164,8 +164,8 @@ def run_ours(args, rank, world, local_rank):
     interior = (NR - 2) * (NZ - 2)
     ef = 4 if args.storage == "f32" else 2          # flow populations; temperature populations are FP32
     # algorithmic bytes of one bulk launch: 14 populations read and written, the porosity
-    # and the FP16 temperature reference read
-    bulk_bytes = interior * (2 * (9 * ef + 5 * 4) + ef + 2)
+    # and (FP32 storage) the FP16 temperature reference read
+    bulk_bytes = interior * (2 * (9 * ef + 5 * 4) + ef + (2 if args.storage == "f32" else 0))
 
     s.step(args.warmup)
     torch.cuda.synchronize()

@@ -100,8 +100,8 @@ typedef struct lbm_info {
     double Kbar;             /* Da * L^2 */
     int64_t steps;           /* steps taken since the last (re)initialisation */
     int64_t bytes_per_step;  /* algorithmic HBM bytes of one step: read + write of every
-                                population, one porosity and one FP16 reference
-                                (lbm_rebase) read per node */
+                                population, one porosity and (FP32 storage) one FP16
+                                reference (lbm_rebase) read per node */
 } lbm_info;
 
 typedef struct lbm_handle lbm_handle;
@@ -175,7 +175,9 @@ int lbm_run(lbm_handle *h, int64_t max_steps, int64_t check_every, double tol, i
  * so the rounding of later steps: without refreshes, FP32 rounding stops slow thermal
  * modes once their change per step drops below the rounding of |T - T0 - R|
  * (a spread of about 1e-3 in Nu on slowly converging annuli); lbm_run refreshes before
- * every check interval.  Asynchronous on the handle's stream. */
+ * every check interval.  FP32 storage only: with 16-bit flow populations R(x) = 0 and
+ * this call does nothing (their flow rounding sets the steady-state floor).
+ * Asynchronous on the handle's stream. */
 int lbm_rebase(lbm_handle *h);
 
 /* Node classes (LBM_FLUID ... LBM_AXIS) into out[nr*nz] (host memory). */

@@ -124,11 +124,20 @@ __device__ __forceinline__ void reref(R* gh, R r0, R rm, R zm, R rp, R zp) {
 template <typename I>
 __device__ __forceinline__ float ref_at(const __half* __restrict__ Rp, I n) { return __half2float(Rp[n]); }
 
+// The temperature reference is kept with FP32 storage only: with 16-bit flow
+// populations the per-step rounding jitter of the flow (about 4e-4 in u) sets the
+// steady-state floor, and R(x) = 0 there (gh relative to T0, no reference reads).
+template <int STO> __host__ __device__ constexpr bool has_ref() { return STO == LBM_F32; }
+
 // Pull (Eq. 22) with the thermal deviations re-referenced to R(x), which *rref receives.
 template <int STO, typename R, typename I = int64_t>
 __device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh, R* gh,
                                      R& rref) {
     pull_raw<STO, R, I>(c, A, plane, kr, kz, fh, gh);
+    if constexpr (!has_ref<STO>()) {
+        rref = R(0);
+        return;
+    }
     const bool pz = c.geometry != ANNULUS;
     const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;
     const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;
@@ -164,7 +173,7 @@ __device__ __forceinline__ void wall_state(const Consts<R>& c, const Buf<STO> A,
     recover(c, rf, rcp_acc(rf), phif, lin, nl, fhf, ghf, reff, m0f, rhof, urf, uzf, dTf);
     rebuild_flow(rb, rf, ipf, m0f, rhof, urf, uzf, fhf, fh);
     // deviations relative to this wall node's own reference R_b
-    refb = R(__half2float(c.tref[(int64_t)kr * c.nz + kz]));
+    refb = has_ref<STO>() ? R(__half2float(c.tref[(int64_t)kr * c.nz + kz])) : R(0);
     dTb = cls == WALL_IN ? (c.T_hot - c.T0) - refb : cls == WALL_OUT ? (c.T_cold - c.T0) - refb : (dTf + reff) - refb;
     rebuild_thermal(c.T0 + reff, dTf, dTb, urf, uzf, ghf, gh);
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
@@ -337,7 +346,8 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
     double fh[9], gh[5];
     minv(mpre, fh);
     // reference offset R(x) = T - T0 in FP16; gh relative to T0 + R(x)
-    const __half Rh = __float2half_rn(fminf(fmaxf((float)(T - c.T0), -60000.f), 60000.f));
+    const __half Rh = has_ref<STO>() ? __float2half_rn(fminf(fmaxf((float)(T - c.T0), -60000.f), 60000.f))
+                                     : __float2half_rn(0.f);
     tref[n] = Rh;
     const double ref = (double)__half2float(Rh);
     const double dTs = T - c.T0 - ref;
@@ -499,7 +509,7 @@ __global__ void k_export(const Consts<float> c, const Buf<STO> A, int64_t plane,
     const double r = r0 + kr;
     for (int i = 0; i < 9; ++i) out[i * P + m] = (double)ldv(A.f + i * plane + n) + (r + 0.5 * ex9(i)) * w9<double>(i);
     const double wt[5] = {0.6, 0.1, 0.1, 0.1, 0.1};
-    const double Tb = T0 + (double)__half2float(c.tref[n]);
+    const double Tb = T0 + (has_ref<STO>() ? (double)__half2float(c.tref[n]) : 0.0);
     for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)ldv(A.g + i * plane + n) + wt[i] * Tb;
 }
 
@@ -508,20 +518,22 @@ __global__ void k_export(const Consts<float> c, const Buf<STO> A, int64_t plane,
 // populations, and every field they give, are unchanged up to rounding.
 template <int STO>
 __global__ void k_rebase(const Buf<STO> A, int64_t plane, int64_t N, __half* __restrict__ tref) {
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        float g[5];
+    if constexpr (has_ref<STO>()) {
+        for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+            float g[5];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = ldv(A.g + i * plane + n);
-        const float r_old = __half2float(tref[n]);
-        const float t = r_old + (((g[0] + g[1]) + (g[2] + g[3])) + g[4]);
-        const __half h = __float2half_rn(fminf(fmaxf(t, -60000.f), 60000.f));
-        const float d = r_old - __half2float(h), d1 = 0.1f * d;
-        g[0] += d - 4.f * d1;
+            for (int i = 0; i < 5; ++i) g[i] = ldv(A.g + i * plane + n);
+            const float r_old = __half2float(tref[n]);
+            const float t = r_old + (((g[0] + g[1]) + (g[2] + g[3])) + g[4]);
+            const __half h = __float2half_rn(fminf(fmaxf(t, -60000.f), 60000.f));
+            const float d = r_old - __half2float(h), d1 = 0.1f * d;
+            g[0] += d - 4.f * d1;
 #pragma unroll
-        for (int i = 1; i < 5; ++i) g[i] += d1;
+            for (int i = 1; i < 5; ++i) g[i] += d1;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) stv(A.g + i * plane + n, g[i]);
-        tref[n] = h;
+            for (int i = 0; i < 5; ++i) stv(A.g + i * plane + n, g[i]);
+            tref[n] = h;
+        }
     }
 }
 
@@ -616,7 +628,7 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
     o->Kbar = p->Da * o->L * o->L;
     const int64_t N = (int64_t)p->nr * p->nz;
     o->bytes_per_step = N * (int64_t)(2 * (9 * f_size(p->storage) + 5 * g_size(p->storage)) + phi_size(p->storage) +
-                                      sizeof(__half));
+                                      (p->storage == LBM_F32 ? sizeof(__half) : 0));
     if (cd) {
         Consts<double>& c = *cd;
         memset(&c, 0, sizeof(c));
@@ -1044,6 +1056,7 @@ int lbm_run(lbm_handle* h, int64_t max_steps, int64_t check_every, double tol, i
 
 int lbm_rebase(lbm_handle* h) {
     if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    if (h->p.storage != LBM_F32) return LBM_OK;   // no reference with 16-bit flow storage
     CK(cudaSetDevice(h->device));
     const unsigned blocks = (unsigned)std::min<int64_t>((h->N + 255) / 256, (int64_t)h->sms * 16);
     DISPATCH_STO(h->p.storage, k_rebase<S_><<<blocks, 256, 0, h->stream>>>(bufp<S_>(h, h->cur), h->plane, h->N, h->tref));
@@ -1645,6 +1658,7 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 // Reference refresh of instance i (the kernel of lbm_rebase, on the instance's current
 // buffer).
 static int batch_rebase_one(lbm_batch* b, int i) {
+    if (b->storage != LBM_F32) return LBM_OK;   // no reference with 16-bit flow storage
     const InstDesc& d = b->desc[i];
     const int64_t N = (int64_t)b->p[i].nr * b->p[i].nz;
     const unsigned blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 4096);

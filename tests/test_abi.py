@@ -61,8 +61,8 @@ def test_derivation_matches_oracle(lbm, oracle, kw):
                          ("nu_e", "nu_e"), ("nu", "nu"), ("gbeta", "gbeta"), ("T0", "T0"), ("Kbar", "Kbar")):
         assert np.isclose(getattr(info, k_lib), ref[k_ref], rtol=1e-14, atol=0), k_lib
     ef = 4 if p.storage == 0 else 2           # flow populations; temperature populations stay FP32
-    # + porosity (ef bytes) + the FP16 temperature reference, read once per node
-    assert info.bytes_per_step == p.nr * p.nz * (2 * (9 * ef + 5 * 4) + ef + 2)
+    # + porosity (ef bytes) + the FP16 temperature reference (FP32 storage only), read once per node
+    assert info.bytes_per_step == p.nr * p.nz * (2 * (9 * ef + 5 * 4) + ef + (2 if p.storage == 0 else 0))
 
 
 @pytest.mark.parametrize("bad", [

@@ -271,3 +271,70 @@ def test_table2_free_annulus(lbm):
         nu_i, nu_o = s.nusselt()
         print("Table 2", ra, nu_i, nu_o, nu_paper, steps, res)
         assert abs(nu_i / nu_paper - 1) < 0.02
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_config2_recipe_256x512(lbm, oracle, storage):
+    """The single-domain workload's recipe at 256 x 512 (porosity uniform[0.3, 0.9]
+    smoothed by sigma = 16, seed 2; Ra = 1e6, Da = 1e-4, Pr = 0.71; tau_nu = 0.5372 at this
+    size), 10^4 steps, per storage type.  FP32: relative L2 <= 2e-5 per field (the
+    developing Ra = 1e6 flow amplifies rounding differences: measured 9.7e-6 in u, 3.3e-6
+    in T) and Nu within the linear bound; 16-bit flow storage: |Delta Nu| <= 1e-3 Nu
+    (measured FP16 4e-6 Nu, BF16 5e-4 Nu) and T within 1e-3, the field errors reported."""
+    phi = inputs.porosity_field(256, 512, 0.3, 0.9, 16.0, seed=2)
+    s, st = _pair(lbm, oracle, storage=storage, phi=phi, nr=256, nz=512, Ra=1e6, Da=1e-4, Pr=0.71)
+    assert abs(s.info().tau_nu - 0.5372) < 1e-4
+    s.step(10000)
+    st.run(10000, THREADS)
+    errs = _field_errors(s.moments(), st.moments())
+    nu_g, nu_o = s.nusselt(), st.nusselt()
+    print(storage, "256x512 field errors", errs, "Nu", nu_g, nu_o)
+    if storage == "f32":
+        _fields_close(s, st, 2e-5)
+        _nusselt_within_bound(s, st)
+    else:
+        assert abs(nu_g[0] - nu_o[0]) <= 1e-3 * nu_o[0] and abs(nu_g[1] - nu_o[1]) <= 1e-3 * nu_o[1]
+        assert errs["T"] < 1e-3
+
+
+def test_config5_corner_crop_512(lbm, oracle):
+    """The stress case on the 512 x 512 corner crop of its porosity field (uniform[0.3,
+    0.5] smoothed by sigma = 32 at 8192 x 8192, seed 5; crop first, then the annulus built
+    at 512 x 512): Ra = 1e7, Da = 1e-6, Pr = 0.71, tau_nu = 0.51, FP16 flow storage, 10^4 steps
+    against the FP64 oracle."""
+    phi = inputs.porosity_field(8192, 8192, 0.3, 0.5, 32.0, seed=5)[:512, :512].copy()
+    s, st = _pair(lbm, oracle, storage="f16", phi=phi, nr=512, nz=512, Ra=1e7, Da=1e-6, Pr=0.71, tau_nu=0.51)
+    s.step(10000)
+    st.run(10000, THREADS)
+    errs = _field_errors(s.moments(), st.moments())
+    nu_g, nu_o = s.nusselt(), st.nusselt()
+    print("config5 crop field errors", errs, "Nu", nu_g, nu_o)
+    assert np.isfinite(nu_g).all()
+    assert abs(nu_g[0] - nu_o[0]) <= 1e-3 * abs(nu_o[0]) + 1e-3 and abs(nu_g[1] - nu_o[1]) <= 1e-3 * abs(nu_o[1]) + 1e-3
+    assert errs["T"] < 1e-3
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not os.environ.get("LBM_SLOW"), reason="set LBM_SLOW=1 (about 5 min on one GB300)")
+def test_config5_nusselt_drift_fp16_vs_fp32(lbm):
+    """Stress case at full size (8192 x 8192, tau_nu = 0.51): FP16 flow storage against
+    FP32 storage over 10^5 steps, Nu compared every 10^4 steps; both stay finite."""
+    L = lbm
+    phi = inputs.porosity_field(8192, 8192, 0.3, 0.5, 32.0, seed=5)
+    nus = {}
+    for storage in ("f32", "f16"):
+        p = L.lbm_params_default(nr=8192, nz=8192, Ra=1e7, Da=1e-6, Pr=0.71, tau_nu=0.51, storage=storage,
+                                 eps_mean=float(phi.mean(dtype=np.float64)))
+        s = L.Solver(p)
+        s.set_porosity(phi)
+        s.init_fields()
+        traj = []
+        for _ in range(10):
+            s.step(10000)
+            traj.append(s.nusselt())
+        nus[storage] = np.array(traj)
+        s.close()
+    d = np.abs(nus["f16"] - nus["f32"])
+    print("config5 Nu f32", nus["f32"].tolist(), "f16", nus["f16"].tolist(), "max |dNu|", d.max(axis=0).tolist())
+    assert np.isfinite(nus["f16"]).all() and np.isfinite(nus["f32"]).all()
+    assert (d <= 1e-3 * np.abs(nus["f32"]) + 1e-3).all()
