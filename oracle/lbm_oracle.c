@@ -37,8 +37,9 @@
 #endif
 
 /* ---------------------------------------------------------------- geometry -- */
-enum { ORC_ANNULUS = 0, ORC_ANNULUS_PERIODIC_Z = 1, ORC_PIPE_PERIODIC_Z = 2 };
-enum { ORC_FLUID = 0, ORC_WALL_IN = 1, ORC_WALL_OUT = 2, ORC_BOTTOM = 3, ORC_TOP = 4, ORC_AXIS = 5 };
+enum { ORC_ANNULUS = 0, ORC_ANNULUS_PERIODIC_Z = 1, ORC_PIPE_PERIODIC_Z = 2, ORC_PIPE_INFLOW = 3 };
+enum { ORC_FLUID = 0, ORC_WALL_IN = 1, ORC_WALL_OUT = 2, ORC_BOTTOM = 3, ORC_TOP = 4, ORC_AXIS = 5, ORC_INLET = 6,
+       ORC_OUTLET = 7 };
 
 typedef struct orc_params {
     int32_t nr, nz, geometry;
@@ -53,6 +54,7 @@ typedef struct orc_params {
     double body_accel_z;                 /* external acceleration a of Eq. 7, z component */
     double init_noise;                   /* amplitude of the uniform start-temperature noise */
     uint64_t seed;
+    double u_in;                         /* inlet velocity U_in (pipe with inlet and outlet, Sec. 4.1) */
 } orc_params;
 
 typedef struct orc_consts {
@@ -126,7 +128,7 @@ int orc_derive(const orc_params *p, orc_consts *c)
 {
     memset(c, 0, sizeof(*c));
     if (p->nr < 3 || p->nz < 3) return 1;
-    if (p->geometry == ORC_PIPE_PERIODIC_Z) {
+    if (p->geometry == ORC_PIPE_PERIODIC_Z || p->geometry == ORC_PIPE_INFLOW) {
         c->r0 = 0.5;
         c->L = (p->nr - 1) + 0.5;
     } else {
@@ -320,14 +322,24 @@ void orc_collide(const orc_params *p, const orc_consts *c, double r, double phi,
 }
 
 /* -------------------------------------------------------- grid and classes -- */
-static int periodic_z(const orc_params *p) { return p->geometry != ORC_ANNULUS; }
+static int periodic_z(const orc_params *p)
+{
+    return p->geometry == ORC_ANNULUS_PERIODIC_Z || p->geometry == ORC_PIPE_PERIODIC_Z;
+}
+static int is_pipe(const orc_params *p) { return p->geometry == ORC_PIPE_PERIODIC_Z || p->geometry == ORC_PIPE_INFLOW; }
 
 /* Node classes (Fig. 1 and Fig. 3): walls on the outermost nodes; corners belong
- * to the side walls, so the Dirichlet temperature wins there. */
+ * to the side walls, so the Dirichlet temperature wins there.  Pipe with inlet and
+ * outlet (Fig. 1): the wall is 0 < z < H, so the inlet row z = 0 and the outlet row
+ * z = H own their corners. */
 static int node_class(const orc_params *p, int kr, int kz)
 {
+    if (p->geometry == ORC_PIPE_INFLOW) {
+        if (kz == 0) return ORC_INLET;
+        if (kz == p->nz - 1) return ORC_OUTLET;
+    }
     if (kr == p->nr - 1) return ORC_WALL_OUT;
-    if (kr == 0) return p->geometry == ORC_PIPE_PERIODIC_Z ? ORC_AXIS : ORC_WALL_IN;
+    if (kr == 0) return is_pipe(p) ? ORC_AXIS : ORC_WALL_IN;
     if (!periodic_z(p)) {
         if (kz == 0) return ORC_BOTTOM;
         if (kz == p->nz - 1) return ORC_TOP;
@@ -335,7 +347,7 @@ static int node_class(const orc_params *p, int kr, int kz)
     return ORC_FLUID;
 }
 
-static int is_wall(int cls) { return cls >= ORC_WALL_IN && cls <= ORC_TOP; }
+static int is_wall(int cls) { return (cls >= ORC_WALL_IN && cls <= ORC_TOP) || cls == ORC_INLET || cls == ORC_OUTLET; }
 
 int orc_node_class(const orc_params *p, uint8_t *out)
 {
@@ -373,8 +385,9 @@ static void fluid_neighbour(const orc_params *p, int cls, int kr, int kz, int *f
     *fz = kz;
     if (cls == ORC_WALL_IN) *fr = 1;
     if (cls == ORC_WALL_OUT) *fr = p->nr - 2;
-    if (cls == ORC_BOTTOM) *fz = 1;
-    if (cls == ORC_TOP) *fz = p->nz - 2;
+    if (cls == ORC_BOTTOM || cls == ORC_INLET) *fz = 1;
+    if (cls == ORC_TOP || cls == ORC_OUTLET) *fz = p->nz - 2;
+    if ((cls == ORC_INLET || cls == ORC_OUTLET) && kr == p->nr - 1) *fr = p->nr - 2;
     if ((cls == ORC_WALL_IN || cls == ORC_WALL_OUT) && !periodic_z(p)) {
         if (kz == 0) *fz = 1;
         if (kz == p->nz - 1) *fz = p->nz - 2;
@@ -382,16 +395,21 @@ static void fluid_neighbour(const orc_params *p, int cls, int kr, int kz, int *f
 }
 
 /*
- * Non-equilibrium extrapolation (Sec. 4, ref. [47]) at a wall node x_b:
- *   f(x_b) = f_eq(r_b, rho_f, u = 0) + [f(x_f) - f_eq(r_f, rho_f, u_f)]
- *   g(x_b) = g_eq(T_b, u = 0) + [g(x_f) - g_eq(T_f, u_f)]
+ * Non-equilibrium extrapolation (Sec. 4, ref. [47]) at a boundary node x_b:
+ *   f(x_b) = f_eq(r_b, rho_b, u_b) + [f(x_f) - f_eq(r_f, rho_f, u_f)]
+ *   g(x_b) = g_eq(T_b, u_b) + [g(x_f) - g_eq(T_f, u_f)]
  * with f(x_f), g(x_f) the post-streaming populations of the interior neighbour and
- * rho_f, u_f, T_f recovered from them.  Walls are no-slip (u_b = 0).  T_b is T_hot
- * on the inner wall, T_cold on the outer wall and T_f on the adiabatic top and
- * bottom.  The non-equilibrium part is copied unscaled, as in [47].
+ * rho_f, u_f, T_f recovered from them.  Walls are no-slip (u_b = 0, rho_b = rho_f);
+ * T_b is T_hot on the inner wall, T_cold on the outer wall and T_f on the adiabatic
+ * top and bottom.  Pipe with inlet and outlet (Sec. 4.1): inlet u_b = (0, U_in),
+ * rho_b = rho_f, T_b = T_hot (T_in); outlet zero gradient u_b = u_f, T_b = T_f, with
+ * the density held at rho_0 = 1 there (the paper is silent on the outlet pressure).
+ * The pipe wall is the outer wall, T_cold (T_w).  The non-equilibrium part is
+ * copied unscaled, as in [47].
  */
 static void rebuild(const orc_params *p, const orc_consts *c, const double *phi, const double *fp,
-                    const double *gp, int cls, int kr, int kz, double *f, double *g, double *Tb)
+                    const double *gp, int cls, int kr, int kz, double *f, double *g, double *Tb, double *urb,
+                    double *uzb)
 {
     int fr, fz;
     fluid_neighbour(p, cls, kr, kz, &fr, &fz);
@@ -402,12 +420,22 @@ static void rebuild(const orc_params *p, const orc_consts *c, const double *phi,
     const double phib = phi[(size_t)kr * p->nz + kz];
     double rho_f, ur_f, uz_f, T_f;
     orc_macros(p, c, rf, phif, ff, gf, &rho_f, &ur_f, &uz_f, &T_f);
+    double rho_b = rho_f;
+    *urb = 0;
+    *uzb = 0;
+    if (cls == ORC_INLET) {
+        *uzb = p->u_in;
+    } else if (cls == ORC_OUTLET) {
+        *urb = ur_f;
+        *uzb = uz_f;
+        rho_b = 1.0;
+    }
     double feq_b[9], feq_f[9], geq_b[5], geq_f[5];
-    orc_feq(rb, rho_f, 0, 0, phib, feq_b);
+    orc_feq(rb, rho_b, *urb, *uzb, phib, feq_b);
     orc_feq(rf, rho_f, ur_f, uz_f, phif, feq_f);
     for (int i = 0; i < 9; ++i) f[i] = feq_b[i] + (ff[i] - feq_f[i]);
-    *Tb = (cls == ORC_WALL_IN) ? p->T_hot : (cls == ORC_WALL_OUT) ? p->T_cold : T_f;
-    geq5(*Tb, 0, 0, geq_b);
+    *Tb = (cls == ORC_WALL_IN || cls == ORC_INLET) ? p->T_hot : (cls == ORC_WALL_OUT) ? p->T_cold : T_f;
+    geq5(*Tb, *urb, *uzb, geq_b);
     geq5(T_f, ur_f, uz_f, geq_f);
     for (int i = 0; i < 5; ++i) g[i] = geq_b[i] + (gf[i] - geq_f[i]);
 }
@@ -420,13 +448,13 @@ static void node_state(const orc_params *p, const orc_consts *c, const double *p
     const int cls = node_class(p, kr, kz);
     const double r = c->r0 + kr;
     if (is_wall(cls)) {
-        double Tb;
-        rebuild(p, c, phi, fp, gp, cls, kr, kz, f, g, &Tb);
+        double Tb, urb, uzb;
+        rebuild(p, c, phi, fp, gp, cls, kr, kz, f, g, &Tb, &urb, &uzb);
         double sf = 0;
         for (int i = 0; i < 9; ++i) sf += f[i];
         *rho = sf / r;                                                               /* Eq. 26 */
-        *ur = 0;
-        *uz = 0;
+        *ur = urb;
+        *uz = uzb;
         *T = Tb;
     } else {
         pull(p, fp, gp, kr, kz, f, g);
@@ -506,8 +534,9 @@ uint64_t orc_splitmix64(uint64_t seed, uint64_t n)
  * Start state (the paper is silent).  Fields: rho = rho0 = 1 and either u = 0 with
  * T = T0 + noise * U(-1, 1) on non-wall nodes (cold start; draw number kr*nz + kz
  * of SplitMix64(seed), 53-bit uniform), or caller-given (u_r, u_z, T) (warm start).
- * Wall nodes take u = 0 and their wall temperature; top and bottom take the start
- * temperature of their interior neighbour.  Pre-collision populations:
+ * Wall nodes take u = 0 and their wall temperature; top, bottom and the pipe outlet
+ * take the start temperature of their interior neighbour; the pipe inlet takes
+ * u = (0, U_in) and T_hot.  Pre-collision populations:
  *   f = M^-1 (m_eq - S / 2),   g = g_eq(T, u),
  * so that Eq. 29 returns the given u exactly when u = 0.  The stored state is those
  * populations after one collision at their own node (walls with u = 0, T = T_b).
@@ -539,7 +568,10 @@ int orc_init(const orc_params *p, const double *phi, const double *ur_in, const 
             double ur = 0, uz = 0, T = Tst[n];
             if (cls == ORC_WALL_IN) T = p->T_hot;
             else if (cls == ORC_WALL_OUT) T = p->T_cold;
-            else if (cls == ORC_BOTTOM || cls == ORC_TOP) {
+            else if (cls == ORC_INLET) {
+                T = p->T_hot;
+                uz = p->u_in;
+            } else if (cls == ORC_BOTTOM || cls == ORC_TOP || cls == ORC_OUTLET) {
                 int fr, fz;
                 fluid_neighbour(p, cls, kr, kz, &fr, &fz);
                 T = Tst[(size_t)fr * p->nz + fz];
@@ -568,8 +600,8 @@ int orc_init(const orc_params *p, const double *phi, const double *ur_in, const 
                 double sf = 0;
                 for (int i = 0; i < 9; ++i) sf += fpre[i];
                 rho = sf / r;
-                urr = 0;
-                uzz = 0;
+                urr = ur;
+                uzz = uz;
                 TT = T;
             } else {
                 orc_macros(p, &c, r, phi[n], fpre, gpre, &rho, &urr, &uzz, &TT);
@@ -614,6 +646,39 @@ int orc_nusselt(const orc_params *p, const double *T, double *nu_i, double *nu_o
  * none): max(|u^n - u^(n-1)|_2 / |u^n|_2, |T^n - T^(n-1)|_2 / |T^n|_2) over the
  * non-wall nodes.  Also returns the mass sum over all nodes of r * rho (= sum_i f_i).
  */
+/*
+ * Pipe with inlet and outlet (Sec. 4.1): local wall Nusselt number of Eq. 40,
+ * Nu(z) = D (dT/dr)_w / (T_w - T_b), D = 2 r_i, at every column kz.  T_b is the
+ * mixing-cup bulk temperature int_0^{r_i} u_z r T dr / int_0^{r_i} u_z r dr: Eq. 41
+ * as printed omits u_z, but with that area mean the no-porous pipe gives Nu = 5.3
+ * instead of the printed 3.674 (Table 1) and the classical 3.657, which the
+ * mixing-cup mean reproduces.  Nodes sit at r = k + 1/2 with the wall node at r_i;
+ * the integrals use the trapezoid rule on the points r = 0 (integrand 0), 1/2,
+ * 3/2, ..., r_i.  (dT/dr)_w is the one-sided second-order difference
+ * (3 T_w - 4 T_{w-1} + T_{w-2}) / 2.  Writes nu[0..nz-1].
+ */
+int orc_pipe_nusselt(const orc_params *p, const double *uz, const double *T, double *nu)
+{
+    orc_consts c;
+    if (orc_derive(p, &c) || p->geometry != ORC_PIPE_INFLOW) return 1;
+    const int nr = p->nr, nz = p->nz;
+    const double ri = c.r0 + (nr - 1);
+    for (int kz = 0; kz < nz; ++kz) {
+        double num = 0.25 * (c.r0 * uz[kz] * T[kz]), den = 0.25 * (c.r0 * uz[kz]);   /* [0, 1/2] */
+        for (int k = 0; k + 1 < nr; ++k) {
+            const size_t a = (size_t)k * nz + kz, b = (size_t)(k + 1) * nz + kz;
+            const double ra = c.r0 + k, rb = c.r0 + k + 1;
+            num += 0.5 * (ra * uz[a] * T[a] + rb * uz[b] * T[b]);
+            den += 0.5 * (ra * uz[a] + rb * uz[b]);
+        }
+        const double Tb = num / den;
+        const double Tw = T[(size_t)(nr - 1) * nz + kz];
+        const double dTdr = (3 * Tw - 4 * T[(size_t)(nr - 2) * nz + kz] + T[(size_t)(nr - 3) * nz + kz]) / 2;
+        nu[kz] = 2 * ri * dTdr / (Tw - Tb);
+    }
+    return 0;
+}
+
 int orc_residual(const orc_params *p, const double *rho_n, const double *ur_n, const double *uz_n,
                  const double *T_n, const double *ur_p, const double *uz_p, const double *T_p,
                  double *res, double *mass)

@@ -20,8 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbm_oracle.c")
 LIB = os.path.join(HERE, "liblbm_oracle.so")
 
-ANNULUS, ANNULUS_PERIODIC_Z, PIPE_PERIODIC_Z = 0, 1, 2
-FLUID, WALL_IN, WALL_OUT, BOTTOM, TOP, AXIS = 0, 1, 2, 3, 4, 5
+ANNULUS, ANNULUS_PERIODIC_Z, PIPE_PERIODIC_Z, PIPE_INFLOW = 0, 1, 2, 3
+FLUID, WALL_IN, WALL_OUT, BOTTOM, TOP, AXIS, INLET, OUTLET = 0, 1, 2, 3, 4, 5, 6, 7
 
 _lock = threading.Lock()
 _lib = None
@@ -48,7 +48,7 @@ class Params(C.Structure):
         ("lam", C.c_double), ("Ma", C.c_double), ("tau_nu", C.c_double),
         ("F_eps", C.c_double), ("eps_mean", C.c_double),
         ("T_hot", C.c_double), ("T_cold", C.c_double), ("body_accel_z", C.c_double),
-        ("init_noise", C.c_double), ("seed", C.c_uint64),
+        ("init_noise", C.c_double), ("seed", C.c_uint64), ("u_in", C.c_double),
     ]
 
 
@@ -57,7 +57,7 @@ def params(**kw) -> Params:
     Ra = 1e3, Pr = 1, J = lambda = 1, Ma = 0.1, Ergun F_eps, T_hot = 1, T_cold = 0)."""
     d = dict(nr=48, nz=96, geometry=ANNULUS, radius_ratio=2.0, Ra=1e3, Da=1e-2, Pr=1.0, J=1.0,
              lam=1.0, Ma=0.1, tau_nu=0.0, F_eps=-1.0, eps_mean=0.6, T_hot=1.0, T_cold=0.0,
-             body_accel_z=0.0, init_noise=1e-3, seed=1)
+             body_accel_z=0.0, init_noise=1e-3, seed=1, u_in=0.0)
     for k in kw:
         if k not in d:
             raise KeyError(k)
@@ -85,6 +85,7 @@ def lib():
             L.orc_run.argtypes = [pp, dp, dp, dp, C.c_int64, C.c_int]
             L.orc_moments.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp]
             L.orc_nusselt.argtypes = [pp, dp, dp, dp]
+            L.orc_pipe_nusselt.argtypes = [pp, dp, dp, dp]
             L.orc_residual.argtypes = [pp] + [dp] * 9
             L.orc_node_class.argtypes = [pp, C.POINTER(C.c_uint8)]
             L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
@@ -205,6 +206,20 @@ class State:
         b = C.c_double()
         lib().orc_nusselt(C.byref(self.p), _d(T), C.byref(a), C.byref(b))
         return a.value, b.value
+
+    def pipe_nusselt(self):
+        """Local wall Nusselt number Nu(z) of Eq. 40 with the mixing-cup bulk
+        temperature (pipe with inlet and outlet)."""
+        m = self.moments()
+        return pipe_nusselt(self.p, m[2], m[3])
+
+
+def pipe_nusselt(p: Params, uz, T):
+    uz, T = _f64(uz), _f64(T)
+    out = np.zeros(p.nz)
+    if lib().orc_pipe_nusselt(C.byref(p), _d(uz), _d(T), _d(out)):
+        raise ValueError("pipe_nusselt needs the pipe with inlet and outlet")
+    return out
 
 
 def node_update(p: Params, phi, f, g, kr: int, kz: int):

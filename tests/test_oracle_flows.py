@@ -197,3 +197,53 @@ def test_table2_ra1e3_full_grid(oracle):
     st.run(180000, THREADS)
     nu_i, nu_o = st.nusselt()
     assert abs(nu_i / nu_paper - 1) < 0.02
+
+
+# ---- pipe with inlet and outlet (Sec. 4.1, Fig. 1) ----------------------------------
+def _pipe(oracle, nr, nz, tau, u_in, Pr=1.0, Da=1e8):
+    return oracle.params(nr=nr, nz=nz, geometry=oracle.PIPE_INFLOW, Ra=0.0, tau_nu=tau, Da=Da, eps_mean=1.0,
+                         F_eps=0.0, Pr=Pr, u_in=u_in, init_noise=0.0)
+
+
+def _cup(r, f, w):
+    """Trapezoid on r = 0, r_0, ..., r_i of r w f over r w (the integrand is 0 at r = 0)."""
+    num = 0.25 * r[0] * w[0] * f[0] + np.sum(0.5 * (r[:-1] * w[:-1] * f[:-1] + r[1:] * w[1:] * f[1:]))
+    den = 0.25 * r[0] * w[0] + np.sum(0.5 * (r[:-1] * w[:-1] + r[1:] * w[1:]))
+    return num / den
+
+
+def test_pipe_inflow_poiseuille(oracle):
+    """Pipe with a uniform inlet velocity and no porous matrix: downstream of the entrance
+    the axial profile is u_z / u_mean = 2 (1 - r^2 / r_i^2) (Hagen-Poiseuille), converging at
+    second order in the grid, and the mass flux rho u_mean is the same in every section."""
+    dev = []
+    for nr in (11, 21):
+        p = _pipe(oracle, nr, 6 * nr, 0.8, 0.02)
+        st = oracle.State(p)
+        st.run(int(nr * nr * 90), THREADS)
+        rho, ur, uz, T = st.moments()
+        r = oracle.derive(p)["r0"] + np.arange(nr)
+        kz = 4 * nr
+        um = _cup(r, uz[:, kz], np.ones(nr))
+        dev.append(np.abs(uz[:, kz] / um - 2 * (1 - r ** 2 / r[-1] ** 2)).max())
+        flux = [_cup(r, rho[:, z] * uz[:, z], np.ones(nr)) for z in (nr, 3 * nr, 5 * nr)]
+        assert max(flux) - min(flux) < 1e-3 * max(flux), flux
+    assert dev[1] < 0.015 and dev[0] / dev[1] > 3.0, dev
+
+
+def test_pipe_inflow_graetz_nusselt(oracle):
+    """Thermally developing pipe flow at Pe_D = U D / alpha = 140 (Re_D = 100, Pr = 1.4):
+    far downstream the local Nusselt number of Eq. 40 (mixing-cup bulk temperature)
+    settles on the fully developed constant-wall-temperature value 3.6568 (Graetz
+    problem; axial conduction changes it by < 0.1 % at this Pe).  At r_i = 20.5 the
+    scheme's first-order wall error leaves it 2.7 % high (3.757; 3.706 at r_i = 40.5, whose
+    Richardson extrapolation is 3.654)."""
+    nr, nz, U = 21, 700, 0.05
+    nu = (nr - 0.5) * U / 50.0
+    p = _pipe(oracle, nr, nz, 0.5 + 3 * nu, U, Pr=1.4)
+    st = oracle.State(p)
+    st.run(40000, THREADS)
+    Nu = st.pipe_nusselt()
+    a, b = Nu[int(0.75 * nz)], Nu[int(0.9 * nz)]
+    assert abs(a - b) < 5e-3 * b                         # developed
+    assert abs(b / 3.6568 - 1) < 0.035, b
