@@ -58,6 +58,9 @@ extern "C" {
 #define LBM_ANNULUS 0             /* Fig. 3: walls on all four sides */
 #define LBM_ANNULUS_PERIODIC_Z 1  /* side walls only, periodic in z */
 #define LBM_PIPE_PERIODIC_Z 2     /* axis (specular image row) + outer wall, periodic in z */
+#define LBM_PIPE_INFLOW 3         /* Fig. 1 (Sec. 4.1): axis + wall (T_cold), inlet row z = 0
+                                     (u = (0, u_in), T_hot), outlet row z = H (zero gradient of u
+                                     and T, density held at 1); inlet and outlet own their corners */
 
 /* storage type of the distributions between steps (arithmetic is always FP32) */
 #define LBM_F32 0
@@ -71,10 +74,12 @@ extern "C" {
 #define LBM_BOTTOM 3
 #define LBM_TOP 4
 #define LBM_AXIS 5
+#define LBM_INLET 6
+#define LBM_OUTLET 7
 
 typedef struct lbm_params {
     int32_t nr, nz;          /* grid; both >= 3 */
-    int32_t geometry;        /* LBM_ANNULUS, LBM_ANNULUS_PERIODIC_Z, LBM_PIPE_PERIODIC_Z */
+    int32_t geometry;        /* LBM_ANNULUS, LBM_ANNULUS_PERIODIC_Z, LBM_PIPE_PERIODIC_Z, LBM_PIPE_INFLOW */
     int32_t storage;         /* LBM_F32, LBM_F16, LBM_BF16 */
     double radius_ratio;     /* R* = r_o / r_i > 1 (annulus geometries) */
     double Ra, Da, Pr, J, lambda;  /* Eq. 9; the paper uses J = lambda = 1 (Sec. 4) */
@@ -83,10 +88,12 @@ typedef struct lbm_params {
     double F_eps;            /* < 0: Ergun F_phi per node (Eq. 8); 0: no Forchheimer drag; > 0: constant */
     double eps_mean;         /* porosity that, with Da, fixes the particle diameter of Eq. 8;
                                 1 = no solid matrix (K = Da L^2 everywhere) */
-    double T_hot, T_cold;    /* inner and outer wall temperatures; T0 = (T_hot + T_cold) / 2 */
+    double T_hot, T_cold;    /* inner and outer wall temperatures (pipe with inlet: inlet and wall
+                                temperatures); T0 = (T_hot + T_cold) / 2 */
     double body_accel_z;     /* z component of the external acceleration a of Eq. 7 */
     double init_noise;       /* cold start: T = T0 + init_noise * U(-1, 1) on non-wall nodes */
     uint64_t seed;           /* SplitMix64 seed of that noise (draw number kr*nz + kz) */
+    double u_in;             /* LBM_PIPE_INFLOW: inlet velocity U_in (Re = r_i U_in / nu, Sec. 4.1) */
 } lbm_params;
 
 /* Derived lattice constants (Eq. 9, 31, 39), for checks and reporting. */
@@ -146,8 +153,16 @@ int lbm_moments(lbm_handle *h, float *rho, float *ur, float *uz, float *T, int o
 /* Average Nusselt numbers of Eq. 42 on the inner and outer wall of the current
  * state: one-sided second-order dT/dr at the wall, trapezoid rule over the nz wall
  * nodes, H = nz - 1, dT = T_hot - T_cold.  FP64 reduction.  Synchronises.  The
- * inner value is NaN for the pipe. */
+ * inner value is NaN for the pipes; both are NaN for LBM_PIPE_INFLOW (lbm_pipe_nusselt). */
 int lbm_nusselt(lbm_handle *h, double *nu_inner, double *nu_outer);
+
+/* LBM_PIPE_INFLOW only: local wall Nusselt number of Eq. 40 at every column,
+ * Nu(z) = D (dT/dr)_w / (T_w - T_b), D = 2 r_i, into nu[0 .. nz-1] (host memory).
+ * T_b is the mixing-cup temperature int u_z r T dr / int u_z r dr: Eq. 41 as printed
+ * leaves out u_z, which would put the no-porous pipe at Nu = 5.3 instead of the 3.674
+ * of Table 1.  Trapezoid rule on r = 0, 1/2, 3/2, ..., r_i; (dT/dr)_w one-sided,
+ * second order.  FP64.  The inlet column gives NaN (T_w = T_b there).  Synchronises. */
+int lbm_pipe_nusselt(lbm_handle *h, double *nu, int32_t nz);
 
 /* Convergence residual between the current state n and the previous state n - 1:
  * max(|u^n - u^(n-1)|_2 / |u^n|_2, |T^n - T^(n-1)|_2 / |T^n|_2) over non-wall
@@ -258,6 +273,9 @@ int lbm_batch_rebase(lbm_batch *b);
 int lbm_batch_nusselt(lbm_batch *b, double *nu_inner, double *nu_outer);
 /* Fields of instance i, as lbm_moments. */
 int lbm_batch_moments(lbm_batch *b, int32_t i, float *rho, float *ur, float *uz, float *T, int on_device);
+/* lbm_pipe_nusselt of instance i (LBM_PIPE_INFLOW), nu[0 .. nz-1] in host memory.
+ * Synchronises. */
+int lbm_batch_pipe_nusselt(lbm_batch *b, int32_t i, double *nu, int32_t nz);
 /* Autotuner: times `steps` steps for each bulk tile shape (columns x rows per block x
  * rows per thread; twelve shapes of at most 256 threads) and keeps the fastest; *cols and
  * *rows receive the tile's columns and rows, *ms_per_step its time per step.  The state

@@ -83,7 +83,7 @@ constexpr int BULK_RPT_MIN_BLOCKS = LBM_BULK_RPT_MIN_BLOCKS;
 template <int STO, typename R, typename I = int64_t>
 __device__ __forceinline__ void pull_raw(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh,
                                          R* gh) {
-    const bool pz = c.geometry != ANNULUS;
+    const bool pz = c.periodic != 0;
     const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;       // source column for e_z = +1
     const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;       // source column for e_z = -1
     const I row = (I)kr * c.nz;
@@ -138,7 +138,7 @@ __device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I pl
         rref = R(0);
         return;
     }
-    const bool pz = c.geometry != ANNULUS;
+    const bool pz = c.periodic != 0;
     const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;
     const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;
     const I row = (I)kr * c.nz;
@@ -156,12 +156,15 @@ __device__ __forceinline__ void store(const Buf<STO>& B, I plane, I n, const R* 
     for (int i = 0; i < 5; ++i) stv(B.g + i * plane + n, float(gh[i]));
 }
 
-// Wall node state: rebuild (Sec. 4, ref. [47]) from the interior neighbour, then
-// rho from Eq. 26 and the wall temperature (T_hot, T_cold, or T_f when adiabatic).
+// Boundary node state: rebuild (Sec. 4, ref. [47]) from the interior neighbour, then
+// rho from Eq. 26.  Walls: u_b = 0, rho_b = rho_f, T_b = T_hot (inner), T_cold (outer),
+// T_f (adiabatic top and bottom).  Pipe inlet: u_b = (0, u_in), rho_b = rho_f, T_b = T_hot;
+// outlet: u_b = u_f, T_b = T_f, rho_b = 1 (zero gradient of u and T, density held).
 template <int STO, typename R>
 __device__ __forceinline__ void wall_state(const Consts<R>& c, const Buf<STO> A,
                                            const typename St<STO>::P* __restrict__ phi, int64_t plane, int cls,
-                                           int kr, int kz, R* fh, R* gh, R& m0, R& rho, R& dTb, R& refb) {
+                                           int kr, int kz, R* fh, R* gh, R& m0, R& rho, R& urb, R& uzb, R& dTb,
+                                           R& refb) {
     int fr, fz;
     fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
     R fhf[9], ghf[5], reff;
@@ -171,18 +174,43 @@ __device__ __forceinline__ void wall_state(const Consts<R>& c, const Buf<STO> A,
     R m0f, rhof, urf, uzf, dTf, lin, nl, ipf;
     porous(c, phif, lin, nl, ipf);
     recover(c, rf, rcp_acc(rf), phif, lin, nl, fhf, ghf, reff, m0f, rhof, urf, uzf, dTf);
-    rebuild_flow(rb, rf, ipf, m0f, rhof, urf, uzf, fhf, fh);
-    // deviations relative to this wall node's own reference R_b
+    R drhob = m0f * rcp_acc(rf), rhob = rhof;
+    urb = R(0);
+    uzb = R(0);
+    R ipb = R(1);
+    if (cls == INLET) {
+        uzb = c.u_in;
+    } else if (cls == OUTLET) {
+        urb = urf;
+        uzb = uzf;
+        drhob = R(0);
+        rhob = R(1);
+    }
+    if (cls >= INLET) ipb = rcp_acc(R(ldv(phi + (int64_t)kr * c.nz + kz)));
+    rebuild_flow(rb, rf, ipb, ipf, drhob, rhob, urb, uzb, m0f, rhof, urf, uzf, fhf, fh);
+    // deviations relative to this boundary node's own reference R_b
     refb = has_ref<STO>() ? R(__half2float(c.tref[(int64_t)kr * c.nz + kz])) : R(0);
-    dTb = cls == WALL_IN ? (c.T_hot - c.T0) - refb : cls == WALL_OUT ? (c.T_cold - c.T0) - refb : (dTf + reff) - refb;
-    rebuild_thermal(c.T0 + reff, dTf, dTb, urf, uzf, ghf, gh);
+    dTb = (cls == WALL_IN || cls == INLET) ? (c.T_hot - c.T0) - refb
+          : cls == WALL_OUT                 ? (c.T_cold - c.T0) - refb
+                                            : (dTf + reff) - refb;
+    rebuild_thermal(c.T0 + reff, dTf, c.T0 + refb, dTb, urb, uzb, urf, uzf, ghf, gh);
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
     rho = R(1) + m0 * rcp_acc(rb);
 }
 
-// Wall node t -> (kr, kz): inner wall (annulus), outer wall, then bottom and top
-// without the corners (closed annulus).
+// Boundary node t -> (kr, kz): inner wall (annulus), outer wall, then bottom and top
+// without the corners (closed annulus).  Pipe with inlet: inlet row, outlet row, then
+// the wall without the corners.
 __device__ __forceinline__ void wall_node(int geometry, int nr, int nz, int t, int& kr, int& kz) {
+    if (geometry == PIPE_INFLOW) {
+        if (t < nr) { kr = t; kz = 0; return; }
+        t -= nr;
+        if (t < nr) { kr = t; kz = nz - 1; return; }
+        t -= nr;
+        kr = nr - 1;
+        kz = 1 + t;
+        return;
+    }
     if (geometry != PIPE_PERIODIC_Z) {
         if (t < nz) { kr = 0; kz = t; return; }
         t -= nz;
@@ -198,6 +226,7 @@ __device__ __forceinline__ void wall_node(int geometry, int nr, int nz, int t, i
 static int wall_count(int geometry, int nr, int nz) {
     if (geometry == ANNULUS) return 2 * nz + 2 * (nr - 2);
     if (geometry == ANNULUS_PERIODIC_Z) return 2 * nz;
+    if (geometry == PIPE_INFLOW) return 2 * nr + nz - 2;
     return nz;
 }
 
@@ -209,11 +238,15 @@ template <int STO, typename I>
 __device__ __forceinline__ void update_column(const Consts<float>& c, const Buf<STO>& A, const Buf<STO>& B,
                                               const typename St<STO>::P* __restrict__ phi, I plane, int kr0,
                                               int rows, int kz) {
+    // node_class split into its column and row parts: the end columns are boundary
+    // nodes unless z is periodic; row nr - 1 is a wall, row 0 too unless it is a pipe axis
+    const bool zwall = !c.periodic && (kz == 0 || kz == c.nz - 1);
+    const bool row0_wall = c.geometry == ANNULUS || c.geometry == ANNULUS_PERIODIC_Z;
 #pragma unroll 1
     for (int j = 0; j < rows; ++j) {
         const int kr = kr0 + j;
         if (kr >= c.nr) break;
-        if (is_wall(node_class(c.geometry, c.nr, c.nz, kr, kz))) continue;
+        if (zwall || kr == c.nr - 1 || (kr == 0 && row0_wall)) continue;
         float fh[9], gh[5], ref;
         pull<STO, float, I>(c, A, plane, kr, kz, fh, gh, ref);
         const I n = (I)kr * c.nz + kz;
@@ -230,8 +263,15 @@ __device__ __forceinline__ void update_column(const Consts<float>& c, const Buf<
 // One thread per column segment of RPT rows: the column's index arithmetic, the
 // kernel-argument loads and the class checks are shared by RPT nodes.
 // I: index type; 32-bit when the state buffer holds fewer than 2^31 elements.
+// Resident blocks of 128 threads per SM the register allocation must allow.  16-bit flow
+// storage is issue-bound: ten blocks (48 registers) beat nine (measured 0.5306 vs
+// 0.5425 ms at 4096 x 8192); FP32 is bandwidth-bound and does best at nine (56
+// registers: 0.6083 ms, against 0.6376 at ten).
+template <int STO>
+constexpr int bulk_min_blocks() { return STO == LBM_F32 ? 9 : 10; }
+
 template <int STO, typename I, int RPT>
-__global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
+__global__ void __launch_bounds__(BULK_THREADS, bulk_min_blocks<STO>()) k_bulk(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
                                                        const typename St<STO>::P* __restrict__ phi, I plane) {
     const int kz = blockIdx.x * BULK_THREADS + threadIdx.x;
     if (kz >= c.nz) return;
@@ -247,13 +287,13 @@ __global__ void k_wall(const Consts<float> c, const Buf<STO> A,
     int kr, kz;
     wall_node(c.geometry, c.nr, c.nz, t, kr, kz);
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
-    float fh[9], gh[5], m0, rho, dTb, refb;
-    wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dTb, refb);
+    float fh[9], gh[5], m0, rho, urb, uzb, dTb, refb;
+    wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, urb, uzb, dTb, refb);
     const int64_t n = (int64_t)kr * c.nz + kz;
     const float r = c.r0 + float(kr), ph = ldv(phi + n);
     float lin, nl, iph;
     porous(c, ph, lin, nl, iph);
-    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, 0.0f, 0.0f, dTb);
+    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, urb, uzb, dTb);
     store<STO>(B, plane, n, fh, gh);
 }
 
@@ -269,7 +309,7 @@ __global__ void k_moments(const Consts<float> c, const Buf<STO> A,
     const int64_t n = (int64_t)kr * c.nz + kz;
     float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT, ref;
     if (is_wall(cls)) {
-        wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, dT, ref);
+        wall_state<STO>(c, A, phi, plane, cls, kr, kz, fh, gh, m0, rho, ur, uz, dT, ref);
     } else {
         pull<STO>(c, A, plane, kr, kz, fh, gh, ref);
         const float r = c.r0 + float(kr), ph = ldv(phi + n);
@@ -313,7 +353,10 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
     double T = start_T(c, T_in, noise, seed, n), ur = 0, uz = 0;
     if (cls == WALL_IN) T = c.T_hot;
     else if (cls == WALL_OUT) T = c.T_cold;
-    else if (cls == BOTTOM || cls == TOP) {
+    else if (cls == INLET) {
+        T = c.T_hot;
+        uz = c.u_in;
+    } else if (cls == BOTTOM || cls == TOP || cls == OUTLET) {
         int fr, fz;
         fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
         T = start_T(c, T_in, noise, seed, (int64_t)fr * c.nz + fz);
@@ -356,7 +399,7 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
     gh[2] = 0.1 * dTs + 0.5 * T * uz;
     gh[3] = 0.1 * dTs - 0.5 * T * ur;
     gh[4] = 0.1 * dTs - 0.5 * T * uz;
-    double m0, rho, u_r = 0, u_z = 0, dT;
+    double m0, rho, u_r = ur, u_z = uz, dT;   // boundary nodes keep their start velocity
     if (is_wall(cls)) {
         m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
         rho = 1 + m0 * inv_r;
@@ -461,9 +504,9 @@ template <int STO>
 __device__ double node_T(const Consts<float>& c, const Buf<STO> A, int64_t plane, int kr,
                          int kz) {
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
-    if (cls == WALL_IN) return (double)c.T_hot;
+    if (cls == WALL_IN || cls == INLET) return (double)c.T_hot;
     if (cls == WALL_OUT) return (double)c.T_cold;
-    if (cls == BOTTOM || cls == TOP) {
+    if (cls == BOTTOM || cls == TOP || cls == OUTLET) {
         int fr, fz;
         fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
         kr = fr;
@@ -494,6 +537,26 @@ __global__ void __launch_bounds__(256) k_nusselt(const Consts<float> c, const Bu
         result[0] = -ri * out[0] / (H * dTw);
         result[1] = -ro * out[1] / (H * dTw);
     }
+}
+
+// Eq. 40 per column for the pipe with inlet and outlet: Nu(z) = D (dT/dr)_w / (T_w - T_b)
+// with the mixing-cup T_b = int u_z r T dr / int u_z r dr (trapezoid on r = 0, r0, r0 + 1,
+// ..., r_i; the integrand is 0 at r = 0) and the one-sided second-order wall derivative.
+// uz, T: field planes (row stride nz).  One thread per column, FP64.
+__global__ void k_pipe_nusselt(int nr, int nz, double r0, const float* __restrict__ uz, const float* __restrict__ T,
+                               double* __restrict__ nu) {
+    const int kz = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kz >= nz) return;
+    double num = 0.25 * (r0 * (double)uz[kz] * (double)T[kz]), den = 0.25 * (r0 * (double)uz[kz]);
+    for (int k = 0; k + 1 < nr; ++k) {
+        const int64_t a = (int64_t)k * nz + kz, b = a + nz;
+        const double ra = r0 + k, rb = r0 + k + 1;
+        num += 0.5 * (ra * (double)uz[a] * (double)T[a] + rb * (double)uz[b] * (double)T[b]);
+        den += 0.5 * (ra * (double)uz[a] + rb * (double)uz[b]);
+    }
+    const double Tw = T[(int64_t)(nr - 1) * nz + kz];
+    const double dTdr = (3 * Tw - 4 * (double)T[(int64_t)(nr - 2) * nz + kz] + (double)T[(int64_t)(nr - 3) * nz + kz]) / 2;
+    nu[kz] = 2 * (r0 + (nr - 1)) * dTdr / (Tw - num / den);
 }
 
 // FP64 export of rows [row0, row0 + nrows): raw post-collision populations
@@ -591,13 +654,13 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
     if (!p) return fail(LBM_ERR_INVALID, "params is NULL");
     if (p->nr < 3 || p->nz < 3) return fail(LBM_ERR_INVALID, "grid %d x %d: need nr, nz >= 3", p->nr, p->nz);
     if (p->nr > 65535) return fail(LBM_ERR_INVALID, "nr = %d exceeds 65535", p->nr);
-    if (p->geometry < 0 || p->geometry > 2) return fail(LBM_ERR_INVALID, "unknown geometry %d", p->geometry);
+    if (p->geometry < 0 || p->geometry > 3) return fail(LBM_ERR_INVALID, "unknown geometry %d", p->geometry);
     if (p->storage < 0 || p->storage > 2) return fail(LBM_ERR_INVALID, "unknown storage %d", p->storage);
     if (!(p->J > 0) || !(p->lambda > 0) || !(p->Pr > 0))
         return fail(LBM_ERR_INVALID, "J, lambda and Pr must be positive");
     if (!(p->eps_mean > 0 && p->eps_mean <= 1)) return fail(LBM_ERR_INVALID, "eps_mean %g outside (0, 1]", p->eps_mean);
     const double cs = std::sqrt(1.0 / 3.0);
-    if (p->geometry == PIPE_PERIODIC_Z) {
+    if (p->geometry == PIPE_PERIODIC_Z || p->geometry == PIPE_INFLOW) {
         o->r0 = 0.5;
         o->L = (p->nr - 1) + 0.5;
     } else {
@@ -635,6 +698,7 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         c.nr = p->nr;
         c.nz = p->nz;
         c.geometry = p->geometry;
+        c.periodic = periodic_z(p->geometry) ? 1 : 0;
         c.porous_mode = !(p->Da > 0) ? 0 : (p->eps_mean >= 1 ? 1 : 2);
         c.ergun = p->F_eps < 0;
         c.r0 = o->r0;
@@ -650,6 +714,7 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         c.gbeta = o->gbeta;
         c.T0 = o->T0;
         c.az = p->body_accel_z;
+        c.u_in = p->u_in;
         // Eq. 8 coefficients (see porous()): 1/K(phi) = c_k (1 - phi)^2 / phi^3 with
         // c_k = eps_mean^3 / ((1 - eps_mean)^2 Da L^2), i.e. K(eps_mean) = Da L^2.
         const double em = p->eps_mean;
@@ -670,12 +735,13 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
 
 static Consts<float> to_float(const Consts<double>& d) {
     Consts<float> f;
-    f.nr = d.nr; f.nz = d.nz; f.geometry = d.geometry; f.porous_mode = d.porous_mode; f.ergun = d.ergun; f.pad = 0;
+    f.nr = d.nr; f.nz = d.nz; f.geometry = d.geometry; f.porous_mode = d.porous_mode; f.ergun = d.ergun; f.periodic = d.periodic;
     f.r0 = (float)d.r0; f.cs2tau = (float)d.cs2tau; f.two_taum = (float)d.two_taum;
     f.s_e = (float)d.s_e; f.s_eps = (float)d.s_eps; f.s_j = (float)d.s_j; f.s_q = (float)d.s_q; f.s_nu = (float)d.s_nu;
     f.tauT = (float)d.tauT; f.wg_den = (float)d.wg_den; f.gbeta = (float)d.gbeta; f.T0 = (float)d.T0;
     f.az = (float)d.az; f.lin_coef = (float)d.lin_coef; f.nl_coef = (float)d.nl_coef;
     f.T_hot = (float)d.T_hot; f.T_cold = (float)d.T_cold;
+    f.u_in = (float)d.u_in;
     f.tref = d.tref;
     return f;
 }
@@ -970,6 +1036,11 @@ int lbm_moments(lbm_handle* h, float* rho, float* ur, float* uz, float* T, int o
 
 int lbm_nusselt(lbm_handle* h, double* nu_inner, double* nu_outer) {
     if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    if (h->p.geometry == LBM_PIPE_INFLOW) {   // Eq. 42 has no meaning there: lbm_pipe_nusselt
+        if (nu_inner) *nu_inner = NAN;
+        if (nu_outer) *nu_outer = NAN;
+        return LBM_OK;
+    }
     CK(cudaSetDevice(h->device));
     const double dTw = h->p.T_hot - h->p.T_cold;
     const double ri = h->info.r0, ro = h->info.r0 + (h->p.nr - 1);
@@ -1052,6 +1123,26 @@ int lbm_run(lbm_handle* h, int64_t max_steps, int64_t check_every, double tol, i
     if (steps_done) *steps_done = done;
     if (res) *res = r;
     return rc;
+}
+
+int lbm_pipe_nusselt(lbm_handle* h, double* nu, int32_t nz) {
+    if (!h || !nu) return fail(LBM_ERR_INVALID, "NULL argument");
+    if (h->p.geometry != LBM_PIPE_INFLOW) return fail(LBM_ERR_INVALID, "lbm_pipe_nusselt needs LBM_PIPE_INFLOW");
+    if (nz != h->p.nz) return fail(LBM_ERR_INVALID, "nz = %d, the grid has %d", nz, h->p.nz);
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_mac(h);
+    if (rc) return rc;
+    if ((rc = snapshot(h, h->cur, h->mac))) return rc;
+    double* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, (size_t)nz * sizeof(double), h->stream));
+    k_pipe_nusselt<<<(unsigned)((nz + 127) / 128), 128, 0, h->stream>>>(h->p.nr, nz, h->info.r0, h->mac + 2 * h->mstride,
+                                                                       h->mac + 3 * h->mstride, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nu, d, (size_t)nz * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "pipe Nusselt: %s", cudaGetErrorString(e));
+    return LBM_OK;
 }
 
 int lbm_rebase(lbm_handle* h) {
@@ -1152,7 +1243,7 @@ extern "C" int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t 
                                           const float* prev, int64_t field_stride, double* res, double* mass,
                                           void* stream) {
     if (!cur || !prev || !res || !mass) return fail(LBM_ERR_INVALID, "NULL argument");
-    if (geometry < 0 || geometry > 2) return fail(LBM_ERR_INVALID, "unknown geometry %d", geometry);
+    if (geometry < 0 || geometry > 3) return fail(LBM_ERR_INVALID, "unknown geometry %d", geometry);
     if (nr < 3 || nz < 3 || nr > 65535 || nz > 65535 || (int64_t)nr * nz >= ((int64_t)1 << 31))
         return fail(LBM_ERR_INVALID, "grid %d x %d outside 3..65535 per side with nr*nz < 2^31", nr, nz);
     const int64_t N = (int64_t)nr * nz;
@@ -1263,13 +1354,13 @@ __global__ void k_batch_wall(const InstDesc* __restrict__ desc, char* __restrict
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
     const Buf<STO> A = inst_buf<STO>(d, pool, parity), B = inst_buf<STO>(d, pool, parity ^ 1);
     const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
-    float fh[9], gh[5], m0, rho, dTb, refb;
-    wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dTb, refb);
+    float fh[9], gh[5], m0, rho, urb, uzb, dTb, refb;
+    wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, urb, uzb, dTb, refb);
     const int64_t n = (int64_t)kr * c.nz + kz;
     const float r = c.r0 + float(kr), ph = ldv(phi + n);
     float lin, nl, iph;
     porous(c, ph, lin, nl, iph);
-    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, 0.0f, 0.0f, dTb);
+    collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, urb, uzb, dTb);
     store<STO>(B, d.plane, n, fh, gh);
 }
 
@@ -1294,7 +1385,7 @@ __global__ void __launch_bounds__(256) k_batch_moments(const InstDesc* __restric
         const int64_t n = (int64_t)kr * c.nz + kz;
         float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT, ref;
         if (is_wall(cls)) {
-            wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, dT, ref);
+            wall_state<STO>(c, A, phi, d.plane, cls, kr, kz, fh, gh, m0, rho, ur, uz, dT, ref);
         } else {
             pull<STO>(c, A, d.plane, kr, kz, fh, gh, ref);
             const float r = c.r0 + float(kr), ph = ldv(phi + n);
@@ -1795,9 +1886,34 @@ int lbm_batch_nusselt(lbm_batch* b, double* nu_inner, double* nu_outer) {
     CK(cudaMemcpyAsync(r.data(), b->result, r.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
     for (int i = 0; i < b->n; ++i) {
-        nu_inner[i] = b->p[i].geometry == LBM_PIPE_PERIODIC_Z ? NAN : r[2 * i];
-        nu_outer[i] = r[2 * i + 1];
+        nu_inner[i] = b->p[i].geometry == LBM_PIPE_PERIODIC_Z || b->p[i].geometry == LBM_PIPE_INFLOW ? NAN : r[2 * i];
+        nu_outer[i] = b->p[i].geometry == LBM_PIPE_INFLOW ? NAN : r[2 * i + 1];
     }
+    return LBM_OK;
+}
+
+int lbm_batch_pipe_nusselt(lbm_batch* b, int32_t i, double* nu, int32_t nz) {
+    if (!b || !nu || i < 0 || i >= b->n) return fail(LBM_ERR_INVALID, "bad batch, instance or pointer");
+    if (b->p[i].geometry != LBM_PIPE_INFLOW) return fail(LBM_ERR_INVALID, "instance %d is not LBM_PIPE_INFLOW", i);
+    if (nz != b->p[i].nz) return fail(LBM_ERR_INVALID, "nz = %d, instance %d has %d", nz, i, b->p[i].nz);
+    CK(cudaSetDevice(b->device));
+    const InstDesc& d = b->desc[i];
+    float* m = b->macpool + d.off_mac;   // snapshot slot 0 of this instance as staging
+    const dim3 g((unsigned)((nz + 127) / 128), (unsigned)b->p[i].nr);
+    DISPATCH_STO(b->storage, k_moments<S_><<<g, 128, 0, b->stream>>>(d.c, batch_buf<S_>(b, i, b->cur_parity(i)),
+                                                                      (const PP<S_>*)(b->pool + d.off_phi), d.plane,
+                                                                      nullptr, nullptr, m + 2 * d.plane,
+                                                                      m + 3 * d.plane));
+    CK(cudaGetLastError());
+    double* dn = nullptr;
+    CK(cudaMallocAsync((void**)&dn, (size_t)nz * sizeof(double), b->stream));
+    k_pipe_nusselt<<<(unsigned)((nz + 127) / 128), 128, 0, b->stream>>>(b->p[i].nr, nz, d.r0, m + 2 * d.plane,
+                                                                        m + 3 * d.plane, dn);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nu, dn, (size_t)nz * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    cudaFreeAsync(dn, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "batch pipe Nusselt: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 

@@ -27,8 +27,8 @@
 
 namespace lbm {
 
-enum { ANNULUS = 0, ANNULUS_PERIODIC_Z = 1, PIPE_PERIODIC_Z = 2 };
-enum { FLUID = 0, WALL_IN = 1, WALL_OUT = 2, BOTTOM = 3, TOP = 4, AXIS = 5 };
+enum { ANNULUS = 0, ANNULUS_PERIODIC_Z = 1, PIPE_PERIODIC_Z = 2, PIPE_INFLOW = 3 };
+enum { FLUID = 0, WALL_IN = 1, WALL_OUT = 2, BOTTOM = 3, TOP = 4, AXIS = 5, INLET = 6, OUTLET = 7 };
 
 // Lattice constants, in the arithmetic type R of the kernel that uses them.
 template <typename R>
@@ -36,7 +36,7 @@ struct Consts {
     int nr, nz, geometry;
     int porous_mode;   // 0: no drag; 1: K = Da L^2 everywhere; 2: K(phi) from Eq. 8
     int ergun;         // 1: F_phi from Eq. 8 per node; 0: constant F_eps
-    int pad;
+    int periodic;      // 1: periodic in z (ANNULUS_PERIODIC_Z, PIPE_PERIODIC_Z)
     R r0;              // r(kr = 0)
     R cs2tau;          // c_s^2 (tau - 1/2)
     R two_taum;        // 2 (tau - 1/2)
@@ -46,6 +46,7 @@ struct Consts {
     R lin_coef;        // nu / K = lin_coef (mode 1) or lin_coef (1 - phi)^2 / phi^3 (mode 2)
     R nl_coef;         // F_phi / sqrt(K), see porous()
     R T_hot, T_cold;
+    R u_in;               // inlet velocity (PIPE_INFLOW)
     const __half* tref;   // per-node reference offset R(x) (FP16, one plane)
 };
 
@@ -71,16 +72,24 @@ __device__ __forceinline__ float sqrt_fast(float x) { return x > 0.0f ? x * rsqr
 __device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
 
 // Node class (Fig. 1, Fig. 3): walls on the outermost nodes, corners on the side walls.
+__host__ __device__ __forceinline__ bool periodic_z(int geometry) {
+    return geometry == ANNULUS_PERIODIC_Z || geometry == PIPE_PERIODIC_Z;
+}
 __host__ __device__ __forceinline__ int node_class(int geometry, int nr, int nz, int kr, int kz) {
+    if (geometry == PIPE_INFLOW) {   // Fig. 1: the wall is 0 < z < H; inlet and outlet own the corners
+        if (kz == 0) return INLET;
+        if (kz == nz - 1) return OUTLET;
+    }
     if (kr == nr - 1) return WALL_OUT;
-    if (kr == 0) return geometry == PIPE_PERIODIC_Z ? AXIS : WALL_IN;
+    if (kr == 0) return (geometry == PIPE_PERIODIC_Z || geometry == PIPE_INFLOW) ? AXIS : WALL_IN;
     if (geometry == ANNULUS) {
         if (kz == 0) return BOTTOM;
         if (kz == nz - 1) return TOP;
     }
     return FLUID;
 }
-__host__ __device__ __forceinline__ bool is_wall(int cls) { return cls >= WALL_IN && cls <= TOP; }
+// Boundary nodes rebuilt by non-equilibrium extrapolation (walls, inlet, outlet).
+__host__ __device__ __forceinline__ bool is_wall(int cls) { return (cls >= WALL_IN && cls <= TOP) || cls >= INLET; }
 
 // Interior neighbour a wall node extrapolates from (wall normal; corners diagonal).
 __device__ __forceinline__ void fluid_neighbour(int geometry, int nr, int nz, int cls, int kr, int kz,
@@ -89,8 +98,9 @@ __device__ __forceinline__ void fluid_neighbour(int geometry, int nr, int nz, in
     fz = kz;
     if (cls == WALL_IN) fr = 1;
     else if (cls == WALL_OUT) fr = nr - 2;
-    else if (cls == BOTTOM) fz = 1;
-    else if (cls == TOP) fz = nz - 2;
+    else if (cls == BOTTOM || cls == INLET) fz = 1;
+    else if (cls == TOP || cls == OUTLET) fz = nz - 2;
+    if ((cls == INLET || cls == OUTLET) && kr == nr - 1) fr = nr - 2;
     if ((cls == WALL_IN || cls == WALL_OUT) && geometry == ANNULUS) {
         if (kz == 0) fz = 1;
         if (kz == nz - 1) fz = nz - 2;
@@ -257,38 +267,45 @@ __host__ __device__ constexpr int ez9(int i) { return (i == 2 || i == 5 || i == 
 __host__ __device__ constexpr int mirror9(int i) { return i == 1 ? 3 : i == 3 ? 1 : i == 5 ? 6 : i == 6 ? 5 : i == 7 ? 8 : i == 8 ? 7 : i; }
 template <typename R> __host__ __device__ constexpr R w9(int i) { return i == 0 ? R(4) / R(9) : i < 5 ? R(1) / R(9) : R(1) / R(36); }
 
-// Wall node rebuild by non-equilibrium extrapolation (Sec. 4, ref. [47]) from the
-// interior neighbour's pre-collision deviations (fhf at radius rf; iphi = 1/phi_f):
-//   f_b = f_eq(r_b, rho_f, 0) + [f_f - f_eq(r_f, rho_f, u_f)]      (Eq. 32)
-// In deviations: fh_b,i = r_b w_i drho_f + fh_f,i - r_f w_i [drho_f + rho_f (3 eu
-// + 4.5 eu^2 / phi_f - 1.5 u^2 / phi_f)], drho_f = m0f / r_f.
+// Boundary node rebuild by non-equilibrium extrapolation (Sec. 4, ref. [47]) from the
+// interior neighbour's pre-collision deviations (fhf at radius rf; iphif = 1/phi_f):
+//   f_b = f_eq(r_b, rho_b, u_b) + [f_f - f_eq(r_f, rho_f, u_f)]      (Eq. 32)
+// In deviations: fh_b,i = r_b w_i [drho_b + rho_b (3 eu_b + 4.5 eu_b^2 / phi_b - 1.5 u_b^2
+// / phi_b)] + fh_f,i - r_f w_i [drho_f + rho_f (3 eu + 4.5 eu^2 / phi_f - 1.5 u^2 / phi_f)],
+// drho = rho - 1, drho_f = m0f / r_f.  Walls: u_b = 0, rho_b = rho_f.
 template <typename R>
-__device__ __forceinline__ void rebuild_flow(R rb, R rf, R iphi, R m0f, R rhof, R urf, R uzf, const R* fhf,
-                                             R* fh) {
+__device__ __forceinline__ void rebuild_flow(R rb, R rf, R iphib, R iphif, R drhob, R rhob, R urb, R uzb, R m0f,
+                                             R rhof, R urf, R uzf, const R* fhf, R* fh) {
     const R drho = m0f * rcp_acc(rf);
     const R u2 = urf * urf + uzf * uzf;
+    const R ub2 = urb * urb + uzb * uzb;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const R eu = R(ex9(i)) * urf + R(ez9(i)) * uzf;
-        const R q = drho + rhof * (R(3) * eu + R(4.5) * eu * eu * iphi - R(1.5) * u2 * iphi);
-        fh[i] = rb * w9<R>(i) * drho + fhf[i] - rf * w9<R>(i) * q;
+        const R q = drho + rhof * (R(3) * eu + R(4.5) * eu * eu * iphif - R(1.5) * u2 * iphif);
+        const R eb = R(ex9(i)) * urb + R(ez9(i)) * uzb;
+        const R qb = drhob + rhob * (R(3) * eb + R(4.5) * eb * eb * iphib - R(1.5) * ub2 * iphib);
+        fh[i] = rb * w9<R>(i) * qb + fhf[i] - rf * w9<R>(i) * q;
     }
 }
 
-// Thermal part of the wall rebuild: g_b = g_eq(T_b, 0) + [g_f - g_eq(T_f, u_f)]
-// (Eq. 35); in deviations gh_b,i = wT_i dTb + gh_f,i - (g_eq,i(T_f, u_f) - wT_i Tf0) with
-// dTb = T_b - T0 - R_b, Tf0 = T0 + R_f the fluid neighbour's reference, dTf = T_f - Tf0.
+// Thermal part of the boundary rebuild: g_b = g_eq(T_b, u_b) + [g_f - g_eq(T_f, u_f)]
+// (Eq. 35); in deviations gh_b,i = (g_eq,i(T_b, u_b) - wT_i Tb0) + gh_f,i - (g_eq,i(T_f, u_f)
+// - wT_i Tf0) with dTb = T_b - Tb0, Tb0 = T0 + R_b, Tf0 = T0 + R_f the neighbour's reference,
+// dTf = T_f - Tf0.
 template <typename R>
-__device__ __forceinline__ void rebuild_thermal(R Tf0, R dTf, R dTb, R urf, R uzf, const R* ghf, R* gh) {
-    const R Tf = Tf0 + dTf;
+__device__ __forceinline__ void rebuild_thermal(R Tf0, R dTf, R Tb0, R dTb, R urb, R uzb, R urf, R uzf, const R* ghf,
+                                                R* gh) {
+    const R Tf = Tf0 + dTf, Tb = Tb0 + dTb;
     const R tr = R(0.5) * Tf * urf, tz = R(0.5) * Tf * uzf;
+    const R br = R(0.5) * Tb * urb, bz = R(0.5) * Tb * uzb;
     const R d = dTb - dTf;
     const R t1 = R(0.1) * d;
     gh[0] = ghf[0] + (d - R(4) * t1);
-    gh[1] = ghf[1] + (t1 - tr);
-    gh[2] = ghf[2] + (t1 - tz);
-    gh[3] = ghf[3] + (t1 + tr);
-    gh[4] = ghf[4] + (t1 + tz);
+    gh[1] = ghf[1] + (t1 - tr + br);
+    gh[2] = ghf[2] + (t1 - tz + bz);
+    gh[3] = ghf[3] + (t1 + tr - br);
+    gh[4] = ghf[4] + (t1 + tz - bz);
 }
 
 }  // namespace lbm

@@ -18,9 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 LBM_OK, LBM_ERR_INVALID, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT = range(6)
-LBM_ANNULUS, LBM_ANNULUS_PERIODIC_Z, LBM_PIPE_PERIODIC_Z = 0, 1, 2
+LBM_ANNULUS, LBM_ANNULUS_PERIODIC_Z, LBM_PIPE_PERIODIC_Z, LBM_PIPE_INFLOW = 0, 1, 2, 3
 LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2
-LBM_FLUID, LBM_WALL_IN, LBM_WALL_OUT, LBM_BOTTOM, LBM_TOP, LBM_AXIS = range(6)
+LBM_FLUID, LBM_WALL_IN, LBM_WALL_OUT, LBM_BOTTOM, LBM_TOP, LBM_AXIS, LBM_INLET, LBM_OUTLET = range(8)
 STORAGE = {"f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
 
 
@@ -37,7 +37,7 @@ class lbm_params(C.Structure):
         ("Ra", C.c_double), ("Da", C.c_double), ("Pr", C.c_double), ("J", C.c_double), ("lam", C.c_double),
         ("Ma", C.c_double), ("tau_nu", C.c_double), ("F_eps", C.c_double), ("eps_mean", C.c_double),
         ("T_hot", C.c_double), ("T_cold", C.c_double), ("body_accel_z", C.c_double),
-        ("init_noise", C.c_double), ("seed", C.c_uint64),
+        ("init_noise", C.c_double), ("seed", C.c_uint64), ("u_in", C.c_double),
     ]
 
 
@@ -63,6 +63,7 @@ _SIGS = {
     "lbm_step": (C.c_int, [_vp, C.c_int64]),
     "lbm_moments": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int]),
     "lbm_nusselt": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lbm_pipe_nusselt": (C.c_int, [_vp, _vp, C.c_int32]),
     "lbm_residual": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "lbm_rebase": (C.c_int, [_vp]),
@@ -81,6 +82,7 @@ _SIGS = {
     "lbm_batch_step": (C.c_int, [_vp, C.c_int64]),
     "lbm_batch_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, _vp, _vp]),
     "lbm_batch_rebase": (C.c_int, [_vp]),
+    "lbm_batch_pipe_nusselt": (C.c_int, [_vp, C.c_int32, _vp, C.c_int32]),
     "lbm_batch_nusselt": (C.c_int, [_vp, _vp, _vp]),
     "lbm_batch_moments": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_int]),
     "lbm_batch_tune": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -171,6 +173,12 @@ def lbm_step(h, nsteps: int):
 
 def lbm_moments(h, rho, ur, uz, T, on_device: bool):
     _check(load().lbm_moments(h, _ptr(rho), _ptr(ur), _ptr(uz), _ptr(T), int(on_device)))
+
+
+def lbm_pipe_nusselt(h, nz: int):
+    out = np.zeros(nz, np.float64)
+    _check(load().lbm_pipe_nusselt(h, out.ctypes.data, int(nz)))
+    return out
 
 
 def lbm_nusselt(h):
@@ -282,6 +290,9 @@ class Solver:
     def nusselt(self):
         return lbm_nusselt(self.h)
 
+    def pipe_nusselt(self):
+        return lbm_pipe_nusselt(self.h, self.nz)
+
     def residual(self):
         return lbm_residual(self.h)
 
@@ -336,6 +347,12 @@ def lbm_batch_run(b, n: int, max_steps: int, check_every: int, tol: float):
 
 def lbm_batch_rebase(b):
     _check(load().lbm_batch_rebase(b))
+
+
+def lbm_batch_pipe_nusselt(b, i: int, nz: int):
+    out = np.zeros(nz, np.float64)
+    _check(load().lbm_batch_pipe_nusselt(b, int(i), out.ctypes.data, int(nz)))
+    return out
 
 
 def lbm_batch_nusselt(b, n: int):
@@ -399,6 +416,9 @@ class Batch:
 
     def rebase(self):
         lbm_batch_rebase(self.b)
+
+    def pipe_nusselt(self, i):
+        return lbm_batch_pipe_nusselt(self.b, i, self.params[i].nz)
 
     def nusselt(self):
         return lbm_batch_nusselt(self.b, self.n)
