@@ -55,6 +55,8 @@ typedef struct orc_params {
     double init_noise;                   /* amplitude of the uniform start-temperature noise */
     uint64_t seed;
     double u_in;                         /* inlet velocity U_in (pipe with inlet and outlet, Sec. 4.1) */
+    double heater_len;                   /* > 0: isoflux discrete heater on the inner wall (Sec. 4.4), l / H */
+    double heater_center;                /* its centre h / H */
 } orc_params;
 
 typedef struct orc_consts {
@@ -159,7 +161,8 @@ int orc_derive(const orc_params *p, orc_consts *c)
     } else {
         c->gbeta = 0.0;
     }
-    c->T0 = 0.5 * (p->T_hot + p->T_cold);                                        /* Sec. 4.2 */
+    /* Sec. 4.2; with the discrete heater T0 = T_o (Sec. 4.4) */
+    c->T0 = p->heater_len > 0 ? p->T_cold : 0.5 * (p->T_hot + p->T_cold);
     c->Kbar = p->Da * c->L * c->L;                                                /* Eq. 9: Da = K / L^2 */
     /* Eq. 23 with the rates of Sec. 4. */
     const double s_nu = 1.0 / c->tau;
@@ -395,6 +398,16 @@ static void fluid_neighbour(const orc_params *p, int cls, int kr, int kz, int *f
 }
 
 /*
+ * Discrete heater (Sec. 4.4, Fig. 7): inner-wall node kz is heated when
+ * |kz - h H| <= l H / 2 (H = nz - 1); the rest of the inner wall is insulated.
+ */
+static int in_heater(const orc_params *p, int kz)
+{
+    const double H = p->nz - 1;
+    return fabs(kz - p->heater_center * H) <= 0.5 * p->heater_len * H;
+}
+
+/*
  * Non-equilibrium extrapolation (Sec. 4, ref. [47]) at a boundary node x_b:
  *   f(x_b) = f_eq(r_b, rho_b, u_b) + [f(x_f) - f_eq(r_f, rho_f, u_f)]
  *   g(x_b) = g_eq(T_b, u_b) + [g(x_f) - g_eq(T_f, u_f)]
@@ -435,6 +448,22 @@ static void rebuild(const orc_params *p, const orc_consts *c, const double *phi,
     orc_feq(rf, rho_f, ur_f, uz_f, phif, feq_f);
     for (int i = 0; i < 9; ++i) f[i] = feq_b[i] + (ff[i] - feq_f[i]);
     *Tb = (cls == ORC_WALL_IN || cls == ORC_INLET) ? p->T_hot : (cls == ORC_WALL_OUT) ? p->T_cold : T_f;
+    if (cls == ORC_WALL_IN && p->heater_len > 0) {
+        /* Sec. 4.4: q' = -k dT/dr on the heater (q' L / k = T_hot - T_cold), dT/dr = 0 on the
+         * insulated rest.  The wall temperature solves the one-sided second-order
+         * difference (-3 T_b + 4 T_1 - T_2) / 2 = -q'/k with T_1, T_2 the temperatures of
+         * the next two nodes inward; the corners (diagonal neighbour) take T_f. */
+        if (fz == kz) {
+            double f2[9], g2[5];
+            pull(p, fp, gp, 2, kz, f2, g2);
+            double T2 = 0;
+            for (int i = 0; i < 5; ++i) T2 += g2[i];
+            const double G = in_heater(p, kz) ? (p->T_hot - p->T_cold) / c->L : 0.0;
+            *Tb = (4 * T_f - T2 + 2 * G) / 3;
+        } else {
+            *Tb = T_f;
+        }
+    }
     geq5(*Tb, *urb, *uzb, geq_b);
     geq5(T_f, ur_f, uz_f, geq_f);
     for (int i = 0; i < 5; ++i) g[i] = geq_b[i] + (gf[i] - geq_f[i]);
@@ -566,7 +595,11 @@ int orc_init(const orc_params *p, const double *phi, const double *ur_in, const 
             const int cls = node_class(p, kr, kz);
             const double r = c.r0 + kr;
             double ur = 0, uz = 0, T = Tst[n];
-            if (cls == ORC_WALL_IN) T = p->T_hot;
+            if (cls == ORC_WALL_IN && p->heater_len > 0) {
+                int fr, fz;
+                fluid_neighbour(p, cls, kr, kz, &fr, &fz);
+                T = Tst[(size_t)fr * p->nz + fz];
+            } else if (cls == ORC_WALL_IN) T = p->T_hot;
             else if (cls == ORC_WALL_OUT) T = p->T_cold;
             else if (cls == ORC_INLET) {
                 T = p->T_hot;
@@ -676,6 +709,33 @@ int orc_pipe_nusselt(const orc_params *p, const double *uz, const double *T, dou
         const double dTdr = (3 * Tw - 4 * T[(size_t)(nr - 2) * nz + kz] + T[(size_t)(nr - 3) * nz + kz]) / 2;
         nu[kz] = 2 * ri * dTdr / (Tw - Tb);
     }
+    return 0;
+}
+
+/*
+ * Discrete heater (Sec. 4.4): local Nusselt number of Eq. 44 at the heated inner-wall
+ * nodes, Nu(z) = q' L / (k (T_h - T_o)) = (T_hot - T_cold) / (T_h(z) - T_cold), and
+ * its mean over the heater (Eq. 43; the heated nodes weigh equally).  nu_z[kz] is
+ * NaN off the heater.  T: the fields of a state (T_h = the inner wall node's T).
+ */
+int orc_heater_nusselt(const orc_params *p, const double *T, double *nu_mean, double *nu_z)
+{
+    orc_consts c;
+    if (orc_derive(p, &c) || !(p->heater_len > 0)) return 1;
+    const double dT = p->T_hot - p->T_cold;
+    double sum = 0;
+    int n = 0;
+    for (int kz = 0; kz < p->nz; ++kz) {
+        const int heated = in_heater(p, kz) && node_class(p, 0, kz) == ORC_WALL_IN &&
+                           (periodic_z(p) || (kz > 0 && kz < p->nz - 1));
+        const double nu = heated ? dT / (T[kz] - p->T_cold) : NAN;
+        if (nu_z) nu_z[kz] = nu;
+        if (heated) {
+            sum += nu;
+            ++n;
+        }
+    }
+    *nu_mean = n ? sum / n : NAN;
     return 0;
 }
 

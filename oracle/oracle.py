@@ -49,6 +49,7 @@ class Params(C.Structure):
         ("F_eps", C.c_double), ("eps_mean", C.c_double),
         ("T_hot", C.c_double), ("T_cold", C.c_double), ("body_accel_z", C.c_double),
         ("init_noise", C.c_double), ("seed", C.c_uint64), ("u_in", C.c_double),
+        ("heater_len", C.c_double), ("heater_center", C.c_double),
     ]
 
 
@@ -57,7 +58,7 @@ def params(**kw) -> Params:
     Ra = 1e3, Pr = 1, J = lambda = 1, Ma = 0.1, Ergun F_eps, T_hot = 1, T_cold = 0)."""
     d = dict(nr=48, nz=96, geometry=ANNULUS, radius_ratio=2.0, Ra=1e3, Da=1e-2, Pr=1.0, J=1.0,
              lam=1.0, Ma=0.1, tau_nu=0.0, F_eps=-1.0, eps_mean=0.6, T_hot=1.0, T_cold=0.0,
-             body_accel_z=0.0, init_noise=1e-3, seed=1, u_in=0.0)
+             body_accel_z=0.0, init_noise=1e-3, seed=1, u_in=0.0, heater_len=0.0, heater_center=0.5)
     for k in kw:
         if k not in d:
             raise KeyError(k)
@@ -86,6 +87,7 @@ def lib():
             L.orc_moments.argtypes = [pp, dp, dp, dp, dp, dp, dp, dp]
             L.orc_nusselt.argtypes = [pp, dp, dp, dp]
             L.orc_pipe_nusselt.argtypes = [pp, dp, dp, dp]
+            L.orc_heater_nusselt.argtypes = [pp, dp, dp, dp]
             L.orc_residual.argtypes = [pp] + [dp] * 9
             L.orc_node_class.argtypes = [pp, C.POINTER(C.c_uint8)]
             L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
@@ -207,11 +209,24 @@ class State:
         lib().orc_nusselt(C.byref(self.p), _d(T), C.byref(a), C.byref(b))
         return a.value, b.value
 
+    def heater_nusselt(self):
+        return heater_nusselt(self.p, self.moments()[3])
+
     def pipe_nusselt(self):
         """Local wall Nusselt number Nu(z) of Eq. 40 with the mixing-cup bulk
         temperature (pipe with inlet and outlet)."""
         m = self.moments()
         return pipe_nusselt(self.p, m[2], m[3])
+
+
+def heater_nusselt(p: Params, T):
+    """Eq. 43-44: (mean over the heater, local Nu(z) with NaN off the heater)."""
+    T = _f64(T)
+    m = C.c_double()
+    nz = np.zeros(p.nz)
+    if lib().orc_heater_nusselt(C.byref(p), _d(T), C.byref(m), _d(nz)):
+        raise ValueError("heater_nusselt needs heater_len > 0")
+    return m.value, nz
 
 
 def pipe_nusselt(p: Params, uz, T):

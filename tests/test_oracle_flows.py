@@ -247,3 +247,44 @@ def test_pipe_inflow_graetz_nusselt(oracle):
     a, b = Nu[int(0.75 * nz)], Nu[int(0.9 * nz)]
     assert abs(a - b) < 5e-3 * b                         # developed
     assert abs(b / 3.6568 - 1) < 0.035, b
+
+
+# ---- annulus with an isoflux discrete heater (Sec. 4.4, Fig. 7) ----------------------
+def test_heater_conduction_limit(oracle):
+    """Periodic annulus, no flow, the whole inner wall an isoflux heater (q' L / k = 10):
+    radial conduction T(r) = T_o + (q' r_i / k) ln(r_o / r), so Eq. 44 gives
+    Nu = (R* - 1) / ln R* = 1 / ln 2 at R* = 2; the scheme converges at second order."""
+    err = []
+    for nr in (11, 21):
+        p = oracle.params(nr=nr, nz=8, geometry=oracle.ANNULUS_PERIODIC_Z, Ra=0.0, tau_nu=0.8, Da=1e8, eps_mean=1.0,
+                          F_eps=0.0, Pr=1.0, T_hot=11.0, T_cold=1.0, heater_len=1.0, heater_center=0.5,
+                          init_noise=0.0, radius_ratio=2.0)
+        st = oracle.State(p)
+        st.run(40 * nr * nr, THREADS)
+        m, nz = st.heater_nusselt()
+        assert np.isfinite(nz).all()
+        err.append(abs(m * np.log(2.0) - 1))
+    assert err[1] < 3e-3 and err[0] / err[1] > 3.0, err
+
+
+def test_heater_heat_balance(oracle):
+    """Closed porous annulus (A = 1, R* = 2, phi = 0.9, Da = 1e-2, Ra = 1e3) heated by the
+    discrete heater of Sec. 4.4 (l / H = 0.4 centred): at steady state the heat leaving
+    through the cold outer wall equals the heat the heater puts in (the rest of the
+    boundary is insulated); the mismatch falls at second order with the grid."""
+    mis = []
+    for nr in (21, 41):
+        p = oracle.params(nr=nr, nz=nr, Ra=1e3, Da=1e-2, eps_mean=0.9, F_eps=0.0, Pr=0.7, T_hot=11.0, T_cold=1.0,
+                          heater_len=0.4, heater_center=0.5, init_noise=0.0, radius_ratio=2.0)
+        d = oracle.derive(p)
+        st = oracle.State(p)
+        st.run(40 * nr * nr, THREADS)
+        T = st.moments()[3]
+        L, ri = nr - 1, d["r0"]
+        heated = [kz for kz in range(1, nr - 1) if abs(kz - 0.5 * L) <= 0.2 * L]
+        q_in = (10.0 / L) * ri * len(heated)
+        w = np.ones(nr)
+        w[0] = w[-1] = 0.5
+        q_out = -(ri + L) * np.sum(w * (3 * T[-1] - 4 * T[-2] + T[-3]) / 2)
+        mis.append(abs(q_out / q_in - 1))
+    assert mis[1] < 0.04 and mis[0] / mis[1] > 3.0, mis
