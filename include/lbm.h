@@ -94,6 +94,11 @@ typedef struct lbm_params {
     double init_noise;       /* cold start: T = T0 + init_noise * U(-1, 1) on non-wall nodes */
     uint64_t seed;           /* SplitMix64 seed of that noise (draw number kr*nz + kz) */
     double u_in;             /* LBM_PIPE_INFLOW: inlet velocity U_in (Re = r_i U_in / nu, Sec. 4.1) */
+    double heater_len;       /* annulus geometries: > 0 puts an isoflux discrete heater of length
+                                heater_len * H on the inner wall (Sec. 4.4, Fig. 7) with
+                                q' L / k = T_hot - T_cold, insulates the rest of the inner wall
+                                and sets T0 = T_cold; 0: inner wall held at T_hot */
+    double heater_center;    /* heater centre h / H (node kz is heated when |kz - h H| <= l H / 2) */
 } lbm_params;
 
 /* Derived lattice constants (Eq. 9, 31, 39), for checks and reporting. */
@@ -115,7 +120,7 @@ typedef struct lbm_handle lbm_handle;
 
 /* Fill *p with the porous-annulus defaults (48 x 96, R* = 2, eps = 0.6, Da = 1e-2,
  * Ra = 1e3, Pr = 1, J = lambda = 1, Ma = 0.1, Ergun F_eps, T_hot = 1, T_cold = 0,
- * noise 1e-3, seed 1, FP32 storage). */
+ * noise 1e-3, seed 1, FP32 storage, no discrete heater, heater centre 0.5). */
 void lbm_params_default(lbm_params *p);
 
 /* Validate *p and derive the lattice constants without touching a GPU. */
@@ -153,8 +158,17 @@ int lbm_moments(lbm_handle *h, float *rho, float *ur, float *uz, float *T, int o
 /* Average Nusselt numbers of Eq. 42 on the inner and outer wall of the current
  * state: one-sided second-order dT/dr at the wall, trapezoid rule over the nz wall
  * nodes, H = nz - 1, dT = T_hot - T_cold.  FP64 reduction.  Synchronises.  The
- * inner value is NaN for the pipes; both are NaN for LBM_PIPE_INFLOW (lbm_pipe_nusselt). */
+ * inner value is NaN for the pipes; both are NaN for LBM_PIPE_INFLOW (lbm_pipe_nusselt)
+ * and with the discrete heater (lbm_heater_nusselt). */
 int lbm_nusselt(lbm_handle *h, double *nu_inner, double *nu_outer);
+
+/* Discrete heater (heater_len > 0) only: Eq. 44 at every heated inner-wall node,
+ * Nu(z) = q' L / (k (T_h - T_o)) = (T_hot - T_cold) / (T_h(z) - T_cold), and its mean
+ * over the heater (Eq. 43, heated nodes weighted equally) into *nu_mean.  nu_z (may be
+ * NULL) receives nz values, NaN off the heater.  The heater wall temperature solves the
+ * one-sided second-order difference of q' = -k dT/dr with the next two nodes inward.
+ * FP64.  Synchronises. */
+int lbm_heater_nusselt(lbm_handle *h, double *nu_mean, double *nu_z);
 
 /* LBM_PIPE_INFLOW only: local wall Nusselt number of Eq. 40 at every column,
  * Nu(z) = D (dT/dr)_w / (T_w - T_b), D = 2 r_i, into nu[0 .. nz-1] (host memory).

@@ -193,6 +193,21 @@ __device__ __forceinline__ void wall_state(const Consts<R>& c, const Buf<STO> A,
     dTb = (cls == WALL_IN || cls == INLET) ? (c.T_hot - c.T0) - refb
           : cls == WALL_OUT                 ? (c.T_cold - c.T0) - refb
                                             : (dTf + reff) - refb;
+    if (cls == WALL_IN && c.heater) {
+        // Sec. 4.4: q' = -k dT/dr on the heater, dT/dr = 0 on the rest of the inner wall;
+        // (-3 T_b + 4 T_1 - T_2) / 2 = -q'/k with the next two nodes inward (T_1 = T_f);
+        // corners (diagonal neighbour) take T_f
+        if (fz == kz) {
+            R f2[9], g2[5], ref2;
+            pull<STO>(c, A, plane, 2, kz, f2, g2, ref2);
+            const R T1 = (c.T0 + reff) + dTf;
+            const R T2 = (c.T0 + ref2) + (((g2[0] + g2[1]) + (g2[2] + g2[3])) + g2[4]);
+            const R G = (kz >= c.hz0 && kz <= c.hz1) ? c.hG : R(0);
+            dTb = (R(4) * T1 - T2 + R(2) * G) * R(1.0 / 3.0) - (c.T0 + refb);
+        } else {
+            dTb = (dTf + reff) - refb;
+        }
+    }
     rebuild_thermal(c.T0 + reff, dTf, c.T0 + refb, dTb, urb, uzb, urf, uzf, ghf, gh);
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
     rho = R(1) + m0 * rcp_acc(rb);
@@ -263,12 +278,13 @@ __device__ __forceinline__ void update_column(const Consts<float>& c, const Buf<
 // One thread per column segment of RPT rows: the column's index arithmetic, the
 // kernel-argument loads and the class checks are shared by RPT nodes.
 // I: index type; 32-bit when the state buffer holds fewer than 2^31 elements.
-// Resident blocks of 128 threads per SM the register allocation must allow.  16-bit flow
-// storage is issue-bound: ten blocks (48 registers) beat nine (measured 0.5306 vs
-// 0.5425 ms at 4096 x 8192); FP32 is bandwidth-bound and does best at nine (56
-// registers: 0.6083 ms, against 0.6376 at ten).
+// Resident blocks of 128 threads per SM the register allocation must allow (0: no
+// constraint).  16-bit flow storage is issue-bound: ten blocks (48 registers) beat the
+// compiler's nine (measured 0.5303 vs 0.5425 ms at 4096 x 8192); FP32 is bandwidth-bound
+// and does best with the compiler's own allocation (56 registers, 0.6079 ms; 0.6119 with
+// nine blocks required, 0.6376 with ten).
 template <int STO>
-constexpr int bulk_min_blocks() { return STO == LBM_F32 ? 9 : 10; }
+constexpr int bulk_min_blocks() { return STO == LBM_F32 ? 0 : 10; }
 
 template <int STO, typename I, int RPT>
 __global__ void __launch_bounds__(BULK_THREADS, bulk_min_blocks<STO>()) k_bulk(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
@@ -351,7 +367,11 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
     const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
     const double r = c.r0 + kr, inv_r = 1.0 / r;
     double T = start_T(c, T_in, noise, seed, n), ur = 0, uz = 0;
-    if (cls == WALL_IN) T = c.T_hot;
+    if (cls == WALL_IN && c.heater) {
+        int fr, fz;
+        fluid_neighbour(c.geometry, c.nr, c.nz, cls, kr, kz, fr, fz);
+        T = start_T(c, T_in, noise, seed, (int64_t)fr * c.nz + fz);
+    } else if (cls == WALL_IN) T = c.T_hot;
     else if (cls == WALL_OUT) T = c.T_cold;
     else if (cls == INLET) {
         T = c.T_hot;
@@ -559,6 +579,27 @@ __global__ void k_pipe_nusselt(int nr, int nz, double r0, const float* __restric
     nu[kz] = 2 * (r0 + (nr - 1)) * dTdr / (Tw - num / den);
 }
 
+// Eq. 43-44 for the discrete heater: Nu(z) = dT / (T_h(z) - T_o) at the heated inner-wall
+// columns hz0..hz1 (corners excluded unless z is periodic), NaN elsewhere, and the mean
+// over the heated columns.  Th: the inner-wall row of the T field.  One block, FP64.
+__global__ void __launch_bounds__(256) k_heater_nusselt(int nz, int hz0, int hz1, int periodic, double dT, double To,
+                                                        const float* __restrict__ Th, double* __restrict__ nu_z,
+                                                        double* __restrict__ result) {
+    double v[2] = {0, 0};
+    for (int kz = threadIdx.x; kz < nz; kz += blockDim.x) {
+        const bool heated = kz >= hz0 && kz <= hz1 && (periodic || (kz > 0 && kz < nz - 1));
+        const double nu = heated ? dT / ((double)Th[kz] - To) : NAN;
+        nu_z[kz] = nu;
+        if (heated) {
+            v[0] += nu;
+            v[1] += 1;
+        }
+    }
+    double out[2];
+    block_sum<2>(v, out);
+    if (threadIdx.x == 0) result[0] = out[1] > 0 ? out[0] / out[1] : NAN;
+}
+
 // FP64 export of rows [row0, row0 + nrows): raw post-collision populations
 // f_i = ft_i + r w_i + e_ir w_i / 2, g_i = gh_i + wT_i (T0 + R(x)).
 template <int STO>
@@ -687,7 +728,12 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         const double U = o->Ma * cs;                                                             // Ma = U / c_s
         o->gbeta = U * U / (dTw * o->L);                                                         // U^2 = g beta dT L
     }
-    o->T0 = 0.5 * (p->T_hot + p->T_cold);
+    if (p->heater_len > 0) {
+        if (p->geometry != LBM_ANNULUS && p->geometry != LBM_ANNULUS_PERIODIC_Z)
+            return fail(LBM_ERR_INVALID, "the discrete heater needs an annulus geometry");
+        if (p->nr < 4) return fail(LBM_ERR_INVALID, "the discrete heater needs nr >= 4");
+    }
+    o->T0 = p->heater_len > 0 ? p->T_cold : 0.5 * (p->T_hot + p->T_cold);   // Sec. 4.4: T0 = T_o
     o->Kbar = p->Da * o->L * o->L;
     const int64_t N = (int64_t)p->nr * p->nz;
     o->bytes_per_step = N * (int64_t)(2 * (9 * f_size(p->storage) + 5 * g_size(p->storage)) + phi_size(p->storage) +
@@ -715,6 +761,13 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         c.T0 = o->T0;
         c.az = p->body_accel_z;
         c.u_in = p->u_in;
+        if (p->heater_len > 0) {
+            const double H = p->nz - 1, h = p->heater_center * H, half = 0.5 * p->heater_len * H;
+            c.heater = 1;
+            c.hz0 = (int)std::max(0.0, std::ceil(h - half));
+            c.hz1 = (int)std::min(H, std::floor(h + half));
+            c.hG = (p->T_hot - p->T_cold) / o->L;
+        }
         // Eq. 8 coefficients (see porous()): 1/K(phi) = c_k (1 - phi)^2 / phi^3 with
         // c_k = eps_mean^3 / ((1 - eps_mean)^2 Da L^2), i.e. K(eps_mean) = Da L^2.
         const double em = p->eps_mean;
@@ -736,6 +789,7 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
 static Consts<float> to_float(const Consts<double>& d) {
     Consts<float> f;
     f.nr = d.nr; f.nz = d.nz; f.geometry = d.geometry; f.porous_mode = d.porous_mode; f.ergun = d.ergun; f.periodic = d.periodic;
+    f.heater = d.heater; f.hz0 = d.hz0; f.hz1 = d.hz1; f.hG = (float)d.hG;
     f.r0 = (float)d.r0; f.cs2tau = (float)d.cs2tau; f.two_taum = (float)d.two_taum;
     f.s_e = (float)d.s_e; f.s_eps = (float)d.s_eps; f.s_j = (float)d.s_j; f.s_q = (float)d.s_q; f.s_nu = (float)d.s_nu;
     f.tauT = (float)d.tauT; f.wg_den = (float)d.wg_den; f.gbeta = (float)d.gbeta; f.T0 = (float)d.T0;
@@ -798,6 +852,7 @@ void lbm_params_default(lbm_params* p) {
     p->body_accel_z = 0.0;
     p->init_noise = 1e-3;
     p->seed = 1;
+    p->heater_center = 0.5;
 }
 
 int lbm_derive(const lbm_params* p, lbm_info* out) {
@@ -1036,7 +1091,7 @@ int lbm_moments(lbm_handle* h, float* rho, float* ur, float* uz, float* T, int o
 
 int lbm_nusselt(lbm_handle* h, double* nu_inner, double* nu_outer) {
     if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
-    if (h->p.geometry == LBM_PIPE_INFLOW) {   // Eq. 42 has no meaning there: lbm_pipe_nusselt
+    if (h->p.geometry == LBM_PIPE_INFLOW || h->p.heater_len > 0) {   // lbm_pipe_nusselt, lbm_heater_nusselt
         if (nu_inner) *nu_inner = NAN;
         if (nu_outer) *nu_outer = NAN;
         return LBM_OK;
@@ -1142,6 +1197,28 @@ int lbm_pipe_nusselt(lbm_handle* h, double* nu, int32_t nz) {
     cudaFreeAsync(d, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "pipe Nusselt: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_heater_nusselt(lbm_handle* h, double* nu_mean, double* nu_z) {
+    if (!h || !nu_mean) return fail(LBM_ERR_INVALID, "NULL argument");
+    if (!(h->p.heater_len > 0)) return fail(LBM_ERR_INVALID, "lbm_heater_nusselt needs heater_len > 0");
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_mac(h);
+    if (rc) return rc;
+    if ((rc = snapshot(h, h->cur, h->mac))) return rc;
+    const int nz = h->p.nz;
+    double* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, (size_t)(nz + 1) * sizeof(double), h->stream));
+    k_heater_nusselt<<<1, 256, 0, h->stream>>>(nz, h->cf.hz0, h->cf.hz1, h->cf.periodic, h->p.T_hot - h->p.T_cold,
+                                               h->p.T_cold, h->mac + 3 * h->mstride, d + 1, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(nu_mean, d, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && nu_z)
+        e = cudaMemcpyAsync(nu_z, d + 1, (size_t)nz * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "heater Nusselt: %s", cudaGetErrorString(e));
     return LBM_OK;
 }
 
@@ -1886,8 +1963,9 @@ int lbm_batch_nusselt(lbm_batch* b, double* nu_inner, double* nu_outer) {
     CK(cudaMemcpyAsync(r.data(), b->result, r.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
     for (int i = 0; i < b->n; ++i) {
-        nu_inner[i] = b->p[i].geometry == LBM_PIPE_PERIODIC_Z || b->p[i].geometry == LBM_PIPE_INFLOW ? NAN : r[2 * i];
-        nu_outer[i] = b->p[i].geometry == LBM_PIPE_INFLOW ? NAN : r[2 * i + 1];
+        const bool no_eq42 = b->p[i].geometry == LBM_PIPE_INFLOW || b->p[i].heater_len > 0;
+        nu_inner[i] = b->p[i].geometry == LBM_PIPE_PERIODIC_Z || no_eq42 ? NAN : r[2 * i];
+        nu_outer[i] = no_eq42 ? NAN : r[2 * i + 1];
     }
     return LBM_OK;
 }

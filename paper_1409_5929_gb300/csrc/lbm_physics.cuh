@@ -37,6 +37,8 @@ struct Consts {
     int porous_mode;   // 0: no drag; 1: K = Da L^2 everywhere; 2: K(phi) from Eq. 8
     int ergun;         // 1: F_phi from Eq. 8 per node; 0: constant F_eps
     int periodic;      // 1: periodic in z (ANNULUS_PERIODIC_Z, PIPE_PERIODIC_Z)
+    int heater;        // 1: isoflux discrete heater on the inner wall (Sec. 4.4)
+    int hz0, hz1;      // heated inner-wall columns hz0 .. hz1
     R r0;              // r(kr = 0)
     R cs2tau;          // c_s^2 (tau - 1/2)
     R two_taum;        // 2 (tau - 1/2)
@@ -47,6 +49,7 @@ struct Consts {
     R nl_coef;         // F_phi / sqrt(K), see porous()
     R T_hot, T_cold;
     R u_in;               // inlet velocity (PIPE_INFLOW)
+    R hG;                 // heater gradient q' / k = (T_hot - T_cold) / L
     const __half* tref;   // per-node reference offset R(x) (FP16, one plane)
 };
 

@@ -38,6 +38,7 @@ class lbm_params(C.Structure):
         ("Ma", C.c_double), ("tau_nu", C.c_double), ("F_eps", C.c_double), ("eps_mean", C.c_double),
         ("T_hot", C.c_double), ("T_cold", C.c_double), ("body_accel_z", C.c_double),
         ("init_noise", C.c_double), ("seed", C.c_uint64), ("u_in", C.c_double),
+        ("heater_len", C.c_double), ("heater_center", C.c_double),
     ]
 
 
@@ -64,6 +65,7 @@ _SIGS = {
     "lbm_moments": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int]),
     "lbm_nusselt": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_pipe_nusselt": (C.c_int, [_vp, _vp, C.c_int32]),
+    "lbm_heater_nusselt": (C.c_int, [_vp, C.POINTER(C.c_double), _vp]),
     "lbm_residual": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "lbm_rebase": (C.c_int, [_vp]),
@@ -173,6 +175,14 @@ def lbm_step(h, nsteps: int):
 
 def lbm_moments(h, rho, ur, uz, T, on_device: bool):
     _check(load().lbm_moments(h, _ptr(rho), _ptr(ur), _ptr(uz), _ptr(T), int(on_device)))
+
+
+def lbm_heater_nusselt(h, nz: int):
+    """(mean over the heater, Nu(z) with NaN off the heater) of Eq. 43-44."""
+    m = C.c_double()
+    out = np.zeros(nz, np.float64)
+    _check(load().lbm_heater_nusselt(h, C.byref(m), out.ctypes.data))
+    return m.value, out
 
 
 def lbm_pipe_nusselt(h, nz: int):
@@ -292,6 +302,9 @@ class Solver:
 
     def pipe_nusselt(self):
         return lbm_pipe_nusselt(self.h, self.nz)
+
+    def heater_nusselt(self):
+        return lbm_heater_nusselt(self.h, self.nz)
 
     def residual(self):
         return lbm_residual(self.h)
