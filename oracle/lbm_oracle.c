@@ -43,7 +43,7 @@ enum { ORC_FLUID = 0, ORC_WALL_IN = 1, ORC_WALL_OUT = 2, ORC_BOTTOM = 3, ORC_TOP
 
 typedef struct orc_params {
     int32_t nr, nz, geometry;
-    int32_t pad0;
+    int32_t collision;                   /* 0: MRT (Eq. 21, rates of Sec. 4); 1: BGK, every rate 1/tau (Sec. 3.1) */
     double radius_ratio;                 /* R* = r_o / r_i (annulus) */
     double Ra, Da, Pr, J, lambda;        /* Eq. 9 */
     double Ma;                           /* Mach number of Eq. 39 */
@@ -164,10 +164,13 @@ int orc_derive(const orc_params *p, orc_consts *c)
     /* Sec. 4.2; with the discrete heater T0 = T_o (Sec. 4.4) */
     c->T0 = p->heater_len > 0 ? p->T_cold : 0.5 * (p->T_hot + p->T_cold);
     c->Kbar = p->Da * c->L * c->L;                                                /* Eq. 9: Da = K / L^2 */
-    /* Eq. 23 with the rates of Sec. 4. */
+    /* Eq. 23 with the rates of Sec. 4; the BGK limit of Sec. 3.1 relaxes every moment
+     * at 1/tau */
     const double s_nu = 1.0 / c->tau;
     const double s[9] = {1.0, 1.1, 1.1, 1.0, 1.2, 1.0, 1.2, s_nu, s_nu};
     memcpy(c->s, s, sizeof(s));
+    if (p->collision == 1)
+        for (int k = 0; k < 9; ++k) c->s[k] = s_nu;
     return 0;
 }
 

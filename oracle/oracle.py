@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
 
 class Params(C.Structure):
     _fields_ = [
-        ("nr", C.c_int32), ("nz", C.c_int32), ("geometry", C.c_int32), ("pad0", C.c_int32),
+        ("nr", C.c_int32), ("nz", C.c_int32), ("geometry", C.c_int32), ("collision", C.c_int32),
         ("radius_ratio", C.c_double),
         ("Ra", C.c_double), ("Da", C.c_double), ("Pr", C.c_double), ("J", C.c_double),
         ("lam", C.c_double), ("Ma", C.c_double), ("tau_nu", C.c_double),
@@ -56,7 +56,7 @@ class Params(C.Structure):
 def params(**kw) -> Params:
     """Parameters with the porous-annulus defaults (R* = 2, eps = 0.6, Da = 1e-2,
     Ra = 1e3, Pr = 1, J = lambda = 1, Ma = 0.1, Ergun F_eps, T_hot = 1, T_cold = 0)."""
-    d = dict(nr=48, nz=96, geometry=ANNULUS, radius_ratio=2.0, Ra=1e3, Da=1e-2, Pr=1.0, J=1.0,
+    d = dict(nr=48, nz=96, geometry=ANNULUS, collision=0, radius_ratio=2.0, Ra=1e3, Da=1e-2, Pr=1.0, J=1.0,
              lam=1.0, Ma=0.1, tau_nu=0.0, F_eps=-1.0, eps_mean=0.6, T_hot=1.0, T_cold=0.0,
              body_accel_z=0.0, init_noise=1e-3, seed=1, u_in=0.0, heater_len=0.0, heater_center=0.5)
     for k in kw:

@@ -241,3 +241,19 @@ def test_node_classes_brute_force(oracle, geom):
                 else:
                     want = oracle.FLUID
                 assert cls[kr, kz] == want, (nr, nz, kr, kz)
+
+
+def test_bgk_collision_option(oracle):
+    """collision = 1 selects the BGK limit (Sec. 3.1): a node update equals the MRT update
+    with every rate 1/tau (itself pinned against the BGK formula by test_bgk_limit) and
+    differs from the MRT rates of Sec. 4."""
+    p_mrt, p_bgk = oracle.params(), oracle.params(collision=1)
+    tau = oracle.derive(p_mrt)["tau"]
+    rng = np.random.default_rng(12)
+    r = 60.0
+    f, g = _random_node(rng, oracle, r)
+    fo_bgk, go_bgk, _ = oracle.collide_node(p_bgk, r, 0.6, f, g)
+    fo_ref, go_ref, _ = oracle.collide_node(p_mrt, r, 0.6, f, g, s=np.full(9, 1 / tau))
+    fo_mrt, _, _ = oracle.collide_node(p_mrt, r, 0.6, f, g)
+    assert np.array_equal(fo_bgk, fo_ref) and np.array_equal(go_bgk, go_ref)
+    assert np.abs(fo_bgk - fo_mrt).max() > 1e-6 * np.abs(fo_mrt).max()
