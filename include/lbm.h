@@ -62,6 +62,10 @@ extern "C" {
                                      (u = (0, u_in), T_hot), outlet row z = H (zero gradient of u
                                      and T, density held at 1); inlet and outlet own their corners */
 
+/* collision of the flow populations */
+#define LBM_MRT 0
+#define LBM_BGK 1
+
 /* storage type of the distributions between steps (arithmetic is always FP32) */
 #define LBM_F32 0
 #define LBM_F16 1
@@ -99,6 +103,9 @@ typedef struct lbm_params {
                                 q' L / k = T_hot - T_cold, insulates the rest of the inner wall
                                 and sets T0 = T_cold; 0: inner wall held at T_hot */
     double heater_center;    /* heater centre h / H (node kz is heated when |kz - h H| <= l H / 2) */
+    int32_t collision;       /* LBM_MRT (Eq. 21 with the rates of Sec. 4) or LBM_BGK (every rate
+                                1/tau_nu: the BGK limit of Sec. 3.1) */
+    int32_t reserved;        /* 0 */
 } lbm_params;
 
 /* Derived lattice constants (Eq. 9, 31, 39), for checks and reporting. */

@@ -697,6 +697,8 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
     if (p->nr > 65535) return fail(LBM_ERR_INVALID, "nr = %d exceeds 65535", p->nr);
     if (p->geometry < 0 || p->geometry > 3) return fail(LBM_ERR_INVALID, "unknown geometry %d", p->geometry);
     if (p->storage < 0 || p->storage > 2) return fail(LBM_ERR_INVALID, "unknown storage %d", p->storage);
+    if (p->collision != LBM_MRT && p->collision != LBM_BGK)
+        return fail(LBM_ERR_INVALID, "unknown collision %d", p->collision);
     if (!(p->J > 0) || !(p->lambda > 0) || !(p->Pr > 0))
         return fail(LBM_ERR_INVALID, "J, lambda and Pr must be positive");
     if (!(p->eps_mean > 0 && p->eps_mean <= 1)) return fail(LBM_ERR_INVALID, "eps_mean %g outside (0, 1]", p->eps_mean);
@@ -755,6 +757,8 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         c.s_j = 1.0;
         c.s_q = 1.2;
         c.s_nu = 1.0 / o->tau_nu;
+        if (p->collision == LBM_BGK)   // Sec. 3.1: every moment relaxes at 1/tau
+            c.s_e = c.s_eps = c.s_j = c.s_q = c.s_nu;
         c.tauT = o->tau_T;
         c.wg_den = 1.0 / (o->tau_T + 0.5);
         c.gbeta = o->gbeta;

@@ -253,8 +253,10 @@ class FNO2d:
         fno_gemm(0, 0, m2, Cc, nz, 1.0, self.Gz, nz, 0, dout, Cc, nz * Cc, 0.0, dV, Cc, m2 * Cc, B * self.nr)
 
     def _wgrad(self, X, dY, K, Min, Nout, dW):
-        """dW [Min, Nout] = X^T dY with X [K, Min], dY [K, Nout]; split over K."""
-        S = max(1, min(64, K // 4096))
+        """dW [Min, Nout] = X^T dY with X [K, Min], dY [K, Nout]; split over K into up to 512
+        slices of >= 512 rows (one CTA each: 64 slices left most of the 152 SMs idle), the
+        slices summed by fno_colsum."""
+        S = max(1, min(512, K // 512))
         while K % S:
             S -= 1
         tmp = self._b(f"wg_{Min}_{Nout}_{S}", (S, Min, Nout))

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 LBM_OK, LBM_ERR_INVALID, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT = range(6)
 LBM_ANNULUS, LBM_ANNULUS_PERIODIC_Z, LBM_PIPE_PERIODIC_Z, LBM_PIPE_INFLOW = 0, 1, 2, 3
 LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2
+LBM_MRT, LBM_BGK = 0, 1
 LBM_FLUID, LBM_WALL_IN, LBM_WALL_OUT, LBM_BOTTOM, LBM_TOP, LBM_AXIS, LBM_INLET, LBM_OUTLET = range(8)
 STORAGE = {"f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
 
@@ -39,6 +40,7 @@ class lbm_params(C.Structure):
         ("T_hot", C.c_double), ("T_cold", C.c_double), ("body_accel_z", C.c_double),
         ("init_noise", C.c_double), ("seed", C.c_uint64), ("u_in", C.c_double),
         ("heater_len", C.c_double), ("heater_center", C.c_double),
+        ("collision", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
