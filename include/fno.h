@@ -63,7 +63,8 @@ int fno_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, 
              int t, void *stream);
 
 /* Tensor-core path of fno_gemm: 0 = mma.sync m16n8k16 (default), 1 = tcgen05.mma with
- * the accumulator in tensor memory (128 x N tiles, N <= 256 per CTA).  Process-wide. */
+ * the accumulator in tensor memory (persistent CTAs, 128 x N tiles with N <= 256 chosen
+ * so that there are four tiles per SM, two stage buffers).  Process-wide. */
 int fno_set_tensor_path(int path);
 /* 1 if a tcgen05 GEMM gave up a bounded wait since the last clear (its output is then
  * invalid), 0 otherwise, -1 on a CUDA error; clear = 1 resets the flag.  Synchronous. */

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -134,15 +135,20 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, float alpha, 
 
 
 // ------------------------------------------------------- tcgen05 GEMM path --
-// One CTA (four warps) computes a 128 x ntile tile of C (ntile <= 256, a multiple of
-// 16) on the 5th-generation tensor cores: operands are staged from FP32 global memory
-// as BF16 into shared memory in the canonical K-major layout without swizzle (core
-// matrices of 8 rows x 16 bytes; LBO = 128 B between core matrices along K, SBO =
-// 1024 B between 8-row groups for a 64-wide K chunk), thread 0 issues four
-// tcgen05.mma (K = 16 each) per chunk into an FP32 accumulator in tensor memory and
-// commits them to an mbarrier, and each warp reads its 32 accumulator lanes back with
-// tcgen05.ld.  Every wait is bounded: on timeout the kernel records an error, waits
-// once more (bounded) for the tensor core, frees its tensor memory and returns.
+// Persistent CTAs (four warps) on the 5th-generation tensor cores.  Each CTA allocates
+// its tensor-memory accumulator (128 lanes x ncols FP32 columns) once and walks a
+// strided list of steps: (tile, K chunk) pairs, a tile being 128 x ntile of C (ntile <=
+// 256, a multiple of 16) of one batch entry and a chunk 64 of K.  Operands are staged
+// from FP32 global memory as BF16 into shared memory in the canonical K-major layout
+// without swizzle (core matrices of 8 rows x 16 bytes; LBO = 128 B between core
+// matrices along K, SBO = 1024 B between 8-row groups), with 16-byte loads where the
+// layout allows; two stage buffers let the next chunk be staged while thread 0's four
+// tcgen05.mma (K = 16 each) on the current one run.  Each buffer has an mbarrier that
+// tcgen05.commit arrives on.  After a tile's last chunk each warp reads its 32
+// accumulator lanes back with tcgen05.ld and writes C (16-byte stores where aligned).
+// Every wait is bounded: on timeout the kernel records an error, stops issuing work,
+// waits once more (bounded) for each committed buffer, frees its tensor memory and
+// returns.
 constexpr int TC_BM = 128, TC_BK = 64;
 __device__ int g_tc_error;
 
@@ -172,25 +178,78 @@ __device__ __forceinline__ uint32_t tc_off(int row, int k) {
     return (uint32_t)((((row >> 3) * 8 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
 }
 
+__device__ __forceinline__ void st_bf16x4(uint8_t* p, float a, float b, float c, float d) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    uint2 v;
+    v.x = *reinterpret_cast<uint32_t*>(&lo);
+    v.y = *reinterpret_cast<uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(p) = v;
+}
+
+// Stage the rows x 64 chunk starting at (r0, k0) of an operand X whose element (row, k)
+// is at X[row * ld + k] (kmajor) or X[k * ld + row] (!kmajor) into tile T, as BF16,
+// zero outside [0, R) x [0, K).  vec: ld and X allow 16-byte loads along the contiguous
+// direction.
+template <bool KMAJOR>
+__device__ __forceinline__ void tc_stage(uint8_t* T, const float* __restrict__ X, int64_t ld, int rows, int r0,
+                                         int R, int k0, int K, bool vec) {
+    const int tid = threadIdx.x;
+    if (KMAJOR) {   // 16 float4 along k per row
+        for (int f = tid; f < rows * 16; f += 128) {
+            const int r = f >> 4, kq = (f & 15) << 2;
+            const int gr = r0 + r, gk = k0 + kq;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (gr < R) {
+                const float* src = X + (int64_t)gr * ld + gk;
+                if (vec && gk + 3 < K) {
+                    const float4 q = *reinterpret_cast<const float4*>(src);
+                    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (gk + i < K) v[i] = src[i];
+                }
+            }
+            st_bf16x4(T + tc_off(r, kq), v[0], v[1], v[2], v[3]);
+        }
+    } else {        // rows / 4 float4 along the row index per k
+        const int rq = rows >> 2;
+        for (int f = tid; f < rq * 64; f += 128) {
+            const int k = f / rq, r = (f - k * rq) << 2;
+            const int gr = r0 + r, gk = k0 + k;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (gk < K) {
+                const float* src = X + (int64_t)gk * ld + gr;
+                if (vec && gr + 3 < R) {
+                    const float4 q = *reinterpret_cast<const float4*>(src);
+                    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (gr + i < R) v[i] = src[i];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<__nv_bfloat16*>(T + tc_off(r + i, k)) = __float2bfloat16_rn(v[i]);
+        }
+    }
+}
+
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile, float alpha,
-                                                 const float* __restrict__ A, int64_t lda, int64_t sA,
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile, int ntm, int ntn, int batch,
+                                                 float alpha, const float* __restrict__ A, int64_t lda, int64_t sA,
                                                  const float* __restrict__ B, int64_t ldb, int64_t sB, float beta,
                                                  float* __restrict__ C, int64_t ldc, int64_t sC,
-                                                 const float* __restrict__ bias) {
+                                                 const float* __restrict__ bias, int vecA, int vecB, int vecC) {
     extern __shared__ __align__(1024) uint8_t tc_smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_sh;
-    uint8_t* As = tc_smem;
-    uint8_t* Bs = tc_smem + TC_BM * TC_BK * 2;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * ntile;
-    A += (int64_t)blockIdx.z * sA;
-    B += (int64_t)blockIdx.z * sB;
-    C += (int64_t)blockIdx.z * sC;
+    const uint32_t abytes = TC_BM * TC_BK * 2, stage_bytes = abytes + (uint32_t)ntile * TC_BK * 2;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)ntile) ncols <<= 1;
-    const uint32_t mbar_a = smem_u32(&mbar);
+    const uint32_t mb0 = smem_u32(&mbar[0]);   // buffer b's barrier at mb0 + 8 b
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
                      "r"(ncols)
@@ -198,7 +257,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -207,75 +267,120 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
     const uint32_t tmem = tmem_sh;
     // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, N, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-    uint32_t phase = 0;
+    const int nk = (K + TC_BK - 1) / TC_BK;
+    const int64_t ntiles = (int64_t)ntm * ntn * batch;
+    // this CTA's steps: tiles t = blockIdx.x + j gridDim.x, each in nk chunks of K
+    const int64_t my_tiles = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nsteps = my_tiles * nk;
+    uint32_t phase_bits = 0, pend_bits = 0;   // per stage buffer: mbarrier phase, commit outstanding
     bool ok = true;
-    for (int k0 = 0; k0 < K && ok; k0 += TC_BK) {
-        for (int i = tid; i < TC_BM * TC_BK; i += 128) {
-            int m, k;
-            if (TA) { k = i / TC_BM; m = i % TC_BM; } else { m = i / TC_BK; k = i % TC_BK; }
-            const int gm = m0 + m, gk = k0 + k;
-            float v = 0.f;
-            if (gm < M && gk < K) v = TA ? A[(int64_t)gk * lda + gm] : A[(int64_t)gm * lda + gk];
-            *reinterpret_cast<__nv_bfloat16*>(As + tc_off(m, k)) = __float2bfloat16_rn(v);
-        }
-        for (int i = tid; i < ntile * TC_BK; i += 128) {
-            int n, k;
-            if (TB) { n = i / TC_BK; k = i % TC_BK; } else { k = i / ntile; n = i % ntile; }
-            const int gn = n0 + n, gk = k0 + k;
-            float v = 0.f;
-            if (gn < N && gk < K) v = TB ? B[(int64_t)gn * ldb + gk] : B[(int64_t)gk * ldb + gn];
-            *reinterpret_cast<__nv_bfloat16*>(Bs + tc_off(n, k)) = __float2bfloat16_rn(v);
-        }
+    auto step_tile = [&](int64_t st, int& tb, int& tm, int& tn, int& kc) {
+        const int64_t t = blockIdx.x + (st / nk) * (int64_t)gridDim.x;
+        kc = (int)(st % nk);
+        tb = (int)(t / ((int64_t)ntm * ntn));
+        const int64_t rem = t - (int64_t)tb * ntm * ntn;
+        tm = (int)(rem / ntn);
+        tn = (int)(rem - (int64_t)tm * ntn);
+    };
+    auto stage = [&](int64_t st, int buf) {
+        int tb, tm, tn, kc;
+        step_tile(st, tb, tm, tn, kc);
+        uint8_t* As = tc_smem + buf * stage_bytes;
+        tc_stage<!TA>(As, A + (int64_t)tb * sA, lda, TC_BM, tm * TC_BM, M, kc * TC_BK, K, vecA != 0);
+        tc_stage<TB>(As + abytes, B + (int64_t)tb * sB, ldb, ntile, tn * ntile, N, kc * TC_BK, K, vecB != 0);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+    };
+    auto issue = [&](int64_t st, int buf) {   // all threads call it (state stays uniform)
         if (tid == 0) {
+            const int kc = (int)(st % nk);
+            const uint32_t a0 = smem_u32(tc_smem + buf * stage_bytes);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < TC_BK / 16; ++j) {
-                const uint64_t ad = tc_desc(smem_u32(As) + j * 256), bd = tc_desc(smem_u32(Bs) + j * 256);
-                const uint32_t acc = (k0 > 0 || j > 0) ? 1u : 0u;
+                const uint64_t ad = tc_desc(a0 + j * 256), bd = tc_desc(a0 + abytes + j * 256);
+                const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                     : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             mb0 + 8 * buf)
                          : "memory");
         }
-        ok = tc_wait(mbar_a, phase);
-        phase ^= 1;
+        pend_bits |= 1u << buf;
+    };
+    // wait for the commit on buf, if one is outstanding; every thread reaches each call,
+    // and the block agrees on the outcome (a lone timeout must not split the barriers)
+    auto drain = [&](int buf) {
+        if (pend_bits & (1u << buf)) {
+            const bool got = tc_wait(mb0 + 8 * buf, (phase_bits >> buf) & 1u);
+            ok = __syncthreads_and(ok && got) != 0;
+            phase_bits ^= 1u << buf;
+            pend_bits &= ~(1u << buf);
+        }
+    };
+    if (nsteps > 0) {
+        stage(0, 0);
         __syncthreads();
+        issue(0, 0);
     }
-    if (!ok) {
-        if (tid == 0) atomicExch(&g_tc_error, 1);
-        tc_wait(mbar_a, phase ^ 1);   // one more bounded wait for the tensor core
-    } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = m0 + warp * 32 + lane;
-        for (int c = 0; c < ntile; c += 8) {
-            uint32_t r[8];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                           "=r"(r[7])
-                         : "r"(taddr)
-                         : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
+    for (int64_t st = 0; st < nsteps && ok; ++st) {
+        const int buf = (int)(st & 1), nb = buf ^ 1;
+        if (st + 1 < nsteps) {
+            drain(nb);                 // the MMA that read buffer nb (step st - 1) is done
+            if (!ok) break;
+            stage(st + 1, nb);         // overlaps the MMA of step st
+        }
+        int tb, tm, tn, kc;
+        step_tile(st, tb, tm, tn, kc);
+        if (kc == nk - 1) {            // last chunk of the tile: epilogue
+            drain(buf);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = tm * TC_BM + warp * 32 + lane;
+            float* Cb = C + (int64_t)tb * sC;
+            for (int c = 0; c < ntile; c += 8) {
+                uint32_t r[8];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                               "=r"(r[7])
+                             : "r"(taddr)
+                             : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int col0 = tn * ntile + c;
+                if (row < M) {
+                    float* cp = Cb + (int64_t)row * ldc + col0;
+                    float v[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int col = n0 + c + q;
-                    if (col < N && c + q < ntile) {
-                        float* cp = C + (int64_t)row * ldc + col;
-                        float v = alpha * __uint_as_float(r[q]);
-                        if (beta != 0.f) v += beta * *cp;
-                        if (bias) v += bias[col];
-                        *cp = v;
+                    for (int q = 0; q < 8; ++q) {
+                        v[q] = alpha * __uint_as_float(r[q]);
+                        if (bias && col0 + q < N) v[q] += bias[col0 + q];
+                    }
+                    if (vecC && beta == 0.f && col0 + 7 < N && c + 7 < ntile) {
+                        *reinterpret_cast<float4*>(cp) = make_float4(v[0], v[1], v[2], v[3]);
+                        *reinterpret_cast<float4*>(cp + 4) = make_float4(v[4], v[5], v[6], v[7]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            if (col0 + q < N && c + q < ntile) cp[q] = beta != 0.f ? v[q] + beta * cp[q] : v[q];
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         }
+        __syncthreads();               // staging of st + 1 complete; accumulator free after an epilogue
+        if (st + 1 < nsteps) issue(st + 1, nb);
+    }
+    if (ok) {                          // consume any commit left (complete: they finish in order)
+        drain(0);
+        drain(1);
+    } else {
+        if (tid == 0) atomicExch(&g_tc_error, 1);
+        for (int b = 0; b < 2; ++b)    // one more bounded wait for work already committed
+            if (pend_bits & (1u << b)) tc_wait(mb0 + 8 * b, (phase_bits >> b) & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -284,32 +389,54 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
 }
 
 static int g_tc_path = 0;   // 1: route fno_gemm through the tcgen05 kernel
+static int g_num_sms = 0;
+
+static bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 static int gemm_tc(int transA, int transB, int M, int N, int K, float alpha, const float* A, int64_t lda,
                    int64_t strideA, const float* B, int64_t ldb, int64_t strideB, float beta, float* C, int64_t ldc,
                    int64_t strideC, int batch, const float* bias, cudaStream_t s) {
-    int ntile = ((N + 15) / 16) * 16;
-    if (ntile > 256) ntile = 256;
-    const dim3 grid((unsigned)((N + ntile - 1) / ntile), (unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)batch);
-    if (grid.y > 65535) return fno_fail(FNO_ERR_INVALID, "GEMM grid too large");
-    const size_t smem = (size_t)(TC_BM + ntile) * TC_BK * 2;
+    if (!g_num_sms) {
+        int dev = 0;
+        FCK(cudaGetDevice(&dev));
+        FCK(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    // tile width: the widest (<= 256, a multiple of 16, not wider than N needs) that still
+    // gives four tiles per SM; small GEMMs take narrower tiles to fill the machine
+    const int ntm = (M + TC_BM - 1) / TC_BM;
+    int ntile = std::min(256, ((N + 15) / 16) * 16);
+    while (ntile > 16 && (int64_t)ntm * ((N + ntile - 1) / ntile) * batch < 4LL * g_num_sms)
+        ntile = std::max(16, ((ntile / 2 + 15) / 16) * 16);
+    const int ntn = (N + ntile - 1) / ntile;
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)ntile) ncols <<= 1;
+    // resident CTAs per SM whose accumulators fit the 512 tensor-memory columns
+    const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, 512 / ncols));
+    const int64_t ntiles = (int64_t)ntm * ntn * batch;
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, per_sm * g_num_sms);
+    const size_t smem = 2 * (size_t)(TC_BM + ntile) * TC_BK * 2;
     static bool attr_done = false;
     if (!attr_done) {
-        const int lim = (TC_BM + 256) * TC_BK * 2;
+        const int lim = 2 * (TC_BM + 256) * TC_BK * 2;
         FCK(cudaFuncSetAttribute(k_gemm_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         FCK(cudaFuncSetAttribute(k_gemm_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         FCK(cudaFuncSetAttribute(k_gemm_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         FCK(cudaFuncSetAttribute(k_gemm_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         attr_done = true;
     }
-    if (!transA && !transB)
-        k_gemm_tc<false, false><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
-    else if (!transA && transB)
-        k_gemm_tc<false, true><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
-    else if (transA && !transB)
-        k_gemm_tc<true, false><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
-    else
-        k_gemm_tc<true, true><<<grid, 128, smem, s>>>(M, N, K, ntile, alpha, A, lda, strideA, B, ldb, strideB, beta, C, ldc, strideC, bias);
+    // 16-byte loads along the contiguous direction: base, leading dimension and batch stride
+    // aligned, the row length in that direction a multiple of 4
+    const int vecA = al16(A) && lda % 4 == 0 && strideA % 4 == 0;
+    const int vecB = al16(B) && ldb % 4 == 0 && strideB % 4 == 0;
+    const int vecC = al16(C) && ldc % 4 == 0 && strideC % 4 == 0 && ntile % 8 == 0;
+#define TC_LAUNCH(TA_, TB_)                                                                                      \
+    k_gemm_tc<TA_, TB_><<<grid, 128, smem, s>>>(M, N, K, ntile, ntm, ntn, batch, alpha, A, lda, strideA, B, ldb,  \
+                                                  strideB, beta, C, ldc, strideC, bias, vecA, vecB, vecC)
+    if (!transA && !transB) TC_LAUNCH(false, false);
+    else if (!transA && transB) TC_LAUNCH(false, true);
+    else if (transA && !transB) TC_LAUNCH(true, false);
+    else TC_LAUNCH(true, true);
+#undef TC_LAUNCH
     FCK(cudaGetLastError());
     return FNO_OK;
 }

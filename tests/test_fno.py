@@ -29,9 +29,11 @@ def _bf16_tol(a, b):
 @pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("shape", [(1, 64, 64, 32), (3, 77, 45, 130), (2, 300, 3, 8), (1, 5, 200, 513),
-                                   (1, 1000, 300, 96)])
-def test_gemm_against_fp64(fno, path, ta, tb, shape):
-    """Both tensor-core paths: mma.sync (0) and tcgen05 with a tensor-memory accumulator (1)."""
+                                   (1, 1000, 300, 96), (4, 640, 32, 256), (2, 260, 48, 20)])
+@pytest.mark.parametrize("beta", [2.0, 0.0])
+def test_gemm_against_fp64(fno, path, ta, tb, shape, beta):
+    """Both tensor-core paths: mma.sync (0) and tcgen05 with a tensor-memory accumulator (1);
+    aligned and ragged shapes, several K chunks, beta = 0 (vector stores) and beta != 0."""
     import torch
 
     fno.fno_set_tensor_path(path)
@@ -44,11 +46,11 @@ def test_gemm_against_fp64(fno, path, ta, tb, shape):
     Ad, Bd, Cd, bd = (torch.tensor(v, device="cuda") for v in (A, B, C0, bias))
     lda = M if ta else K
     ldb = K if tb else N
-    fno.fno_gemm(ta, tb, M, N, K, 0.5, Ad, lda, A[0].size, Bd, ldb, B[0].size, 2.0, Cd, N, M * N, batch, bias=bd)
+    fno.fno_gemm(ta, tb, M, N, K, 0.5, Ad, lda, A[0].size, Bd, ldb, B[0].size, beta, Cd, N, M * N, batch, bias=bd)
     torch.cuda.synchronize()
     opA = np.swapaxes(A, 1, 2) if ta else A
     opB = np.swapaxes(B, 1, 2) if tb else B
-    ref = 0.5 * np.einsum("bmk,bkn->bmn", opA.astype(np.float64), opB.astype(np.float64)) + 2.0 * C0 + bias
+    ref = 0.5 * np.einsum("bmk,bkn->bmn", opA.astype(np.float64), opB.astype(np.float64)) + beta * C0 + bias
     # bound: |sum a b| error <= K * 2 * 2^-9 * max|a b| per element; L2-relative check
     got = Cd.cpu().numpy()
     fno.fno_set_tensor_path(0)
