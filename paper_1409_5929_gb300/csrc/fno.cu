@@ -154,8 +154,11 @@ __device__ int g_tc_error;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Shared-memory matrix descriptor of a K-major tile whose rows hold BK elements: LBO =
+// 128 B between the core matrices along K, SBO = BK / 8 x 128 B between 8-row groups.
+template <int BK>
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    const uint64_t lbo = 128, sbo = 1024;
+    const uint64_t lbo = 128, sbo = (uint64_t)(BK / 8) * 128;
     return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
            ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
 }
@@ -173,9 +176,10 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
     return false;
 }
 
-// byte offset of element (row, k) of a [rows x 64] K-major tile in the canonical layout
+// byte offset of element (row, k) of a [rows x BK] K-major tile in the canonical layout
+template <int BK>
 __device__ __forceinline__ uint32_t tc_off(int row, int k) {
-    return (uint32_t)((((row >> 3) * 8 + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+    return (uint32_t)((((row >> 3) * (BK / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
 }
 
 __device__ __forceinline__ void st_bf16x4(uint8_t* p, float a, float b, float c, float d) {
@@ -190,13 +194,14 @@ __device__ __forceinline__ void st_bf16x4(uint8_t* p, float a, float b, float c,
 // is at X[row * ld + k] (kmajor) or X[k * ld + row] (!kmajor) into tile T, as BF16,
 // zero outside [0, R) x [0, K).  vec: ld and X allow 16-byte loads along the contiguous
 // direction.
-template <bool KMAJOR>
+template <bool KMAJOR, int BK>
 __device__ __forceinline__ void tc_stage(uint8_t* T, const float* __restrict__ X, int64_t ld, int rows, int r0,
                                          int R, int k0, int K, bool vec) {
     const int tid = threadIdx.x;
-    if (KMAJOR) {   // 16 float4 along k per row
-        for (int f = tid; f < rows * 16; f += 128) {
-            const int r = f >> 4, kq = (f & 15) << 2;
+    constexpr int KQ = BK / 4;   // float4 per row along k
+    if (KMAJOR) {
+        for (int f = tid; f < rows * KQ; f += 128) {
+            const int r = f / KQ, kq = (f % KQ) << 2;
             const int gr = r0 + r, gk = k0 + kq;
             float v[4] = {0.f, 0.f, 0.f, 0.f};
             if (gr < R) {
@@ -210,11 +215,11 @@ __device__ __forceinline__ void tc_stage(uint8_t* T, const float* __restrict__ X
                         if (gk + i < K) v[i] = src[i];
                 }
             }
-            st_bf16x4(T + tc_off(r, kq), v[0], v[1], v[2], v[3]);
+            st_bf16x4(T + tc_off<BK>(r, kq), v[0], v[1], v[2], v[3]);
         }
     } else {        // rows / 4 float4 along the row index per k
         const int rq = rows >> 2;
-        for (int f = tid; f < rq * 64; f += 128) {
+        for (int f = tid; f < rq * BK; f += 128) {
             const int k = f / rq, r = (f - k * rq) << 2;
             const int gr = r0 + r, gk = k0 + k;
             float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -231,12 +236,12 @@ __device__ __forceinline__ void tc_stage(uint8_t* T, const float* __restrict__ X
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                *reinterpret_cast<__nv_bfloat16*>(T + tc_off(r + i, k)) = __float2bfloat16_rn(v[i]);
+                *reinterpret_cast<__nv_bfloat16*>(T + tc_off<BK>(r + i, k)) = __float2bfloat16_rn(v[i]);
         }
     }
 }
 
-template <bool TA, bool TB>
+template <bool TA, bool TB, int BK>
 __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile, int ntm, int ntn, int batch,
                                                  float alpha, const float* __restrict__ A, int64_t lda, int64_t sA,
                                                  const float* __restrict__ B, int64_t ldb, int64_t sB, float beta,
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t abytes = TC_BM * TC_BK * 2, stage_bytes = abytes + (uint32_t)ntile * TC_BK * 2;
+    const uint32_t abytes = TC_BM * BK * 2, stage_bytes = abytes + (uint32_t)ntile * BK * 2;
     uint32_t ncols = 32;
     while (ncols < (uint32_t)ntile) ncols <<= 1;
     const uint32_t mb0 = smem_u32(&mbar[0]);   // buffer b's barrier at mb0 + 8 b
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
     const uint32_t tmem = tmem_sh;
     // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, N, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
-    const int nk = (K + TC_BK - 1) / TC_BK;
+    const int nk = (K + BK - 1) / BK;
     const int64_t ntiles = (int64_t)ntm * ntn * batch;
     // this CTA's steps: tiles t = blockIdx.x + j gridDim.x, each in nk chunks of K
     const int64_t my_tiles = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -286,8 +291,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
         int tb, tm, tn, kc;
         step_tile(st, tb, tm, tn, kc);
         uint8_t* As = tc_smem + buf * stage_bytes;
-        tc_stage<!TA>(As, A + (int64_t)tb * sA, lda, TC_BM, tm * TC_BM, M, kc * TC_BK, K, vecA != 0);
-        tc_stage<TB>(As + abytes, B + (int64_t)tb * sB, ldb, ntile, tn * ntile, N, kc * TC_BK, K, vecB != 0);
+        tc_stage<!TA, BK>(As, A + (int64_t)tb * sA, lda, TC_BM, tm * TC_BM, M, kc * BK, K, vecA != 0);
+        tc_stage<TB, BK>(As + abytes, B + (int64_t)tb * sB, ldb, ntile, tn * ntile, N, kc * BK, K, vecB != 0);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     };
     auto issue = [&](int64_t st, int buf) {   // all threads call it (state stays uniform)
@@ -296,8 +301,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
             const uint32_t a0 = smem_u32(tc_smem + buf * stage_bytes);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < TC_BK / 16; ++j) {
-                const uint64_t ad = tc_desc(a0 + j * 256), bd = tc_desc(a0 + abytes + j * 256);
+            for (int j = 0; j < BK / 16; ++j) {
+                const uint64_t ad = tc_desc<BK>(a0 + j * 256), bd = tc_desc<BK>(a0 + abytes + j * 256);
                 const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -414,14 +419,20 @@ static int gemm_tc(int transA, int transB, int M, int N, int K, float alpha, con
     const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, 512 / ncols));
     const int64_t ntiles = (int64_t)ntm * ntn * batch;
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, per_sm * g_num_sms);
-    const size_t smem = 2 * (size_t)(TC_BM + ntile) * TC_BK * 2;
+    // K chunk: 32 when K fits in it (half the staging of a padded 64-wide chunk), else 64
+    const int bk = K <= 32 ? 32 : TC_BK;
+    const size_t smem = 2 * (size_t)(TC_BM + ntile) * bk * 2;
     static bool attr_done = false;
     if (!attr_done) {
         const int lim = 2 * (TC_BM + 256) * TC_BK * 2;
-        FCK(cudaFuncSetAttribute(k_gemm_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        FCK(cudaFuncSetAttribute(k_gemm_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        FCK(cudaFuncSetAttribute(k_gemm_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        FCK(cudaFuncSetAttribute(k_gemm_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<false, false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<false, true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<true, false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<true, true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<false, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<false, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<true, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        FCK(cudaFuncSetAttribute(k_gemm_tc<true, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
         attr_done = true;
     }
     // 16-byte loads along the contiguous direction: base, leading dimension and batch stride
@@ -430,8 +441,16 @@ static int gemm_tc(int transA, int transB, int M, int N, int K, float alpha, con
     const int vecB = al16(B) && ldb % 4 == 0 && strideB % 4 == 0;
     const int vecC = al16(C) && ldc % 4 == 0 && strideC % 4 == 0 && ntile % 8 == 0;
 #define TC_LAUNCH(TA_, TB_)                                                                                      \
-    k_gemm_tc<TA_, TB_><<<grid, 128, smem, s>>>(M, N, K, ntile, ntm, ntn, batch, alpha, A, lda, strideA, B, ldb,  \
-                                                  strideB, beta, C, ldc, strideC, bias, vecA, vecB, vecC)
+    do {                                                                                                         \
+        if (bk == 32)                                                                                            \
+            k_gemm_tc<TA_, TB_, 32><<<grid, 128, smem, s>>>(M, N, K, ntile, ntm, ntn, batch, alpha, A, lda,     \
+                                                            strideA, B, ldb, strideB, beta, C, ldc, strideC,    \
+                                                            bias, vecA, vecB, vecC);                            \
+        else                                                                                                     \
+            k_gemm_tc<TA_, TB_, 64><<<grid, 128, smem, s>>>(M, N, K, ntile, ntm, ntn, batch, alpha, A, lda,     \
+                                                            strideA, B, ldb, strideB, beta, C, ldc, strideC,    \
+                                                            bias, vecA, vecB, vecC);                            \
+    } while (0)
     if (!transA && !transB) TC_LAUNCH(false, false);
     else if (!transA && transB) TC_LAUNCH(false, true);
     else if (transA && !transB) TC_LAUNCH(true, false);
