@@ -759,6 +759,12 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         c.s_nu = 1.0 / o->tau_nu;
         if (p->collision == LBM_BGK)   // Sec. 3.1: every moment relaxes at 1/tau
             c.s_e = c.s_eps = c.s_j = c.s_q = c.s_nu;
+        c.h_e = 1 - 0.5 * c.s_e;
+        c.h_eps = 1 - 0.5 * c.s_eps;
+        c.h_j = 1 - 0.5 * c.s_j;
+        c.h_q = 1 - 0.5 * c.s_q;
+        c.h_nu = 1 - 0.5 * c.s_nu;
+        c.cs2_2tm = c.two_taum / 3.0;
         c.tauT = o->tau_T;
         c.wg_den = 1.0 / (o->tau_T + 0.5);
         c.gbeta = o->gbeta;
@@ -796,6 +802,8 @@ static Consts<float> to_float(const Consts<double>& d) {
     f.heater = d.heater; f.hz0 = d.hz0; f.hz1 = d.hz1; f.hG = (float)d.hG;
     f.r0 = (float)d.r0; f.cs2tau = (float)d.cs2tau; f.two_taum = (float)d.two_taum;
     f.s_e = (float)d.s_e; f.s_eps = (float)d.s_eps; f.s_j = (float)d.s_j; f.s_q = (float)d.s_q; f.s_nu = (float)d.s_nu;
+    f.h_e = (float)d.h_e; f.h_eps = (float)d.h_eps; f.h_j = (float)d.h_j; f.h_q = (float)d.h_q; f.h_nu = (float)d.h_nu;
+    f.cs2_2tm = (float)d.cs2_2tm;
     f.tauT = (float)d.tauT; f.wg_den = (float)d.wg_den; f.gbeta = (float)d.gbeta; f.T0 = (float)d.T0;
     f.az = (float)d.az; f.lin_coef = (float)d.lin_coef; f.nl_coef = (float)d.nl_coef;
     f.T_hot = (float)d.T_hot; f.T_cold = (float)d.T_cold;

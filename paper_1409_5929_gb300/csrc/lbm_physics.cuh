@@ -43,6 +43,8 @@ struct Consts {
     R cs2tau;          // c_s^2 (tau - 1/2)
     R two_taum;        // 2 (tau - 1/2)
     R s_e, s_eps, s_j, s_q, s_nu;   // Eq. 23 with the rates of Sec. 4
+    R h_e, h_eps, h_j, h_q, h_nu;   // 1 - s / 2 of each (the source weights of Eq. 21)
+    R cs2_2tm;                      // c_s^2 2 (tau - 1/2)
     R tauT, wg_den;    // tau_T and 1 / (tau_T + 1/2)
     R gbeta, T0, az;   // buoyancy, reference temperature, external acceleration (z)
     R lin_coef;        // nu / K = lin_coef (mode 1) or lin_coef (1 - phi)^2 / phi^3 (mode 2)
@@ -199,13 +201,13 @@ __device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi,
     const R Gz = c.gbeta * (dT + rref) + c.az;
     const R drag = lin + nl * um;
     const R Fr = -phi * drag * ur;
-    const R Ftr = Fr + cs2<R>() * (R(1) - c.two_taum * ur * inv_r) * inv_r;   // Eq. 25
+    const R Ftr = Fr + (cs2<R>() - c.cs2_2tm * ur * inv_r) * inv_r;   // Eq. 25
     const R Ftz = -phi * drag * uz + phi * Gz;
     const R rr = r * rho;
     // Eq. 24; S_3 = r rho F~_r = c_s^2 + S3, the constant c_s^2 cancelling against
     // the rest offsets of the stored deviations
     const R S1 = R(6) * rr * (ur * Ftr + uz * Ftz) * inv_phi;
-    const R S3 = cs2<R>() * m0 * inv_r + rr * Fr - rho * cs2<R>() * c.two_taum * ur * inv_r;
+    const R S3 = cs2<R>() * m0 * inv_r + rr * Fr - rho * c.cs2_2tm * ur * inv_r;
     const R S5 = rr * Ftz;
     const R S7 = R(2) * rr * (ur * Ftr - uz * Ftz) * inv_phi;
     const R S8 = rr * (ur * Ftz + uz * Ftr) * inv_phi;
@@ -233,14 +235,14 @@ __device__ __forceinline__ void collide(const Consts<R>& c, R r, R inv_r, R phi,
     // collision increment and not the conserved moments themselves (a factor like
     // 6 fl(1/6) = 1 + 3e-8 on the momentum every step would act as a spurious force).
     const R dm[9] = {R(0),
-                     -c.s_e * (m1 - e1) + (R(1) - R(0.5) * c.s_e) * S1,
-                     -c.s_eps * (m2 - e2) - (R(1) - R(0.5) * c.s_eps) * S1,
-                     -c.s_j * (m3 - e3) + (R(1) - R(0.5) * c.s_j) * S3,
-                     -c.s_q * (m4 + e3) - (R(1) - R(0.5) * c.s_q) * S3,
-                     -c.s_j * (m5 - e5) + (R(1) - R(0.5) * c.s_j) * S5,
-                     -c.s_q * (m6 + e5) - (R(1) - R(0.5) * c.s_q) * S5,
-                     -c.s_nu * (m7 - e7) + (R(1) - R(0.5) * c.s_nu) * S7,
-                     -c.s_nu * (m8 - e8) + (R(1) - R(0.5) * c.s_nu) * S8};
+                     -c.s_e * (m1 - e1) + c.h_e * S1,
+                     -c.s_eps * (m2 - e2) - c.h_eps * S1,
+                     -c.s_j * (m3 - e3) + c.h_j * S3,
+                     -c.s_q * (m4 + e3) - c.h_q * S3,
+                     -c.s_j * (m5 - e5) + c.h_j * S5,
+                     -c.s_q * (m6 + e5) - c.h_q * S5,
+                     -c.s_nu * (m7 - e7) + c.h_nu * S7,
+                     -c.s_nu * (m8 - e8) + c.h_nu * S8};
     R df[9];
     minv(dm, df);
 #pragma unroll
