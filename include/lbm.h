@@ -146,6 +146,20 @@ int lbm_set_stream(lbm_handle *h, void *stream);
  * from the next step; the state is not re-initialised (call lbm_init_fields). */
 int lbm_set_porosity(lbm_handle *h, const float *phi, int on_device);
 
+/* Storage detail with no counterpart in the paper: the porosity upload of lbm_set_porosity
+ * without its synchronisation.  phi (nr*nz floats, host memory; pinned memory lets the
+ * copy run asynchronously) is copied on a copy stream of the handle while earlier work runs,
+ * then converted on the handle's stream in order: the steps queued before this call see the
+ * old field, the steps queued after it the new one.  Two staging buffers alternate, so one
+ * upload can be in flight while the previous one is converted.  phi must stay valid until
+ * the next synchronising call on the handle.  Values outside (0, 1] are counted, not
+ * rejected: lbm_porosity_errors reports them.  Returns at once. */
+int lbm_set_porosity_async(lbm_handle *h, const float *phi);
+
+/* Number of porosity values outside (0, 1] seen by lbm_set_porosity_async since the last
+ * clear (clear = 1 resets the count).  Synchronises. */
+int lbm_porosity_errors(lbm_handle *h, uint32_t *count, int clear);
+
 /* (Re)initialise the state from the fields (u_r, u_z, T), each nr*nz, or pass three
  * NULLs for the cold start.  The populations are f = M^-1(m_eq - S/2) (Eq. 19-20,
  * 24, so that Eq. 29 returns the given u at rest), g = g_eq(T, u) (Eq. 35), after

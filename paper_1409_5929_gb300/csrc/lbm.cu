@@ -679,6 +679,13 @@ struct lbm_handle {
     void* phi = nullptr;
     __half* tref = nullptr;  // per-node reference offset R(x) of the thermal deviations
     float* fstage = nullptr; // N floats: porosity / init field upload
+    // lbm_set_porosity_async: its own copy stream, two staging buffers (the upload into one
+    // overlaps the step that follows the conversion of the other), events and an error count
+    cudaStream_t copy_stream = nullptr;
+    float* astage[2] = {nullptr, nullptr};
+    cudaEvent_t staged[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    int astage_i = 0;
+    unsigned int* bad_async = nullptr;
     float* mac = nullptr;    // two snapshots of 4 planes: rho, ur, uz, T
     int64_t mstride = 0;
     double* partials = nullptr;
@@ -880,6 +887,16 @@ int lbm_destroy(lbm_handle* h) {
     cudaFree(h->tref);
     cudaFree(h->phi);
     cudaFree(h->fstage);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamDestroy(h->copy_stream);
+    }
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h->astage[i]);
+        if (h->staged[i]) cudaEventDestroy(h->staged[i]);
+        if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
+    }
+    cudaFree(h->bad_async);
     cudaFree(h->mac);
     cudaFree(h->partials);
     cudaFree(h->result);
@@ -985,6 +1002,49 @@ int lbm_set_porosity(lbm_handle* h, const float* phi, int on_device) {
     CK(cudaMemcpyAsync(&bad, h->bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (bad) return fail(LBM_ERR_INVALID, "%u porosity values outside (0, 1]", bad);
+    return LBM_OK;
+}
+
+int lbm_set_porosity_async(lbm_handle* h, const float* phi) {
+    if (!h || !phi) return fail(LBM_ERR_INVALID, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    if (!h->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaMalloc((void**)&h->astage[i], h->N * sizeof(float)));
+            CK(cudaEventCreateWithFlags(&h->staged[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->consumed[i], cudaEventDisableTiming));
+        }
+        CK(cudaMalloc((void**)&h->bad_async, sizeof(unsigned int)));
+        CK(cudaMemsetAsync(h->bad_async, 0, sizeof(unsigned int), h->stream));
+    }
+    const int i = h->astage_i;
+    h->astage_i ^= 1;
+    // the conversion that last read staging buffer i has finished before it is refilled
+    CK(cudaStreamWaitEvent(h->copy_stream, h->consumed[i], 0));
+    CK(cudaMemcpyAsync(h->astage[i], phi, h->N * sizeof(float), cudaMemcpyHostToDevice, h->copy_stream));
+    CK(cudaEventRecord(h->staged[i], h->copy_stream));
+    // conversion in stream order on the handle's stream: after the steps queued so far
+    CK(cudaStreamWaitEvent(h->stream, h->staged[i], 0));
+    const int thr = 256;
+    const unsigned blocks = (unsigned)((h->N + thr - 1) / thr);
+    DISPATCH_STO(h->p.storage,
+                 k_phi<S_><<<blocks, thr, 0, h->stream>>>(h->astage[i], (PP<S_>*)h->phi, h->N, h->bad_async));
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->consumed[i], h->stream));
+    return LBM_OK;
+}
+
+int lbm_porosity_errors(lbm_handle* h, uint32_t* count, int clear) {
+    if (!h || !count) return fail(LBM_ERR_INVALID, "NULL argument");
+    *count = 0;
+    if (!h->bad_async) return LBM_OK;
+    CK(cudaSetDevice(h->device));
+    unsigned int v = 0;
+    CK(cudaMemcpyAsync(&v, h->bad_async, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    if (clear) CK(cudaMemsetAsync(h->bad_async, 0, sizeof(unsigned int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *count = v;
     return LBM_OK;
 }
 

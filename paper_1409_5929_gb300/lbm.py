@@ -71,6 +71,8 @@ _SIGS = {
     "lbm_residual": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "lbm_rebase": (C.c_int, [_vp]),
+    "lbm_set_porosity_async": (C.c_int, [_vp, _vp]),
+    "lbm_porosity_errors": (C.c_int, [_vp, C.POINTER(C.c_uint32), C.c_int]),
     "lbm_node_class": (C.c_int, [_vp, _vp]),
     "lbm_export_populations": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp]),
     "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
@@ -209,6 +211,17 @@ def lbm_run(h, max_steps: int, check_every: int, tol: float):
     n, r = C.c_int64(), C.c_double()
     _check(load().lbm_run(h, int(max_steps), int(check_every), float(tol), C.byref(n), C.byref(r)))
     return n.value, r.value
+
+
+def lbm_set_porosity_async(h, phi_ptr: int):
+    """phi_ptr: address of nr*nz float32 in host memory (pinned for an asynchronous copy)."""
+    _check(load().lbm_set_porosity_async(h, phi_ptr))
+
+
+def lbm_porosity_errors(h, clear: bool = True) -> int:
+    n = C.c_uint32()
+    _check(load().lbm_porosity_errors(h, C.byref(n), int(clear)))
+    return n.value
 
 
 def lbm_rebase(h):

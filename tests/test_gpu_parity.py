@@ -360,3 +360,34 @@ def test_config5_nusselt_drift_fp16_vs_fp32(lbm):
     print("config5 Nu f32", nus["f32"].tolist(), "f16", nus["f16"].tolist(), "max |dNu|", d.max(axis=0).tolist())
     assert np.isfinite(nus["f16"]).all() and np.isfinite(nus["f32"]).all()
     assert (d <= 1e-3 * np.abs(nus["f32"]) + 1e-3).all()
+
+
+def test_async_porosity_upload(lbm):
+    """lbm_set_porosity_async: the same fields as lbm_set_porosity when the uploads are
+    pipelined behind queued steps (each step sees the field set before it), and invalid
+    values counted by lbm_porosity_errors."""
+    import torch
+
+    p = lbm.lbm_params_default(nr=64, nz=200, Ra=1e5, Da=1e-3)
+    phis = [inputs.porosity_field(64, 200, 0.3, 0.9, 2.0, seed=k) for k in (1, 2, 3)]
+    pins = [torch.from_numpy(f).pin_memory() for f in phis]
+    a, b = lbm.Solver(p), lbm.Solver(p)
+    for f in phis:
+        a.set_porosity(f)
+        a.step(7)
+    lbm.lbm_set_porosity_async(b.h, pins[0].data_ptr())
+    b.step(7)
+    lbm.lbm_set_porosity_async(b.h, pins[1].data_ptr())   # queued behind the first 7 steps
+    b.step(7)
+    lbm.lbm_set_porosity_async(b.h, pins[2].data_ptr())
+    b.step(7)
+    for x, y in zip(a.moments(), b.moments()):
+        assert np.array_equal(x, y)
+    assert lbm.lbm_porosity_errors(b.h) == 0
+    bad = phis[0].copy()
+    bad[3, 3] = 0.0
+    bad[5, 7] = 1.5
+    pin_bad = torch.from_numpy(bad).pin_memory()
+    lbm.lbm_set_porosity_async(b.h, pin_bad.data_ptr())
+    assert lbm.lbm_porosity_errors(b.h) == 2
+    assert lbm.lbm_porosity_errors(b.h) == 0
