@@ -148,12 +148,13 @@ int lbm_set_porosity(lbm_handle *h, const float *phi, int on_device);
 
 /* Storage detail with no counterpart in the paper: the porosity upload of lbm_set_porosity
  * without its synchronisation.  phi (nr*nz floats, host memory; pinned memory lets the
- * copy run asynchronously) is copied on a copy stream of the handle while earlier work runs,
- * then converted on the handle's stream in order: the steps queued before this call see the
- * old field, the steps queued after it the new one.  Two staging buffers alternate, so one
- * upload can be in flight while the previous one is converted.  phi must stay valid until
- * the next synchronising call on the handle.  Values outside (0, 1] are counted, not
- * rejected: lbm_porosity_errors reports them.  Returns at once. */
+ * copy run asynchronously) is copied on a copy stream of the handle and converted there once
+ * the work already queued on the handle's stream has finished: steps queued before this call
+ * see the old field, and the next call that reads the field (a step, the fields, the
+ * residual, a re-initialisation) waits for the new one, while calls that do not read it (the
+ * Nusselt numbers of Eq. 42) overlap the copy.  Two staging buffers alternate.  phi must stay
+ * valid until the next synchronising call on the handle.  Values outside (0, 1] are
+ * counted, not rejected: lbm_porosity_errors reports them.  Returns at once. */
 int lbm_set_porosity_async(lbm_handle *h, const float *phi);
 
 /* Number of porosity values outside (0, 1] seen by lbm_set_porosity_async since the last

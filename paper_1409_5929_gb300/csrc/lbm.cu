@@ -683,8 +683,9 @@ struct lbm_handle {
     // overlaps the step that follows the conversion of the other), events and an error count
     cudaStream_t copy_stream = nullptr;
     float* astage[2] = {nullptr, nullptr};
-    cudaEvent_t staged[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    cudaEvent_t queued = nullptr, consumed[2] = {nullptr, nullptr}, phi_ready = nullptr;
     int astage_i = 0;
+    bool phi_pending = false;       // the compute stream has not waited for phi_ready yet
     unsigned int* bad_async = nullptr;
     float* mac = nullptr;    // two snapshots of 4 planes: rho, ur, uz, T
     int64_t mstride = 0;
@@ -819,6 +820,15 @@ static Consts<float> to_float(const Consts<double>& d) {
     return f;
 }
 
+// Work that reads or writes the porosity field first waits for an asynchronous upload.
+static int wait_phi(lbm_handle* h) {
+    if (h->phi_pending) {
+        CK(cudaStreamWaitEvent(h->stream, h->phi_ready, 0));
+        h->phi_pending = false;
+    }
+    return LBM_OK;
+}
+
 static dim3 grid2d(const lbm_handle* h, int threads) {
     return dim3((unsigned)((h->p.nz + threads - 1) / threads), (unsigned)h->p.nr);
 }
@@ -882,20 +892,19 @@ int lbm_derive(const lbm_params* p, lbm_info* out) {
 int lbm_destroy(lbm_handle* h) {
     if (!h) return LBM_OK;
     cudaSetDevice(h->device);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);   // an upload may still write phi
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* b : h->buf) cudaFree(b);
     cudaFree(h->tref);
     cudaFree(h->phi);
     cudaFree(h->fstage);
-    if (h->copy_stream) {
-        cudaStreamSynchronize(h->copy_stream);
-        cudaStreamDestroy(h->copy_stream);
-    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     for (int i = 0; i < 2; ++i) {
         cudaFree(h->astage[i]);
-        if (h->staged[i]) cudaEventDestroy(h->staged[i]);
         if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
     }
+    if (h->queued) cudaEventDestroy(h->queued);
+    if (h->phi_ready) cudaEventDestroy(h->phi_ready);
     cudaFree(h->bad_async);
     cudaFree(h->mac);
     cudaFree(h->partials);
@@ -908,6 +917,7 @@ int lbm_destroy(lbm_handle* h) {
 }
 
 static int launch_init(lbm_handle* h, const float* ur, const float* uz, const float* T) {
+    if (int rc = wait_phi(h)) return rc;
     dim3 g = grid2d(h, 128);
     DISPATCH_STO(h->p.storage,
                  k_init<S_><<<g, 128, 0, h->stream>>>(h->cd, bufp<S_>(h, 0), (const PP<S_>*)h->phi, h->plane, ur, uz,
@@ -986,6 +996,7 @@ static int ensure_fstage(lbm_handle* h) {
 int lbm_set_porosity(lbm_handle* h, const float* phi, int on_device) {
     if (!h || !phi) return fail(LBM_ERR_INVALID, "NULL argument");
     CK(cudaSetDevice(h->device));
+    if (int rc = wait_phi(h)) return rc;
     const float* src = phi;
     if (!on_device) {
         int rc = ensure_fstage(h);
@@ -1012,26 +1023,33 @@ int lbm_set_porosity_async(lbm_handle* h, const float* phi) {
         CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
         for (int i = 0; i < 2; ++i) {
             CK(cudaMalloc((void**)&h->astage[i], h->N * sizeof(float)));
-            CK(cudaEventCreateWithFlags(&h->staged[i], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&h->consumed[i], cudaEventDisableTiming));
         }
+        CK(cudaEventCreateWithFlags(&h->queued, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->phi_ready, cudaEventDisableTiming));
         CK(cudaMalloc((void**)&h->bad_async, sizeof(unsigned int)));
         CK(cudaMemsetAsync(h->bad_async, 0, sizeof(unsigned int), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
     }
     const int i = h->astage_i;
     h->astage_i ^= 1;
-    // the conversion that last read staging buffer i has finished before it is refilled
+    // on the copy stream: staging buffer i free (its last conversion done), copy, then
+    // convert once the work queued so far on the compute stream (which reads the old
+    // field) has finished; the compute stream waits for the result only before the next
+    // call that reads the field (wait_phi), so other work overlaps the copy
     CK(cudaStreamWaitEvent(h->copy_stream, h->consumed[i], 0));
     CK(cudaMemcpyAsync(h->astage[i], phi, h->N * sizeof(float), cudaMemcpyHostToDevice, h->copy_stream));
-    CK(cudaEventRecord(h->staged[i], h->copy_stream));
-    // conversion in stream order on the handle's stream: after the steps queued so far
-    CK(cudaStreamWaitEvent(h->stream, h->staged[i], 0));
+    CK(cudaEventRecord(h->queued, h->stream));
+    CK(cudaStreamWaitEvent(h->copy_stream, h->queued, 0));
+    if (h->phi_pending) CK(cudaStreamWaitEvent(h->copy_stream, h->phi_ready, 0));
     const int thr = 256;
     const unsigned blocks = (unsigned)((h->N + thr - 1) / thr);
     DISPATCH_STO(h->p.storage,
-                 k_phi<S_><<<blocks, thr, 0, h->stream>>>(h->astage[i], (PP<S_>*)h->phi, h->N, h->bad_async));
+                 k_phi<S_><<<blocks, thr, 0, h->copy_stream>>>(h->astage[i], (PP<S_>*)h->phi, h->N, h->bad_async));
     CK(cudaGetLastError());
-    CK(cudaEventRecord(h->consumed[i], h->stream));
+    CK(cudaEventRecord(h->consumed[i], h->copy_stream));
+    CK(cudaEventRecord(h->phi_ready, h->copy_stream));
+    h->phi_pending = true;
     return LBM_OK;
 }
 
@@ -1040,6 +1058,8 @@ int lbm_porosity_errors(lbm_handle* h, uint32_t* count, int clear) {
     *count = 0;
     if (!h->bad_async) return LBM_OK;
     CK(cudaSetDevice(h->device));
+    int rc = wait_phi(h);
+    if (rc) return rc;
     unsigned int v = 0;
     CK(cudaMemcpyAsync(&v, h->bad_async, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
     if (clear) CK(cudaMemsetAsync(h->bad_async, 0, sizeof(unsigned int), h->stream));
@@ -1074,6 +1094,7 @@ int lbm_init_fields(lbm_handle* h, const float* ur, const float* uz, const float
 }
 
 static int launch_step(lbm_handle* h) {
+    if (int rc = wait_phi(h)) return rc;
     const int nw = wall_count(h->p.geometry, h->p.nr, h->p.nz);
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (h->timing) {
@@ -1131,6 +1152,7 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
 }
 
 static int launch_moments(lbm_handle* h, int which, float* rho, float* ur, float* uz, float* T) {
+    if (int rc = wait_phi(h)) return rc;
     const dim3 g = grid2d(h, 128);
     DISPATCH_STO(h->p.storage,
                  k_moments<S_><<<g, 128, 0, h->stream>>>(h->cf, bufp<S_>(h, which), (const PP<S_>*)h->phi,
@@ -1204,6 +1226,7 @@ static int residual_between(lbm_handle* h, const float* cur, const float* prev, 
 }
 
 static int snapshot(lbm_handle* h, int which, float* m) {
+    if (int rc = wait_phi(h)) return rc;
     return launch_moments(h, which, m, m + h->mstride, m + 2 * h->mstride, m + 3 * h->mstride);
 }
 
