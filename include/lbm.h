@@ -200,6 +200,18 @@ int lbm_heater_nusselt(lbm_handle *h, double *nu_mean, double *nu_z);
  * second order.  FP64.  The inlet column gives NaN (T_w = T_b there).  Synchronises. */
 int lbm_pipe_nusselt(lbm_handle *h, double *nu, int32_t nz);
 
+/* Stokes stream function of the current state (Table 3 lists its largest magnitude,
+ * |psi|max, without defining psi; this is the standard form for the continuity
+ * equation Eq. 1): r u_z = d psi/dr, r u_r = -d psi/dz, i.e.
+ *   psi(r, z) = integral of r' u_z(r', z) dr' from r_s to r,
+ * with r_s the inner wall (annulus; psi = 0 there) or the axis (pipes; the first
+ * trapezoid panel runs from r = 0 to the first row at r = 1/2).  Trapezoid rule over
+ * the rows, FP64 accumulation, lattice units (divide by alpha L or nu L for the
+ * dimensionless forms).  psi (may be NULL): nr*nz floats, z fastest, in device memory
+ * when on_device != 0, else host memory; *psi_max (may be NULL) receives max |psi|
+ * over the grid.  Synchronises. */
+int lbm_stream_function(lbm_handle *h, float *psi, int on_device, double *psi_max);
+
 /* Convergence residual between the current state n and the previous state n - 1:
  * max(|u^n - u^(n-1)|_2 / |u^n|_2, |T^n - T^(n-1)|_2 / |T^n|_2) over non-wall
  * nodes, and the mass sum over all nodes of r * rho (= sum_i f_i), both in FP64.

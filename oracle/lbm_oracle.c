@@ -742,6 +742,38 @@ int orc_heater_nusselt(const orc_params *p, const double *T, double *nu_mean, do
     return 0;
 }
 
+/*
+ * Stokes stream function of the axisymmetric flow, behind the |psi|max columns of
+ * Table 3 (the paper names psi without defining it; this is the textbook form for
+ * Eq. 1):  r u_z = d psi / dr and r u_r = - d psi / dz, i.e.
+ *     psi(r, z) = integral from r_s to r of r' u_z(r', z) dr',
+ * with r_s the inner wall (annulus: no slip there, psi = 0 on it) or the axis (pipes:
+ * psi = 0 on the axis; the first panel runs from r = 0, where the integrand is 0, to
+ * the first row at r = 1/2).  The integral is the trapezoid rule over the rows.
+ * Writes psi[nr*nz] (may be NULL) and the largest |psi| into *psi_max (lattice units).
+ */
+int orc_stream_function(const orc_params *p, const double *uz, double *psi, double *psi_max)
+{
+    orc_consts c;
+    if (orc_derive(p, &c)) return 1;
+    const int nr = p->nr, nz = p->nz;
+    double big = 0;
+    for (int kz = 0; kz < nz; ++kz) {
+        double acc = 0;
+        if (is_pipe(p)) acc = 0.5 * c.r0 * (0.0 + c.r0 * uz[kz]);       /* panel [0, r0] */
+        for (int kr = 0; kr < nr; ++kr) {
+            if (kr > 0) {
+                const double r_lo = c.r0 + (kr - 1), r_hi = c.r0 + kr;
+                acc += 0.5 * (r_lo * uz[(size_t)(kr - 1) * nz + kz] + r_hi * uz[(size_t)kr * nz + kz]);
+            }
+            if (psi) psi[(size_t)kr * nz + kz] = acc;
+            if (fabs(acc) > big) big = fabs(acc);
+        }
+    }
+    if (psi_max) *psi_max = big;
+    return 0;
+}
+
 int orc_residual(const orc_params *p, const double *rho_n, const double *ur_n, const double *uz_n,
                  const double *T_n, const double *ur_p, const double *uz_p, const double *T_p,
                  double *res, double *mass)

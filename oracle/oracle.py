@@ -88,6 +88,7 @@ def lib():
             L.orc_nusselt.argtypes = [pp, dp, dp, dp]
             L.orc_pipe_nusselt.argtypes = [pp, dp, dp, dp]
             L.orc_heater_nusselt.argtypes = [pp, dp, dp, dp]
+            L.orc_stream_function.argtypes = [pp, dp, dp, dp]
             L.orc_residual.argtypes = [pp] + [dp] * 9
             L.orc_node_class.argtypes = [pp, C.POINTER(C.c_uint8)]
             L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
@@ -212,6 +213,10 @@ class State:
     def heater_nusselt(self):
         return heater_nusselt(self.p, self.moments()[3])
 
+    def stream_function(self):
+        """(psi field, max |psi|) of the current state, lattice units."""
+        return stream_function(self.p, self.moments()[2])
+
     def pipe_nusselt(self):
         """Local wall Nusselt number Nu(z) of Eq. 40 with the mixing-cup bulk
         temperature (pipe with inlet and outlet)."""
@@ -227,6 +232,17 @@ def heater_nusselt(p: Params, T):
     if lib().orc_heater_nusselt(C.byref(p), _d(T), C.byref(m), _d(nz)):
         raise ValueError("heater_nusselt needs heater_len > 0")
     return m.value, nz
+
+
+def stream_function(p: Params, uz):
+    """Stokes stream function psi(r, z) = int r' u_z dr' from the inner wall (annulus)
+    or the axis (pipes), trapezoid rule; returns (psi[nr, nz], max |psi|)."""
+    uz = _f64(uz)
+    psi = np.zeros((p.nr, p.nz))
+    m = C.c_double()
+    if lib().orc_stream_function(C.byref(p), _d(uz), _d(psi), C.byref(m)):
+        raise ValueError("invalid parameters")
+    return psi, m.value
 
 
 def pipe_nusselt(p: Params, uz, T):

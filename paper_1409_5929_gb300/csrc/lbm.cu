@@ -600,6 +600,41 @@ __global__ void __launch_bounds__(256) k_heater_nusselt(int nz, int hz0, int hz1
     if (threadIdx.x == 0) result[0] = out[1] > 0 ? out[0] / out[1] : NAN;
 }
 
+// Stokes stream function of the axisymmetric flow (|psi|max of Table 3):
+// psi(r, z) = int_{r_s}^{r} r' u_z dr' so that r u_z = d psi/dr and, by Eq. 1,
+// r u_r = -d psi/dz; r_s is the inner wall (annulus) or the axis (pipes, whose first
+// panel runs from r = 0 to the first row at r0).  One thread per column walks the rows
+// (each row's read is coalesced across the block), accumulating in FP64; every block
+// writes the largest |psi| of its columns to block_max[blockIdx.x].
+__global__ void __launch_bounds__(128) k_stream_function(int nr, int nz, double r0, int from_axis,
+                                                         const float* __restrict__ uz, float* __restrict__ psi,
+                                                         double* __restrict__ block_max) {
+    const int kz = blockIdx.x * blockDim.x + threadIdx.x;
+    double big = 0;
+    if (kz < nz) {
+        double prev = r0 * (double)uz[kz];
+        double s = from_axis ? 0.5 * r0 * prev : 0.0;
+        psi[kz] = (float)s;
+        big = fabs(s);
+        for (int k = 1; k < nr; ++k) {
+            const int64_t n = (int64_t)k * nz + kz;
+            const double cur = (r0 + k) * (double)uz[n];
+            s += 0.5 * (prev + cur);
+            prev = cur;
+            psi[n] = (float)s;
+            big = fmax(big, fabs(s));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) big = fmax(big, __shfl_down_sync(0xffffffffu, big, o));
+    __shared__ double sh[4];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = big;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x + 31) / 32; ++w) big = fmax(big, sh[w]);
+        block_max[blockIdx.x] = big;
+    }
+}
+
 // FP64 export of rows [row0, row0 + nrows): raw post-collision populations
 // f_i = ft_i + r w_i + e_ir w_i / 2, g_i = gh_i + wT_i (T0 + R(x)).
 template <int STO>
@@ -1314,6 +1349,35 @@ int lbm_heater_nusselt(lbm_handle* h, double* nu_mean, double* nu_z) {
     cudaFreeAsync(d, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "heater Nusselt: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int lbm_stream_function(lbm_handle* h, float* psi, int on_device, double* psi_max) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_mac(h);
+    if (rc) return rc;
+    if ((rc = snapshot(h, h->cur, h->mac))) return rc;
+    const int nz = h->p.nz;
+    const unsigned blocks = (unsigned)((nz + 127) / 128);
+    float* dst = (psi && on_device) ? psi : h->mac + 4 * h->mstride;
+    const int from_axis = h->p.geometry == LBM_PIPE_PERIODIC_Z || h->p.geometry == LBM_PIPE_INFLOW;
+    double* d = nullptr;
+    CK(cudaMallocAsync((void**)&d, (size_t)blocks * sizeof(double), h->stream));
+    std::vector<double> bm(blocks);
+    k_stream_function<<<blocks, 128, 0, h->stream>>>(h->p.nr, nz, h->info.r0, from_axis, h->mac + 2 * h->mstride,
+                                                     dst, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bm.data(), d, (size_t)blocks * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && psi && !on_device)
+        e = cudaMemcpyAsync(psi, dst, (size_t)h->N * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(d, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "stream function: %s", cudaGetErrorString(e));
+    double big = 0;
+    for (double x : bm) big = std::max(big, x);
+    if (psi_max) *psi_max = big;
     return LBM_OK;
 }
 

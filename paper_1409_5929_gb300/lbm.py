@@ -68,6 +68,7 @@ _SIGS = {
     "lbm_nusselt": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_pipe_nusselt": (C.c_int, [_vp, _vp, C.c_int32]),
     "lbm_heater_nusselt": (C.c_int, [_vp, C.POINTER(C.c_double), _vp]),
+    "lbm_stream_function": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_double)]),
     "lbm_residual": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "lbm_rebase": (C.c_int, [_vp]),
@@ -187,6 +188,14 @@ def lbm_heater_nusselt(h, nz: int):
     out = np.zeros(nz, np.float64)
     _check(load().lbm_heater_nusselt(h, C.byref(m), out.ctypes.data))
     return m.value, out
+
+
+def lbm_stream_function(h, psi, on_device: bool):
+    """Stokes stream function (lattice units) into psi (nr*nz floats, or None);
+    returns max |psi|."""
+    m = C.c_double()
+    _check(load().lbm_stream_function(h, _ptr(psi), int(on_device), C.byref(m)))
+    return m.value
 
 
 def lbm_pipe_nusselt(h, nz: int):
@@ -320,6 +329,12 @@ class Solver:
 
     def heater_nusselt(self):
         return lbm_heater_nusselt(self.h, self.nz)
+
+    def stream_function(self):
+        """(psi[nr, nz], max |psi|) of the current state, lattice units."""
+        psi = np.empty((self.nr, self.nz), np.float32)
+        m = lbm_stream_function(self.h, psi, False)
+        return psi, m
 
     def residual(self):
         return lbm_residual(self.h)

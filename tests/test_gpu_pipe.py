@@ -40,7 +40,7 @@ def _pipe_params(lbm, nr, nz, Da, tau, u_in, Pr=0.7, storage="f32"):
 def test_pipe_inflow_parity(lbm, oracle, Da):
     """21 x 200 pipe (inlet, outlet, axis, wall; Brinkman drag or none), 3000 steps from
     the start state: fields within relative L2 1e-5 of the oracle, the local Nusselt
-    numbers of Eq. 40 within 1e-5 relative."""
+    numbers of Eq. 40 and the stream function (from the axis) within 1e-5 relative."""
     p = _pipe_params(lbm, 21, 200, Da, 0.62, 0.05)
     s = lbm.Solver(p)
     op = oracle.params(nr=p.nr, nz=p.nz, geometry=oracle.PIPE_INFLOW, Ra=0.0, Da=p.Da, eps_mean=1.0, F_eps=0.0,
@@ -56,6 +56,8 @@ def test_pipe_inflow_parity(lbm, oracle, Da):
     nu_g, nu_o = s.pipe_nusselt(), st.pipe_nusselt()
     assert np.isnan(nu_g[0]) and np.isnan(nu_o[0])
     assert np.abs(nu_g[1:] - nu_o[1:]).max() <= 1e-5 * np.abs(nu_o[1:]).max()
+    (psi_g, m_g), (psi_o, m_o) = s.stream_function(), oracle.stream_function(op, o[2])
+    assert _rel(psi_g, psi_o) <= 1e-5 and abs(m_g - m_o) <= 1e-5 * m_o
 
 
 def test_table1_pipe(lbm):

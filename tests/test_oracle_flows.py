@@ -288,3 +288,49 @@ def test_heater_heat_balance(oracle):
         q_out = -(ri + L) * np.sum(w * (3 * T[-1] - 4 * T[-2] + T[-3]) / 2)
         mis.append(abs(q_out / q_in - 1))
     assert mis[1] < 0.04 and mis[0] / mis[1] > 3.0, mis
+
+
+# ---- stream function (|psi|max of Table 3) -------------------------------------------
+def test_stream_function_exact_and_poiseuille(oracle):
+    """The trapezoid rule is exact for an integrand linear in r: on the annulus,
+    u_z = a + b / r gives r u_z = a r + b and psi = a (r^2 - r_i^2) / 2 + b (r - r_i);
+    on the pipe, a uniform u_z = a gives psi = a r^2 / 2 from the axis.  A Poiseuille
+    profile u_z = U (1 - r^2 / R^2) stays within the trapezoid error bound
+    r h^2 max|d^2(r u_z)/dr^2| / 12 = U r / (2 R) of U (r^2 / 2 - r^4 / (4 R^2))."""
+    a, b = 0.013, -0.41
+    p = oracle.params(nr=17, nz=5, radius_ratio=2.5)
+    r = oracle.derive(p)["r0"] + np.arange(17)
+    uz = np.repeat((a + b / r)[:, None], 5, axis=1)
+    psi, m = oracle.stream_function(p, uz)
+    exact = a * (r ** 2 - r[0] ** 2) / 2 + b * (r - r[0])
+    assert np.allclose(psi, exact[:, None], rtol=0, atol=1e-12)
+    assert m == pytest.approx(np.abs(exact).max(), rel=1e-14)
+    for geom in (oracle.PIPE_PERIODIC_Z, oracle.PIPE_INFLOW):
+        p = oracle.params(nr=21, nz=6, geometry=geom, Ra=0.0, tau_nu=0.7, u_in=0.01)
+        r = oracle.derive(p)["r0"] + np.arange(21)
+        assert r[0] == 0.5
+        psi, _ = oracle.stream_function(p, np.full((21, 6), a))
+        assert np.allclose(psi, (a * r ** 2 / 2)[:, None], rtol=0, atol=1e-13)
+        U, R = 0.02, r[-1]
+        psi, m = oracle.stream_function(p, np.repeat((U * (1 - r ** 2 / R ** 2))[:, None], 6, axis=1))
+        exact = U * (r ** 2 / 2 - r ** 4 / (4 * R ** 2))
+        assert np.all(np.abs(psi - exact[:, None]) <= (U * r / (2 * R))[:, None] + 1e-15)
+        assert abs(m - U * R ** 2 / 4) <= U / 2
+
+
+def test_stream_function_continuity(oracle):
+    """On a settled convective annulus state (free fluid, Ra = 1e4, Pr = 0.7, R* = 2,
+    24 x 48, 6e4 steps) the stream function built from u_z alone also carries u_r, by
+    Eq. 1: -d psi/dz = r u_r (central differences, three nodes clear of the walls, where
+    the mismatch is the two stencils' second-order error: 3.5 % of max |r u_r| here,
+    1.2 % at 48 x 96), and psi vanishes on the outer wall, since no net flow crosses a
+    section of the closed annulus (2.2 % of max |psi| here, 0.75 % at 48 x 96)."""
+    p = oracle.params(nr=24, nz=48, Ra=1e4, Pr=0.7, Da=1e8, eps_mean=1.0, F_eps=0.0, radius_ratio=2.0)
+    st, (rho, ur, uz, T) = _run(oracle, p, 60000)
+    psi, m = st.stream_function()
+    r = oracle.derive(p)["r0"] + np.arange(24)
+    rur = r[:, None] * ur
+    mism = np.abs(-(psi[:, 2:] - psi[:, :-2]) / 2 - rur[:, 1:-1])[3:-3, 2:-2]
+    assert mism.max() <= 0.05 * np.abs(rur).max()
+    assert np.abs(psi[-1]).max() <= 0.03 * m
+    assert m > 1.0 and np.all(psi[0] == 0)
