@@ -191,11 +191,12 @@ def run_ours(args, rank, world, local_rank):
     value = ups / 1e6
 
     # end to end through the C ABI with host buffers: every step uploads its porosity field
-    # from pinned host memory and reads its Nusselt numbers back (synchronising); the upload
-    # of step n + 1's input runs on the handle's copy stream while step n computes
+    # from pinned host memory (the upload of step n + 1's input runs on the handle's copy
+    # stream while step n computes) and copies its two Nusselt numbers back to pinned host
+    # memory; the host waits once, at the end of the timed region, and checks every result
     ke = max(3, min(args.steps // 10, 50))
     phi_pinned = torch.from_numpy(phi).pin_memory()
-    nu = None
+    nus = torch.full((ke, 2), float("nan"), dtype=torch.float64).pin_memory()
     lbm.lbm_porosity_errors(s.h)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -204,8 +205,12 @@ def run_ours(args, rank, world, local_rank):
         s.step(1)
         if n + 1 < ke:
             lbm.lbm_set_porosity_async(s.h, phi_pinned.data_ptr())  # input of step n + 1
-        nu = s.nusselt()
+        lbm.lbm_nusselt_async(s.h, nus[n])
+    lbm.lbm_sync(s.h)
     t1 = time.perf_counter()
+    nu = nus[-1].tolist()
+    if not bool(torch.isfinite(nus).all()):
+        raise RuntimeError("a step's Nusselt numbers did not arrive or are not finite")
     if lbm.lbm_porosity_errors(s.h):
         raise RuntimeError("porosity upload saw values outside (0, 1]")
     e2e_ups, _ = aggregate((t1 - t0) * 1e3, float(nodes) * ke, device="cuda")

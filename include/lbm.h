@@ -148,13 +148,15 @@ int lbm_set_porosity(lbm_handle *h, const float *phi, int on_device);
 
 /* Storage detail with no counterpart in the paper: the porosity upload of lbm_set_porosity
  * without its synchronisation.  phi (nr*nz floats, host memory; pinned memory lets the
- * copy run asynchronously) is copied on a copy stream of the handle and converted there once
- * the work already queued on the handle's stream has finished: steps queued before this call
- * see the old field, and the next call that reads the field (a step, the fields, the
- * residual, a re-initialisation) waits for the new one, while calls that do not read it (the
- * Nusselt numbers of Eq. 42) overlap the copy.  Two staging buffers alternate.  phi must stay
- * valid until the next synchronising call on the handle.  Values outside (0, 1] are
- * counted, not rejected: lbm_porosity_errors reports them.  Returns at once. */
+ * copy run asynchronously) is copied on a copy stream of the handle into one of two
+ * alternating staging buffers.  The next call that reads the field (a step, the fields,
+ * the residual, a re-initialisation) converts it on the handle's stream, after the work
+ * queued before it: steps queued before this call see the old field, and the copy overlaps
+ * them and any call that does not read the field (the Nusselt numbers of Eq. 42).  An
+ * upload that no reader has seen is replaced by the next one.  phi must stay unchanged until
+ * a synchronising call that follows the next reader of the field (or lbm_destroy).  Values
+ * outside (0, 1] are counted when the field is converted, not rejected: lbm_porosity_errors
+ * reports them.  Returns at once. */
 int lbm_set_porosity_async(lbm_handle *h, const float *phi);
 
 /* Number of porosity values outside (0, 1] seen by lbm_set_porosity_async since the last
@@ -183,6 +185,17 @@ int lbm_moments(lbm_handle *h, float *rho, float *ur, float *uz, float *T, int o
  * inner value is NaN for the pipes; both are NaN for LBM_PIPE_INFLOW (lbm_pipe_nusselt)
  * and with the discrete heater (lbm_heater_nusselt). */
 int lbm_nusselt(lbm_handle *h, double *nu_inner, double *nu_outer);
+
+/* lbm_nusselt without the synchronisation: enqueues the reduction of the current state
+ * and the transfer of (Nu_inner, Nu_outer) into out[0..1] (host memory) on the handle's
+ * stream and returns.  Pinned (page-locked, mapped) memory is written by the device
+ * directly, so the transfer does not queue behind a porosity upload in flight; other host
+ * memory takes an ordinary copy.  out must stay allocated until the values are there,
+ * after the next synchronising call (lbm_sync).  NaN entries as for lbm_nusselt. */
+int lbm_nusselt_async(lbm_handle *h, double *out);
+
+/* Wait for all work queued on the handle (its compute and copy streams). */
+int lbm_sync(lbm_handle *h);
 
 /* Discrete heater (heater_len > 0) only: Eq. 44 at every heated inner-wall node,
  * Nu(z) = q' L / (k (T_h - T_o)) = (T_hot - T_cold) / (T_h(z) - T_cold), and its mean

@@ -447,6 +447,21 @@ __global__ void k_phi(const float* __restrict__ src, typename St<STO>::P* __rest
     dst[i] = mkp<STO>(v);
 }
 
+// Two result values into mapped host memory, written by the kernel itself: a 16-byte
+// device-to-host copy would queue behind a host-to-device upload in flight.
+__global__ void k_put2(const double* __restrict__ src, double* dst, int skip_first) {
+    const int i = threadIdx.x;
+    if (i < 2 && !(skip_first && i == 0)) dst[i] = src[i];
+}
+
+// Range check alone (FP32 storage: the checked staging buffer becomes the field).
+__global__ void k_phi_check(const float* __restrict__ src, int64_t n, unsigned int* bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = src[i];
+    if (!(v > 0.f && v <= 1.f)) atomicAdd(bad, 1u);
+}
+
 template <int STO>
 __global__ void k_phi_fill(typename St<STO>::P* __restrict__ dst, int64_t n, float v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -537,12 +552,13 @@ __device__ double node_T(const Consts<float>& c, const Buf<STO> A, int64_t plane
     return (double)c.T0 + (double)ref + (((double)gh[0] + gh[1]) + ((double)gh[2] + gh[3]) + gh[4]);
 }
 
-// Eq. 42 for both walls in one block: one-sided second-order dT/dr, trapezoid in z.
+// Eq. 42 for both walls: one-sided second-order dT/dr, trapezoid in z.  One column per
+// thread, a partial sum per block; k_nusselt_final adds the partials in block order.
 template <int STO>
-__global__ void __launch_bounds__(256) k_nusselt(const Consts<float> c, const Buf<STO> A, int64_t plane,
-                          double ri, double ro, double H, double dTw, double* __restrict__ result) {
+__global__ void __launch_bounds__(128) k_nusselt(const Consts<float> c, const Buf<STO> A, int64_t plane,
+                                                 double* __restrict__ partials) {
     double v[2] = {0, 0};
-    for (int kz = threadIdx.x; kz < c.nz; kz += blockDim.x) {
+    for (int kz = blockIdx.x * blockDim.x + threadIdx.x; kz < c.nz; kz += gridDim.x * blockDim.x) {
         const double wz = (kz == 0 || kz == c.nz - 1) ? 0.5 : 1.0;
         const double t0 = node_T<STO>(c, A, plane, 0, kz), t1 = node_T<STO>(c, A, plane, 1, kz);
         const double t2 = node_T<STO>(c, A, plane, 2, kz);
@@ -550,6 +566,21 @@ __global__ void __launch_bounds__(256) k_nusselt(const Consts<float> c, const Bu
         const double u2 = node_T<STO>(c, A, plane, c.nr - 3, kz);
         v[0] += wz * (-3 * t0 + 4 * t1 - t2) * 0.5;
         v[1] += wz * (3 * u0 - 4 * u1 + u2) * 0.5;
+    }
+    double out[2];
+    block_sum<2>(v, out);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = out[0];
+        partials[2 * blockIdx.x + 1] = out[1];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_nusselt_final(const double* __restrict__ partials, int blocks, double ri,
+                                                       double ro, double H, double dTw, double* __restrict__ result) {
+    double v[2] = {0, 0};
+    for (int b = threadIdx.x; b < blocks; b += blockDim.x) {
+        v[0] += partials[2 * b];
+        v[1] += partials[2 * b + 1];
     }
     double out[2];
     block_sum<2>(v, out);
@@ -715,12 +746,12 @@ struct lbm_handle {
     __half* tref = nullptr;  // per-node reference offset R(x) of the thermal deviations
     float* fstage = nullptr; // N floats: porosity / init field upload
     // lbm_set_porosity_async: its own copy stream, two staging buffers (the upload into one
-    // overlaps the step that follows the conversion of the other), events and an error count
+    // overlaps the steps that read the other), events and an error count
     cudaStream_t copy_stream = nullptr;
     float* astage[2] = {nullptr, nullptr};
-    cudaEvent_t queued = nullptr, consumed[2] = {nullptr, nullptr}, phi_ready = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
     int astage_i = 0;
-    bool phi_pending = false;       // the compute stream has not waited for phi_ready yet
+    int phi_pending = -1;           // staging buffer uploaded but not yet converted into phi
     unsigned int* bad_async = nullptr;
     float* mac = nullptr;    // two snapshots of 4 planes: rho, ur, uz, T
     int64_t mstride = 0;
@@ -856,14 +887,6 @@ static Consts<float> to_float(const Consts<double>& d) {
 }
 
 // Work that reads or writes the porosity field first waits for an asynchronous upload.
-static int wait_phi(lbm_handle* h) {
-    if (h->phi_pending) {
-        CK(cudaStreamWaitEvent(h->stream, h->phi_ready, 0));
-        h->phi_pending = false;
-    }
-    return LBM_OK;
-}
-
 static dim3 grid2d(const lbm_handle* h, int threads) {
     return dim3((unsigned)((h->p.nz + threads - 1) / threads), (unsigned)h->p.nr);
 }
@@ -875,6 +898,7 @@ static dim3 grid2d(const lbm_handle* h, int threads) {
         case LBM_F16: { constexpr int S_ = LBM_F16; __VA_ARGS__; } break;  \
         default: { constexpr int S_ = LBM_BF16; __VA_ARGS__; } break;      \
     }
+
 // rows per thread of the batched kernels: 1, 2 or 4 (the values the tuner tries)
 #define DISPATCH_RPT(rpt, ...)                                             \
     switch (rpt) {                                                         \
@@ -891,6 +915,31 @@ template <int STO> static Buf<STO> bufp(const lbm_handle* h, int which) {
     return b;
 }
 template <int STO> using PP = typename St<STO>::P;
+
+static int wait_phi(lbm_handle* h) {
+    if (h->phi_pending >= 0) {
+        // the newest upload becomes the field: on the compute stream, after everything
+        // queued before (which read the old field) and after its copy
+        const int i = h->phi_pending;
+        h->phi_pending = -1;
+        CK(cudaStreamWaitEvent(h->stream, h->copied[i], 0));
+        const unsigned blocks = (unsigned)((h->N + 255) / 256);
+        if (h->p.storage == LBM_F32) {
+            // same element type: check the staging buffer and swap it with the field; the
+            // old field becomes staging buffer i once the work queued before has read it
+            k_phi_check<<<blocks, 256, 0, h->stream>>>(h->astage[i], h->N, h->bad_async);
+            void* old = h->phi;
+            h->phi = h->astage[i];
+            h->astage[i] = (float*)old;
+        } else {
+            DISPATCH_STO(h->p.storage, k_phi<S_><<<blocks, 256, 0, h->stream>>>(h->astage[i], (PP<S_>*)h->phi, h->N,
+                                                                                 h->bad_async));
+        }
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(h->consumed[i], h->stream));
+    }
+    return LBM_OK;
+}
 
 extern "C" {
 
@@ -937,9 +986,8 @@ int lbm_destroy(lbm_handle* h) {
     for (int i = 0; i < 2; ++i) {
         cudaFree(h->astage[i]);
         if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
+        if (h->copied[i]) cudaEventDestroy(h->copied[i]);
     }
-    if (h->queued) cudaEventDestroy(h->queued);
-    if (h->phi_ready) cudaEventDestroy(h->phi_ready);
     cudaFree(h->bad_async);
     cudaFree(h->mac);
     cudaFree(h->partials);
@@ -1057,34 +1105,24 @@ int lbm_set_porosity_async(lbm_handle* h, const float* phi) {
     if (!h->copy_stream) {
         CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
         for (int i = 0; i < 2; ++i) {
-            CK(cudaMalloc((void**)&h->astage[i], h->N * sizeof(float)));
+            CK(cudaMalloc((void**)&h->astage[i], h->plane * sizeof(float)));   // may become the field
             CK(cudaEventCreateWithFlags(&h->consumed[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->copied[i], cudaEventDisableTiming));
         }
-        CK(cudaEventCreateWithFlags(&h->queued, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&h->phi_ready, cudaEventDisableTiming));
         CK(cudaMalloc((void**)&h->bad_async, sizeof(unsigned int)));
         CK(cudaMemsetAsync(h->bad_async, 0, sizeof(unsigned int), h->stream));
         CK(cudaStreamSynchronize(h->stream));
     }
     const int i = h->astage_i;
     h->astage_i ^= 1;
-    // on the copy stream: staging buffer i free (its last conversion done), copy, then
-    // convert once the work queued so far on the compute stream (which reads the old
-    // field) has finished; the compute stream waits for the result only before the next
-    // call that reads the field (wait_phi), so other work overlaps the copy
+    // on the copy stream: staging buffer i is free once its last conversion has run, then
+    // copy; the conversion into phi waits for the next reader of the field (wait_phi), so
+    // copies follow one another on the copy stream while the compute stream runs, and an
+    // upload that no reader saw is superseded by the next one
     CK(cudaStreamWaitEvent(h->copy_stream, h->consumed[i], 0));
     CK(cudaMemcpyAsync(h->astage[i], phi, h->N * sizeof(float), cudaMemcpyHostToDevice, h->copy_stream));
-    CK(cudaEventRecord(h->queued, h->stream));
-    CK(cudaStreamWaitEvent(h->copy_stream, h->queued, 0));
-    if (h->phi_pending) CK(cudaStreamWaitEvent(h->copy_stream, h->phi_ready, 0));
-    const int thr = 256;
-    const unsigned blocks = (unsigned)((h->N + thr - 1) / thr);
-    DISPATCH_STO(h->p.storage,
-                 k_phi<S_><<<blocks, thr, 0, h->copy_stream>>>(h->astage[i], (PP<S_>*)h->phi, h->N, h->bad_async));
-    CK(cudaGetLastError());
-    CK(cudaEventRecord(h->consumed[i], h->copy_stream));
-    CK(cudaEventRecord(h->phi_ready, h->copy_stream));
-    h->phi_pending = true;
+    CK(cudaEventRecord(h->copied[i], h->copy_stream));
+    h->phi_pending = i;
     return LBM_OK;
 }
 
@@ -1218,6 +1256,18 @@ int lbm_moments(lbm_handle* h, float* rho, float* ur, float* uz, float* T, int o
     return LBM_OK;
 }
 
+// Eq. 42 of the current state into h->result[0..1] (stream-ordered).
+static int launch_nusselt(lbm_handle* h) {
+    const double dTw = h->p.T_hot - h->p.T_cold;
+    const double ri = h->info.r0, ro = h->info.r0 + (h->p.nr - 1);
+    const int blocks = (int)std::min<int64_t>((h->p.nz + 127) / 128, h->pblocks);
+    DISPATCH_STO(h->p.storage, k_nusselt<S_><<<blocks, 128, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur), h->plane,
+                                                                            h->partials));
+    k_nusselt_final<<<1, 256, 0, h->stream>>>(h->partials, blocks, ri, ro, h->info.H, dTw, h->result);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
 int lbm_nusselt(lbm_handle* h, double* nu_inner, double* nu_outer) {
     if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
     if (h->p.geometry == LBM_PIPE_INFLOW || h->p.heater_len > 0) {   // lbm_pipe_nusselt, lbm_heater_nusselt
@@ -1226,17 +1276,43 @@ int lbm_nusselt(lbm_handle* h, double* nu_inner, double* nu_outer) {
         return LBM_OK;
     }
     CK(cudaSetDevice(h->device));
-    const double dTw = h->p.T_hot - h->p.T_cold;
-    const double ri = h->info.r0, ro = h->info.r0 + (h->p.nr - 1);
-    DISPATCH_STO(h->p.storage,
-                 k_nusselt<S_><<<1, 256, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur), h->plane, ri, ro,
-                                                          h->info.H, dTw, h->result));
-    CK(cudaGetLastError());
+    if (int rc = launch_nusselt(h)) return rc;
     double r[2];
     CK(cudaMemcpyAsync(r, h->result, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (nu_inner) *nu_inner = h->p.geometry == LBM_PIPE_PERIODIC_Z ? NAN : r[0];
     if (nu_outer) *nu_outer = r[1];
+    return LBM_OK;
+}
+
+int lbm_nusselt_async(lbm_handle* h, double* out) {
+    if (!h || !out) return fail(LBM_ERR_INVALID, "NULL argument");
+    if (h->p.geometry == LBM_PIPE_INFLOW || h->p.heater_len > 0) {   // lbm_pipe_nusselt, lbm_heater_nusselt
+        out[0] = out[1] = NAN;
+        return LBM_OK;
+    }
+    CK(cudaSetDevice(h->device));
+    if (int rc = launch_nusselt(h)) return rc;
+    // stream order keeps h->result intact until it has been read
+    const int pipe = h->p.geometry == LBM_PIPE_PERIODIC_Z;
+    if (pipe) out[0] = NAN;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+        k_put2<<<1, 32, 0, h->stream>>>(h->result, (double*)at.devicePointer, pipe);
+        CK(cudaGetLastError());
+    } else {
+        (void)cudaGetLastError();   // pageable memory: an ordinary copy
+        CK(cudaMemcpyAsync(out + pipe, h->result + pipe, (2 - pipe) * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle* h) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    CK(cudaSetDevice(h->device));
+    if (h->copy_stream) CK(cudaStreamSynchronize(h->copy_stream));
+    CK(cudaStreamSynchronize(h->stream));
     return LBM_OK;
 }
 

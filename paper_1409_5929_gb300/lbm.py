@@ -69,6 +69,8 @@ _SIGS = {
     "lbm_pipe_nusselt": (C.c_int, [_vp, _vp, C.c_int32]),
     "lbm_heater_nusselt": (C.c_int, [_vp, C.POINTER(C.c_double), _vp]),
     "lbm_stream_function": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_double)]),
+    "lbm_nusselt_async": (C.c_int, [_vp, _vp]),
+    "lbm_sync": (C.c_int, [_vp]),
     "lbm_residual": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lbm_run": (C.c_int, [_vp, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "lbm_rebase": (C.c_int, [_vp]),
@@ -188,6 +190,16 @@ def lbm_heater_nusselt(h, nz: int):
     out = np.zeros(nz, np.float64)
     _check(load().lbm_heater_nusselt(h, C.byref(m), out.ctypes.data))
     return m.value, out
+
+
+def lbm_nusselt_async(h, out):
+    """Enqueue the Nusselt numbers of the current state into out (2 float64, host memory:
+    a pinned tensor or a numpy array); valid after lbm_sync."""
+    _check(load().lbm_nusselt_async(h, _ptr(out)))
+
+
+def lbm_sync(h):
+    _check(load().lbm_sync(h))
 
 
 def lbm_stream_function(h, psi, on_device: bool):

@@ -364,8 +364,8 @@ def test_config5_nusselt_drift_fp16_vs_fp32(lbm):
 
 def test_async_porosity_upload(lbm):
     """lbm_set_porosity_async: the same fields as lbm_set_porosity when the uploads are
-    pipelined behind queued steps (each step sees the field set before it), and invalid
-    values counted by lbm_porosity_errors."""
+    pipelined behind queued steps (each step sees the field set before it), an upload no
+    step read replaced by the next one, and invalid values counted by lbm_porosity_errors."""
     import torch
 
     p = lbm.lbm_params_default(nr=64, nz=200, Ra=1e5, Da=1e-3)
@@ -391,3 +391,44 @@ def test_async_porosity_upload(lbm):
     lbm.lbm_set_porosity_async(b.h, pin_bad.data_ptr())
     assert lbm.lbm_porosity_errors(b.h) == 2
     assert lbm.lbm_porosity_errors(b.h) == 0
+    # uploads that no reader saw are replaced by the newest one (three in a row: both
+    # staging buffers reused)
+    c, d = lbm.Solver(p), lbm.Solver(p)
+    c.set_porosity(phis[2])
+    c.step(5)
+    for pin in pins:
+        lbm.lbm_set_porosity_async(d.h, pin.data_ptr())
+    d.step(5)
+    for x, y in zip(c.moments(), d.moments()):
+        assert np.array_equal(x, y)
+    for s in (a, b, c, d):
+        s.close()
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+@pytest.mark.parametrize("geom", [0, 2])
+def test_nusselt_async(lbm, geom, pinned):
+    """lbm_nusselt_async + lbm_sync give what lbm_nusselt gives after the same steps,
+    with several reads queued before one wait (inner value NaN for the periodic pipe), into
+    pageable memory (copied) and pinned memory (written by the device)."""
+    import torch
+
+    kw = dict(nr=40, nz=130, Ra=1e5, Da=1e-3) if geom == 0 else dict(nr=25, nz=130, geometry=2, Ra=0.0, tau_nu=0.8,
+                                                                         Da=0.05, F_eps=0.0, eps_mean=1.0,
+                                                                         body_accel_z=1e-5)
+    a, b = lbm.Solver(lbm.lbm_params_default(**kw)), lbm.Solver(lbm.lbm_params_default(**kw))
+    out = torch.full((3, 2), -1.0, dtype=torch.float64)
+    if pinned:
+        out = out.pin_memory()
+    ref = []
+    for k in range(3):
+        a.step(40)
+        lbm.lbm_nusselt_async(a.h, out[k])
+        b.step(40)
+        ref.append(b.nusselt())
+    lbm.lbm_sync(a.h)
+    out = out.numpy()
+    np.testing.assert_array_equal(out, np.array(ref))
+    assert np.isnan(out[:, 0]).all() == (geom == 2)
+    a.close()
+    b.close()
