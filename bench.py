@@ -40,7 +40,7 @@ SAMPLE_NR, SAMPLE_NZ = 256, 512   # bounded CPU sample: the same recipe on a 256
 # DRAM traffic of one k_bulk launch on the 4096 x 8192 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum, one single-pass ncu capture; profiles/k_bulk_f32_4096x8192_traffic.md),
 # valid only for the kernel sources it was taken on (hash of csrc/lbm.cu + lbm_physics.cuh).
-TRAFFIC = {("f32", 4096, 8192): ("d92bde0dbab1be2c", 2.09e9 + 1.83e9)}
+TRAFFIC = {("f32", 4096, 8192): ("783b26cec0d9b7f4", 2.09e9 + 1.83e9)}
 
 
 def _kernel_hash() -> str:
