@@ -437,14 +437,31 @@ template <> __device__ __forceinline__ __half mkp<LBM_F16>(float v) { return __f
 template <> __device__ __forceinline__ __half mkp<LBM_BF16>(float v) { return __float2half_rn(v); }
 
 // Porosity upload: validate (0 < phi <= 1) and convert to the storage type.
+__device__ __forceinline__ unsigned int bad_phi(float v) { return !(v > 0.f && v <= 1.f); }
+
+// Porosity upload: count of values outside (0, 1] and conversion to the storage type.
+// Grid-stride; 16-byte loads when src is 16-byte aligned (vec != 0), then the ragged tail
+// one value at a time.
 template <int STO>
-__global__ void k_phi(const float* __restrict__ src, typename St<STO>::P* __restrict__ dst, int64_t n,
+__global__ void k_phi(const float* __restrict__ src, typename St<STO>::P* __restrict__ dst, int64_t n, int vec,
                       unsigned int* bad) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float v = src[i];
-    if (!(v > 0.f && v <= 1.f)) atomicAdd(bad, 1u);
-    dst[i] = mkp<STO>(v);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = vec ? n / 4 : 0;
+    unsigned int cnt = 0;
+    for (int64_t q = t; q < n4; q += stride) {
+        const float4 v = reinterpret_cast<const float4*>(src)[q];
+        cnt += bad_phi(v.x) + bad_phi(v.y) + bad_phi(v.z) + bad_phi(v.w);
+        dst[4 * q] = mkp<STO>(v.x);
+        dst[4 * q + 1] = mkp<STO>(v.y);
+        dst[4 * q + 2] = mkp<STO>(v.z);
+        dst[4 * q + 3] = mkp<STO>(v.w);
+    }
+    for (int64_t i = 4 * n4 + t; i < n; i += stride) {
+        const float v = src[i];
+        cnt += bad_phi(v);
+        dst[i] = mkp<STO>(v);
+    }
+    if (cnt) atomicAdd(bad, cnt);
 }
 
 // Two result values into mapped host memory, written by the kernel itself: a 16-byte
@@ -454,13 +471,26 @@ __global__ void k_put2(const double* __restrict__ src, double* dst, int skip_fir
     if (i < 2 && !(skip_first && i == 0)) dst[i] = src[i];
 }
 
-// Range check alone (FP32 storage: the checked staging buffer becomes the field).
+// Range check alone (FP32 storage: the checked staging buffer becomes the field); src is a
+// staging buffer (cudaMalloc, 16-byte aligned).
 __global__ void k_phi_check(const float* __restrict__ src, int64_t n, unsigned int* bad) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float v = src[i];
-    if (!(v > 0.f && v <= 1.f)) atomicAdd(bad, 1u);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n / 4;
+    unsigned int cnt = 0;
+    for (int64_t q = t; q < n4; q += stride) {
+        const float4 v = reinterpret_cast<const float4*>(src)[q];
+        cnt += bad_phi(v.x) + bad_phi(v.y) + bad_phi(v.z) + bad_phi(v.w);
+    }
+    for (int64_t i = 4 * n4 + t; i < n; i += stride) cnt += bad_phi(src[i]);
+    if (cnt) atomicAdd(bad, cnt);
 }
+
+// Blocks of 256 threads for the grid-stride porosity kernels over n values.
+static unsigned int phi_blocks(int64_t n) {
+    return (unsigned int)std::max<int64_t>(1, std::min<int64_t>((n / 4 + 255) / 256, 4096));
+}
+
+static int aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 template <int STO>
 __global__ void k_phi_fill(typename St<STO>::P* __restrict__ dst, int64_t n, float v) {
@@ -923,7 +953,7 @@ static int wait_phi(lbm_handle* h) {
         const int i = h->phi_pending;
         h->phi_pending = -1;
         CK(cudaStreamWaitEvent(h->stream, h->copied[i], 0));
-        const unsigned blocks = (unsigned)((h->N + 255) / 256);
+        const unsigned blocks = phi_blocks(h->N);
         if (h->p.storage == LBM_F32) {
             // same element type: check the staging buffer and swap it with the field; the
             // old field becomes staging buffer i once the work queued before has read it
@@ -933,7 +963,7 @@ static int wait_phi(lbm_handle* h) {
             h->astage[i] = (float*)old;
         } else {
             DISPATCH_STO(h->p.storage, k_phi<S_><<<blocks, 256, 0, h->stream>>>(h->astage[i], (PP<S_>*)h->phi, h->N,
-                                                                                 h->bad_async));
+                                                                                 1, h->bad_async));
         }
         CK(cudaGetLastError());
         CK(cudaEventRecord(h->consumed[i], h->stream));
@@ -1088,9 +1118,8 @@ int lbm_set_porosity(lbm_handle* h, const float* phi, int on_device) {
         src = h->fstage;
     }
     CK(cudaMemsetAsync(h->bad, 0, sizeof(unsigned int), h->stream));
-    const int thr = 256;
-    const unsigned blocks = (unsigned)((h->N + thr - 1) / thr);
-    DISPATCH_STO(h->p.storage, k_phi<S_><<<blocks, thr, 0, h->stream>>>(src, (PP<S_>*)h->phi, h->N, h->bad));
+    DISPATCH_STO(h->p.storage, k_phi<S_><<<phi_blocks(h->N), 256, 0, h->stream>>>(src, (PP<S_>*)h->phi, h->N,
+                                                                                   aligned16(src), h->bad));
     CK(cudaGetLastError());
     unsigned int bad = 0;
     CK(cudaMemcpyAsync(&bad, h->bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
@@ -2010,8 +2039,8 @@ int lbm_batch_set_porosity(lbm_batch* b, int32_t i, const float* phi, int on_dev
     if (!on_device && (rc = batch_upload(b, phi, N, 0, &src))) return rc;
     unsigned int* bad = (unsigned int*)b->result;   // scratch word
     CK(cudaMemsetAsync(bad, 0, sizeof(unsigned int), b->stream));
-    DISPATCH_STO(b->storage, k_phi<S_><<<(unsigned)((N + 255) / 256), 256, 0, b->stream>>>(
-                                 src, (PP<S_>*)(b->pool + b->desc[i].off_phi), N, bad));
+    DISPATCH_STO(b->storage, k_phi<S_><<<phi_blocks(N), 256, 0, b->stream>>>(
+                                 src, (PP<S_>*)(b->pool + b->desc[i].off_phi), N, aligned16(src), bad));
     CK(cudaGetLastError());
     unsigned int nb = 0;
     CK(cudaMemcpyAsync(&nb, bad, sizeof(nb), cudaMemcpyDeviceToHost, b->stream));

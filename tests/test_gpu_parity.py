@@ -405,6 +405,47 @@ def test_async_porosity_upload(lbm):
         s.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_porosity_range_count_ragged(lbm, storage):
+    """The porosity kernels read four values at a time and the ragged tail one at a time:
+    values outside (0, 1] in either part are all counted (asynchronous upload; synchronous
+    upload from host memory and from a device pointer that is not 16-byte aligned), and the
+    field a step then sees is the one uploaded."""
+    import torch
+
+    p = lbm.lbm_params_default(nr=5, nz=7, storage=storage)   # 35 values: 8 groups of 4 + 3
+    f = np.full((5, 7), 0.5, np.float32)
+    f[0, 1] = 0.0          # in a group of four
+    f[4, 5] = 2.0          # in the tail
+    f[4, 6] = -1.0         # in the tail
+    e = lbm.Solver(p)
+    pin = torch.from_numpy(f).pin_memory()
+    lbm.lbm_set_porosity_async(e.h, pin.data_ptr())
+    assert lbm.lbm_porosity_errors(e.h) == 3
+    with pytest.raises(RuntimeError, match="3 porosity values"):
+        e.set_porosity(f)
+    dev = torch.full((36,), 0.5, dtype=torch.float32, device="cuda")
+    dev[1:] = torch.from_numpy(f.ravel()).cuda()
+    torch.cuda.synchronize()
+    assert dev[1:].data_ptr() % 16 != 0
+    with pytest.raises(RuntimeError, match="3 porosity values"):
+        e.set_porosity(dev[1:])
+    good = np.linspace(0.31, 0.89, 35, dtype=np.float32).reshape(5, 7)
+    dev[1:] = torch.from_numpy(good.ravel()).cuda()
+    torch.cuda.synchronize()
+    e.set_porosity(dev[1:])
+    ref = lbm.Solver(p)
+    ref.set_porosity(good)
+    e.init_fields()
+    ref.init_fields()
+    e.step(20)
+    ref.step(20)
+    for x, y in zip(e.moments(), ref.moments()):
+        assert np.array_equal(x, y)
+    e.close()
+    ref.close()
+
+
 @pytest.mark.parametrize("pinned", [False, True])
 @pytest.mark.parametrize("geom", [0, 2])
 def test_nusselt_async(lbm, geom, pinned):
