@@ -97,12 +97,14 @@ typedef struct lbm_params {
     double body_accel_z;     /* z component of the external acceleration a of Eq. 7 */
     double init_noise;       /* cold start: T = T0 + init_noise * U(-1, 1) on non-wall nodes */
     uint64_t seed;           /* SplitMix64 seed of that noise (draw number kr*nz + kz) */
-    double u_in;             /* LBM_PIPE_INFLOW: inlet velocity U_in (Re = r_i U_in / nu, Sec. 4.1) */
+    double u_in;             /* LBM_PIPE_INFLOW: inlet velocity U_in (Re = r_i U_in / nu, Sec. 4.1),
+                                0 <= u_in < 1/2 (lattice units; a low-Mach model wants u_in << c_s) */
     double heater_len;       /* annulus geometries: > 0 puts an isoflux discrete heater of length
                                 heater_len * H on the inner wall (Sec. 4.4, Fig. 7) with
                                 q' L / k = T_hot - T_cold, insulates the rest of the inner wall
                                 and sets T0 = T_cold; 0: inner wall held at T_hot */
-    double heater_center;    /* heater centre h / H (node kz is heated when |kz - h H| <= l H / 2) */
+    double heater_center;    /* heater centre h / H in [0, 1] (node kz is heated when
+                                |kz - h H| <= l H / 2); heater_len <= 1 */
     int32_t collision;       /* LBM_MRT (Eq. 21 with the rates of Sec. 4) or LBM_BGK (every rate
                                 1/tau_nu: the BGK limit of Sec. 3.1) */
     int32_t reserved;        /* 0 */

@@ -838,7 +838,12 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
         if (p->geometry != LBM_ANNULUS && p->geometry != LBM_ANNULUS_PERIODIC_Z)
             return fail(LBM_ERR_INVALID, "the discrete heater needs an annulus geometry");
         if (p->nr < 4) return fail(LBM_ERR_INVALID, "the discrete heater needs nr >= 4");
+        if (!(p->heater_len <= 1)) return fail(LBM_ERR_INVALID, "heater_len %g exceeds 1 (l / H)", p->heater_len);
+        if (!(p->heater_center >= 0 && p->heater_center <= 1))
+            return fail(LBM_ERR_INVALID, "heater_center %g outside [0, 1] (h / H)", p->heater_center);
     }
+    if (p->geometry == LBM_PIPE_INFLOW && !(p->u_in >= 0 && p->u_in < 0.5))
+        return fail(LBM_ERR_INVALID, "u_in = %g: the inlet velocity must lie in [0, 1/2)", p->u_in);
     o->T0 = p->heater_len > 0 ? p->T_cold : 0.5 * (p->T_hot + p->T_cold);   // Sec. 4.4: T0 = T_o
     o->Kbar = p->Da * o->L * o->L;
     const int64_t N = (int64_t)p->nr * p->nz;

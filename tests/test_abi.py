@@ -43,7 +43,8 @@ def _oracle_params(oracle, p):
     return oracle.params(nr=p.nr, nz=p.nz, geometry=p.geometry, radius_ratio=p.radius_ratio, Ra=p.Ra, Da=p.Da,
                          Pr=p.Pr, J=p.J, lam=p.lam, Ma=p.Ma, tau_nu=p.tau_nu, F_eps=p.F_eps, eps_mean=p.eps_mean,
                          T_hot=p.T_hot, T_cold=p.T_cold, body_accel_z=p.body_accel_z, init_noise=p.init_noise,
-                         seed=p.seed)
+                         seed=p.seed, u_in=p.u_in, heater_len=p.heater_len, heater_center=p.heater_center,
+                         collision=p.collision)
 
 
 @pytest.mark.parametrize("kw", [
@@ -52,6 +53,10 @@ def _oracle_params(oracle, p):
     dict(nr=8192, nz=8192, Ra=1e7, Da=1e-6, Pr=0.71, tau_nu=0.51, eps_mean=0.4, storage="f16"),
     dict(nr=33, nz=4, geometry=2, Ra=0.0, tau_nu=0.8, Da=0.0625, F_eps=0.0, eps_mean=1.0, body_accel_z=1e-5),
     dict(nr=100, nz=200, Ra=1e5, Pr=0.7, Da=1e8, eps_mean=1.0, F_eps=0.0),
+    dict(nr=41, nz=648, geometry=3, Ra=0.0, tau_nu=0.5096, Da=1e-3, eps_mean=1.0, F_eps=0.0, Pr=0.7, u_in=0.0079),
+    dict(nr=200, nz=200, Ra=1e7, Da=1e-4, Pr=0.7, eps_mean=0.9, F_eps=0.0, T_hot=11.0, T_cold=1.0,
+         heater_len=0.4, heater_center=0.5),
+    dict(nr=37, nz=300, Ra=3e4, Da=1e-3, Pr=0.71, radius_ratio=3.0, collision=1),
 ])
 def test_derivation_matches_oracle(lbm, oracle, kw):
     p = lbm.lbm_params_default(**kw)
@@ -68,7 +73,9 @@ def test_derivation_matches_oracle(lbm, oracle, kw):
 @pytest.mark.parametrize("bad", [
     dict(nr=2), dict(nz=1), dict(tau_nu=0.5), dict(radius_ratio=1.0), dict(eps_mean=0.0), dict(eps_mean=1.5),
     dict(geometry=7), dict(storage=5), dict(Ra=0.0, tau_nu=0.0), dict(Pr=0.0), dict(T_hot=0.0, T_cold=0.0),
-    dict(nr=70000),
+    dict(nr=70000), dict(collision=2), dict(heater_len=1.5), dict(heater_len=0.4, heater_center=1.2),
+    dict(heater_len=0.4, geometry=2, Ra=0.0, tau_nu=0.8), dict(geometry=3, Ra=0.0, tau_nu=0.8, u_in=-0.01),
+    dict(geometry=3, Ra=0.0, tau_nu=0.8, u_in=0.6),
 ])
 def test_invalid_parameters_rejected(lbm, bad):
     p = lbm.lbm_params_default(**bad)
