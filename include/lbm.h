@@ -141,7 +141,8 @@ int lbm_derive(const lbm_params *p, lbm_info *out);
 int lbm_create(const lbm_params *p, lbm_handle **out);
 
 /* Queue all further device work of h on `stream` (a cudaStream_t, e.g. from
- * torch.cuda.Stream.cuda_stream); NULL = the legacy default stream. */
+ * torch.cuda.Stream.cuda_stream); NULL = the legacy default stream.  Work queued on the
+ * new stream starts after the work already queued on the old one. */
 int lbm_set_stream(lbm_handle *h, void *stream);
 
 /* Replace the porosity field by phi[nr*nz] (each value in (0, 1]).  Takes effect

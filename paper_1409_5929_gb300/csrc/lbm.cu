@@ -1102,7 +1102,17 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
 
 int lbm_set_stream(lbm_handle* h, void* stream) {
     if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
-    h->stream = (cudaStream_t)stream;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (s == h->stream) return LBM_OK;
+    CK(cudaSetDevice(h->device));
+    // the new stream starts after everything already queued on the old one
+    cudaEvent_t e = nullptr;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t err = cudaEventRecord(e, h->stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e, 0);
+    cudaEventDestroy(e);   // released once the recorded work has completed
+    if (err != cudaSuccess) return fail(LBM_ERR_CUDA, "lbm_set_stream: %s", cudaGetErrorString(err));
+    h->stream = s;
     return LBM_OK;
 }
 
