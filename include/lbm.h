@@ -192,8 +192,7 @@ int lbm_nusselt(lbm_handle *h, double *nu_inner, double *nu_outer);
 /* lbm_nusselt without the synchronisation: enqueues the reduction of the current state
  * and the transfer of (Nu_inner, Nu_outer) into out[0..1] (host memory) on the handle's
  * stream and returns.  Pinned (page-locked, mapped) memory is written by the device
- * directly, so the transfer does not queue behind a porosity upload in flight; other host
- * memory takes an ordinary copy.  out must stay allocated until the values are there,
+ * directly; other host memory takes an ordinary copy.  out must stay allocated until the values are there,
  * after the next synchronising call (lbm_sync).  NaN entries as for lbm_nusselt. */
 int lbm_nusselt_async(lbm_handle *h, double *out);
 

@@ -464,8 +464,8 @@ __global__ void k_phi(const float* __restrict__ src, typename St<STO>::P* __rest
     if (cnt) atomicAdd(bad, cnt);
 }
 
-// Two result values into mapped host memory, written by the kernel itself: a 16-byte
-// device-to-host copy would queue behind a host-to-device upload in flight.
+// Two result values written into mapped host memory by the kernel itself (no copy-engine
+// transfer for 16 bytes).
 __global__ void k_put2(const double* __restrict__ src, double* dst, int skip_first) {
     const int i = threadIdx.x;
     if (i < 2 && !(skip_first && i == 0)) dst[i] = src[i];
