@@ -267,6 +267,73 @@ def test_heater_conduction_limit(oracle):
     assert err[1] < 3e-3 and err[0] / err[1] > 3.0, err
 
 
+def _conduction_fd(nr, nz, r0, G, To, lH, hH):
+    """Second-order finite differences for steady axisymmetric conduction,
+    (1/r) d/dr (r dT/dr) + d2T/dz2 = 0 on the node grid (h = 1), with the boundary
+    conditions of the discrete-heater annulus read the same way as in reading 19: outer
+    wall T = T_o (corners included); inner wall -dT/dr = G on the heated nodes
+    |kz - hH H| <= lH H / 2 and 0 elsewhere, one-sided second order; inner corners take the
+    diagonal neighbour; top and bottom take the next node inward.  Independent of the
+    oracle (a sparse direct solve)."""
+    from scipy.sparse import lil_matrix
+    from scipy.sparse.linalg import spsolve
+
+    H, n = nz - 1, nr * nz
+    A, b = lil_matrix((n, n)), np.zeros(n)
+    for i in range(nr):
+        for j in range(nz):
+            k = i * nz + j
+            if i == nr - 1:
+                A[k, k], b[k] = 1, To
+            elif i == 0 and j in (0, nz - 1):
+                A[k, k], A[k, nz + (1 if j == 0 else nz - 2)] = 1, -1
+            elif i == 0:
+                A[k, k], A[k, nz + j], A[k, 2 * nz + j] = 3, -4, 1
+                b[k] = 2 * G if abs(j - hH * H) <= lH * H / 2 else 0.0
+            elif j in (0, nz - 1):
+                A[k, k], A[k, i * nz + (1 if j == 0 else nz - 2)] = 1, -1
+            else:
+                r = r0 + i
+                A[k, k + nz], A[k, k - nz], A[k, k + 1], A[k, k - 1], A[k, k] = r + 0.5, r - 0.5, r, r, -4 * r
+    return spsolve(A.tocsr(), b).reshape(nr, nz)
+
+
+def test_heater_partial_segment_conduction(oracle):
+    """Closed annulus (A = 1, R* = 2) with no buoyancy and the heater of Sec. 4.4 (l/H = 0.4,
+    q' L / k = 10, T_o = 1): the steady temperature is mirror-symmetric about the heater's
+    centre h/H = 0.5 to round-off, and it approaches the independent finite-difference
+    solution of the same conduction problem as the grid is refined (the wall and corner
+    closures are first order: max |dT| / (T_max - T_o) 5.3 % -> 3.1 %, mean heater Nu of
+    Eq. 43-44 5.2 % -> 3.1 %, at nr = 21 -> 41).  An off-centre heater (h/H = 0.3): 6.5 % ->
+    3.3 % and 5.8 % -> 3.2 %."""
+    diffs = {}
+    for hH in (0.5, 0.3):
+        for nr in (21, 41):
+            p = oracle.params(nr=nr, nz=nr, radius_ratio=2.0, Ra=0.0, tau_nu=1.0, Pr=1.0, Da=1e8, eps_mean=1.0,
+                              F_eps=0.0, T_hot=11.0, T_cold=1.0, heater_len=0.4, heater_center=hH, init_noise=0.0)
+            st = oracle.State(p)
+            prev = None
+            for _ in range(100):
+                st.run(2000, THREADS)
+                T = st.moments()[3]
+                if prev is not None and np.abs(T - prev).max() < 1e-11:
+                    break
+                prev = T
+            Tfd = _conduction_fd(nr, nr, oracle.derive(p)["r0"], 10.0 / (nr - 1), 1.0, 0.4, hH)
+            m, nu_z = st.heater_nusselt()
+            heated = ~np.isnan(nu_z)
+            assert heated.sum() == sum(abs(j - hH * (nr - 1)) <= 0.2 * (nr - 1) for j in range(1, nr - 1))
+            m_fd = np.mean(10.0 / (Tfd[0, heated] - 1.0))
+            diffs[hH, nr] = (np.abs(T - Tfd).max() / (Tfd.max() - 1.0), abs(m / m_fd - 1))
+            if hH == 0.5:
+                assert np.abs(T - T[:, ::-1]).max() < 1e-10
+    print("heater conduction vs FD", diffs)
+    for hH in (0.5, 0.3):
+        coarse, fine = diffs[hH, 21], diffs[hH, 41]
+        assert fine[0] < 0.04 and fine[1] < 0.04, diffs
+        assert fine[0] < 0.7 * coarse[0] and fine[1] < 0.7 * coarse[1], diffs
+
+
 def test_heater_heat_balance(oracle):
     """Closed porous annulus (A = 1, R* = 2, phi = 0.9, Da = 1e-2, Ra = 1e3) heated by the
     discrete heater of Sec. 4.4 (l / H = 0.4 centred): at steady state the heat leaving
