@@ -5,7 +5,7 @@ import os
 import numpy as np
 import pytest
 from scipy.integrate import solve_bvp
-from scipy.special import i0, k0
+from scipy.special import i0, i1, k0, k1
 
 from paper_1409_5929_gb300 import inputs
 
@@ -81,6 +81,40 @@ def test_brinkman_flow(oracle, geom):
     assert e[0][0] / e[1][0] > 2.5 and e[1][0] / e[2][0] > 3.0
     assert e[2][0] < 5e-3
     assert max(x[1] for x in e) < 1e-5     # no radial flow beyond round-off-level truncation
+
+
+def _brinkman_psi(oracle, geom, nr):
+    """Relative max error of the oracle's stream function of its own steady Brinkman flow
+    against the integral of the analytic profile, psi(r) = int r' u_z dr' (from the axis in
+    the pipe, from the inner wall in the annulus), with int r I0(r/l) dr = l r I1(r/l) and
+    int r K0(r/l) dr = -l r K1(r/l)."""
+    a = 1e-5
+    p = oracle.params(nr=nr, nz=4, geometry=geom, Ra=0.0, tau_nu=0.8, Da=0.0625, F_eps=0.0,
+                      eps_mean=1.0, body_accel_z=a)
+    c = oracle.derive(p)
+    st, (rho, ur, uz, T) = _run(oracle, p, int(3 * (nr - 1) ** 2 / c["nu_e"]))
+    psi, m = st.stream_function()
+    r = c["r0"] + np.arange(nr)
+    ell = np.sqrt(c["nu_e"] * c["Kbar"] / c["nu"])
+    C = a * c["Kbar"] / c["nu"]
+    if geom == 2:
+        exact = C * (r ** 2 / 2 - ell * r * i1(r / ell) / i0(r[-1] / ell))
+    else:
+        A = np.array([[i0(r[0] / ell), k0(r[0] / ell)], [i0(r[-1] / ell), k0(r[-1] / ell)]])
+        cA, cB = np.linalg.solve(A, [-1.0, -1.0])
+        F = lambda x: x ** 2 / 2 + cA * ell * x * i1(x / ell) - cB * ell * x * k1(x / ell)
+        exact = C * (F(r) - F(r[0]))
+    assert np.allclose(psi, psi[:, :1], rtol=1e-9, atol=1e-15)    # uniform along the periodic z
+    return np.abs(psi[:, 1] - exact).max() / np.abs(exact).max()
+
+
+@pytest.mark.parametrize("geom", [1, 2])
+def test_brinkman_stream_function(oracle, geom):
+    """The stream function of the steady Brinkman flows above (annulus and pipe) converges
+    at second order to the integral of their analytic profiles."""
+    e = [_brinkman_psi(oracle, geom, nr) for nr in (9, 17, 33)]
+    print("Brinkman psi errors", geom, e)
+    assert e[0] / e[1] > 2.5 and e[1] / e[2] > 3.0 and e[2] < 5e-3
 
 
 def _axial_poiseuille(oracle, phi, nr, a=1e-6):
