@@ -35,11 +35,12 @@ WORKLOAD = dict(nr=NR, nz=NZ, radius_ratio=2.0, Ra=1e6, Da=1e-4, Pr=0.71, F_eps=
 PHI_RECIPE = dict(lo=0.3, hi=0.9, sigma=16.0, seed=2)
 METRIC = "MLUPS & % HBM roofline; time-to-steady vs plain FP32 GPU at |ΔNu|≤1e-3"
 SAMPLE_NR, SAMPLE_NZ = 256, 512   # bounded CPU sample: the same recipe on a 256 x 512 annulus
+E2E_STEPS = 50                    # minimum length of the end-to-end window (steps)
 
 
 # DRAM traffic of one k_bulk launch on the 4096 x 8192 workload (dram__bytes_read.sum +
-# dram__bytes_write.sum, one single-pass ncu capture; profiles/k_bulk_f32_4096x8192_traffic.md),
-# valid only for the bulk kernel's source it was taken on (_kernel_hash).
+# dram__bytes_write.sum of the bulk kernel in one single-pass ncu capture of this
+# benchmark), valid only for the bulk kernel's source it was taken on (_kernel_hash).
 TRAFFIC = {("f32", 4096, 8192): ("c46d47cafaadd9a6", 2.09e9 + 1.83e9)}
 
 
@@ -150,6 +151,62 @@ def aggregate(local_ms: float, local_units: float, device=None) -> tuple[float, 
     return units / (ms * 1e-3), ms
 
 
+def _time_steps(lbm, s, stream, steps):
+    """Device time of `steps` steps on the solver's stream (CUDA events around the loop and
+    around every bulk and wall launch), with nvidia-smi clock samples taken meanwhile."""
+    import torch
+
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    lbm.lbm_set_timing(s.h, True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    bulk_ms, bulk_n, wall_ms, wall_n = lbm.lbm_kernel_times(s.h)
+    lbm.lbm_set_timing(s.h, False)
+    return ms, bulk_ms / max(bulk_n, 1), wall_ms / max(wall_n, 1), clocks.stop()
+
+
+def _solver(lbm, storage, phi, stream):
+    p = lbm.lbm_params_default(storage=storage, eps_mean=float(phi.mean(dtype=np.float64)), **WORKLOAD)
+    s = lbm.Solver(p)
+    s.set_stream(stream.cuda_stream)
+    s.set_porosity(phi)
+    s.init_fields()
+    return s
+
+
+def _bulk_bytes(info):
+    """Algorithmic bytes of one bulk launch: every non-wall node reads and writes its
+    populations and reads its porosity (and the reference planes its storage type
+    keeps); bytes per node as the library states them for the storage type."""
+    return (NR - 2) * (NZ - 2) * (info.bytes_per_step // (NR * NZ))
+
+
+def storage_variant(lbm, storage, phi, steps, warmup, peak):
+    """Single-domain line for another storage type: MLUPS, the bulk kernel's roofline
+    fraction on its own bytes per node, and each kernel's mean launch time."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    s = _solver(lbm, storage, phi, stream)
+    s.step(warmup)
+    ms, bulk_avg, wall_avg, ck = _time_steps(lbm, s, stream, steps)
+    info = s.info()
+    s.close()
+    achieved = _bulk_bytes(info) / (bulk_avg * 1e-3) / 1e9
+    return {"value": round(NR * NZ * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+            "ms_per_step": round(ms / steps, 5), "bytes_per_node": info.bytes_per_step // (NR * NZ),
+            "bulk_avg_ms": round(bulk_avg, 5), "wall_avg_ms": round(wall_avg, 5),
+            "achieved_gbs": round(achieved, 1), "frac": round(achieved / peak, 4), "clocks": ck}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -158,48 +215,29 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     phi = inputs.porosity_field(NR, NZ, PHI_RECIPE["lo"], PHI_RECIPE["hi"], PHI_RECIPE["sigma"], PHI_RECIPE["seed"])
-    p = lbm.lbm_params_default(storage=args.storage, eps_mean=float(phi.mean(dtype=np.float64)), **WORKLOAD)
-    s = lbm.Solver(p)
     stream = torch.cuda.Stream()
-    s.set_stream(stream.cuda_stream)
-    s.set_porosity(phi)
-    s.init_fields()
+    s = _solver(lbm, args.storage, phi, stream)
     info = s.info()
     nodes = NR * NZ
-    interior = (NR - 2) * (NZ - 2)
-    ef = 4 if args.storage == "f32" else 2          # flow populations; temperature populations are FP32
-    # algorithmic bytes of one bulk launch: 14 populations read and written, the porosity
-    # and (FP32 storage) the FP16 temperature reference read
-    bulk_bytes = interior * (2 * (9 * ef + 5 * 4) + ef + (2 if args.storage == "f32" else 0))
+    bulk_bytes = _bulk_bytes(info)
 
     s.step(args.warmup)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = Clocks(local_rank)
-    clocks.start()
-    lbm.lbm_set_timing(s.h, True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
+    ms, bulk_avg, wall_avg, ck = _time_steps(lbm, s, stream, args.steps)
     if world > 1:
         dist.barrier()
-    e0.record(stream)
-    s.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    bulk_ms, bulk_n, wall_ms, wall_n = lbm.lbm_kernel_times(s.h)
-    lbm.lbm_set_timing(s.h, False)
-    ck = clocks.stop()
     ups, ms_max = aggregate(ms, float(nodes) * args.steps, device="cuda")
     value = ups / 1e6
 
     # end to end through the C ABI with host buffers: every step uploads its porosity field
     # from pinned host memory (the upload of step n + 1's input runs on the handle's copy
     # stream while step n computes) and copies its two Nusselt numbers back to pinned host
-    # memory; the host waits once, at the end of the timed region, and checks every result
-    ke = max(3, min(args.steps // 10, 50))
+    # memory; the host waits once, at the end of the timed region, and checks every result.
+    # The window is E2E_STEPS steps whatever --steps is, so that the first upload, which
+    # nothing overlaps, does not dominate it.
+    ke = max(E2E_STEPS, args.steps)
     phi_pinned = torch.from_numpy(phi).pin_memory()
     nus = torch.full((ke, 2), float("nan"), dtype=torch.float64).pin_memory()
     lbm.lbm_porosity_errors(s.h)
@@ -225,7 +263,6 @@ def run_ours(args, rank, world, local_rank):
         return None
 
     peak, peak_kind = _peaks()
-    bulk_avg = bulk_ms / max(bulk_n, 1)
     achieved = bulk_bytes / (bulk_avg * 1e-3) / 1e9
     line = {
         "metric": METRIC,
@@ -248,12 +285,15 @@ def run_ours(args, rank, world, local_rank):
                      "frac": round(achieved / peak, 4), "traffic": _traffic(args.storage),
                      "kernel": f"k_bulk<{args.storage}>", "peak_source": f"{peak_kind} hbm_gbs",
                      "avg_launch_ms": round(bulk_avg, 5), "bytes_per_launch": bulk_bytes,
-                     "wall_kernel_avg_ms": round(wall_ms / max(wall_n, 1), 5)},
+                     "wall_kernel_avg_ms": round(wall_avg, 5)},
         "e2e": {"value": round(e2e_val, 2), "unit": "MLUPS", "h2d_bytes_per_step": nodes * 4,
                 "d2h_bytes_per_step": 16, "steps": ke, "nusselt": list(nu) if nu else None},
         "gpu_launches": 2 * args.steps,
         "clocks": ck,
     }
+    if world == 1 and not args.no_extras:
+        line["storage_variants"] = {sto: storage_variant(lbm, sto, phi, args.steps, args.warmup, peak)
+                                    for sto in ("f32", "f16", "bf16") if sto != args.storage}
     return line
 
 
@@ -336,9 +376,7 @@ def time_to_steady(max_steps: int = 300000, check: int = 1000, tol: float = 1e-8
     return out
 
 
-def cpu_sample(seconds: float):
-    """The oracle as it stands on a bounded sample: the same recipe on a 256 x 512
-    annulus, all host cores, timed for about `seconds`."""
+def _oracle_sample_state():
     from oracle import oracle as O
 
     from paper_1409_5929_gb300 import inputs
@@ -348,17 +386,30 @@ def cpu_sample(seconds: float):
                                 PHI_RECIPE["seed"])
     p = O.params(nr=SAMPLE_NR, nz=SAMPLE_NZ, radius_ratio=2.0, Ra=1e6, Da=1e-4, Pr=0.71, F_eps=-1.0,
                  eps_mean=float(phi.mean(dtype=np.float64)))
-    st = O.State(p, phi=phi.astype(np.float64))
-    cores = os.cpu_count() or 1
-    st.run(2, cores)
+    return O.State(p, phi=phi.astype(np.float64))
+
+
+def _oracle_mlups(threads: int, seconds: float):
+    st = _oracle_sample_state()
+    st.run(2, threads)
     steps, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
-        st.run(10, cores)
-        steps += 10
+        st.run(5 if threads == 1 else 10, threads)
+        steps += 5 if threads == 1 else 10
     dt = time.perf_counter() - t0
-    mlups = SAMPLE_NR * SAMPLE_NZ * steps / dt / 1e6
-    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, same recipe on a {SAMPLE_NR}x{SAMPLE_NZ} annulus, {steps} steps, {dt:.1f} s"}
+    return SAMPLE_NR * SAMPLE_NZ * steps / dt / 1e6, steps, dt
+
+
+def cpu_sample(seconds: float):
+    """The oracle as it stands on a bounded sample: the same recipe on a 256 x 512
+    annulus, on all host cores for about `seconds` and on one core for about half that."""
+    cores = os.cpu_count() or 1
+    v, steps, dt = _oracle_mlups(cores, seconds)
+    v1, steps1, dt1 = _oracle_mlups(1, 0.5 * seconds)
+    return {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, same recipe on a {SAMPLE_NR}x{SAMPLE_NZ} annulus, {steps} steps, {dt:.1f} s",
+            "single_thread": {"value": round(v1, 3), "unit": "MLUPS", "cores": 1,
+                              "sample": f"same, one thread, {steps1} steps, {dt1:.1f} s"}}
 
 
 def run_reference(args):
@@ -435,7 +486,7 @@ def main():
         line["sweep"] = sweep_throughput(100)
         line["time_to_steady"] = time_to_steady()
     if rank == 0:
-        line["cpu_baseline"] = cpu_sample(args.cpu_seconds) if world == 1 else None
+        line["cpu_baseline"] = cpu_sample(args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -66,9 +66,26 @@ int fno_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, 
  * the accumulator in tensor memory (persistent CTAs, 128 x N tiles with N <= 256 chosen
  * so that there are four tiles per SM, two stage buffers).  Process-wide. */
 int fno_set_tensor_path(int path);
-/* 1 if a tcgen05 GEMM gave up a bounded wait since the last clear (its output is then
- * invalid), 0 otherwise, -1 on a CUDA error; clear = 1 resets the flag.  Synchronous. */
+/* Status of the tcgen05 path, synchronous:
+ *   0  no bounded wait ran out since the last clear;
+ *   1  a tcgen05 GEMM gave up a wait (its output is invalid), then saw every MMA it had
+ *      issued complete before freeing its tensor memory: later GEMMs are unaffected;
+ *   2  a recovery wait ran out as well, so tensor memory may have been freed under an
+ *      MMA still in flight and a later GEMM could compute a wrong result unnoticed.
+ *      From the first call that reads 2, the tcgen05 path is off for the rest of the
+ *      process: fno_gemm runs on mma.sync, fno_set_tensor_path(1) fails, and this call
+ *      keeps returning 2;
+ *  -1  CUDA error.  clear = 1 resets the device flag (not the process-wide state of 2). */
 int fno_tensor_path_status(int clear);
+
+/* Test hooks for the failure path (no counterpart in the paper).
+ * fno_test_wait_timeout(1): the next tcgen05 GEMM CTAs replace their first wait for an
+ * MMA commit by a short bounded wait on a barrier that nothing arrives at, so the timeout
+ * path runs (each CTA then waits for its real commits before freeing tensor memory);
+ * 0 restores normal waits.  fno_test_set_tc_error(v) writes v in {0, 1, 2} into the
+ * device flag read by fno_tensor_path_status, to exercise the host's handling of it. */
+int fno_test_wait_timeout(int enable);
+int fno_test_set_tc_error(int value);
 
 const char *fno_last_error(void);
 

@@ -287,17 +287,24 @@ int lbm_kernel_times(lbm_handle *h, double *bulk_ms, int64_t *bulk_launches, dou
  *   cur:  device floats, 4 planes of nr*nz at stride field_stride: rho, u_r, u_z, T
  *         of state n (the layout lbm_moments writes when given plane pointers);
  *   prev: the same 4 planes of state n - 1 (its rho plane is not read);
+ *   each must point into device (or managed) memory of the current device whose
+ *   allocation holds 3*field_stride + nr*nz floats from the pointer on; a host pointer,
+ *   another device's memory or a shorter allocation is rejected with LBM_ERR_INVALID
+ *   before anything is launched (cudaPointerGetAttributes and the driver's
+ *   cuMemGetAddressRange, neither of which allocates; the extent check is skipped if
+ *   the driver does not offer that call);
  *   geometry, nr, nz: as in lbm_params; r0 = r(kr = 0) (lbm_info.r0);
  *   *res, *mass: host doubles receiving the residual and sum of r * rho (FP64).
  * It calls no cudaMalloc, cudaFree or other allocating routine: the reduction's
  * partial sums live in a file-scope static device array of 1025 x 6 doubles (49 KB),
- * held by every GPU that loads the library until the process exits.  The first call
- * on a device looks up that array's address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  All calls share the
- * array and each overwrites it: calls that overlap on the GPU (other streams, other
- * threads) race.  Limits: 3 <= nr, nz <= 65535 and nr*nz < 2^31 (LBM_ERR_INVALID
- * beyond), current device index < 64.  Work runs on `stream` (NULL = legacy default)
- * and the call synchronises it.  LBM_ERR_DIVERGED if cur holds NaN or Inf. */
+ * held by every GPU that loads the library until the process exits.  Every call looks
+ * up that array's address in the current device's context (cudaGetSymbolAddress); the
+ * first call on a device may also load the library's device code there, so make that
+ * first call before any stream capture.  All calls share the array and each overwrites
+ * it: calls that overlap on the GPU (other streams, other threads) race.  Limits:
+ * 3 <= nr, nz <= 65535 and nr*nz < 2^31, nr*nz <= field_stride <= 2^40 (LBM_ERR_INVALID
+ * beyond).  Work runs on `stream` (NULL = legacy default) and the call synchronises it.
+ * LBM_ERR_DIVERGED if cur holds NaN or Inf. */
 int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t nz, double r0, const float *cur,
                                const float *prev, int64_t field_stride, double *res, double *mass,
                                void *stream);

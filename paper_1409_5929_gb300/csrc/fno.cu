@@ -146,11 +146,17 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, float alpha, 
 // tcgen05.mma (K = 16 each) on the current one run.  Each buffer has an mbarrier that
 // tcgen05.commit arrives on.  After a tile's last chunk each warp reads its 32
 // accumulator lanes back with tcgen05.ld and writes C (16-byte stores where aligned).
-// Every wait is bounded: on timeout the kernel records an error, stops issuing work,
-// waits once more (bounded) for each committed buffer, frees its tensor memory and
-// returns.
+// Every wait is bounded: on timeout the kernel stops issuing work, waits once more
+// (bounded) for each buffer whose commit it has not seen complete, records an error
+// (1: those waits completed, so no MMA was outstanding when the tensor memory was
+// freed; 2: one of them ran out too), frees its tensor memory and returns.
 constexpr int TC_BM = 128, TC_BK = 64;
+constexpr int TC_SPIN = 1 << 22;        // try_wait rounds of a normal wait
+constexpr int TC_TEST_SPIN = 1 << 12;   // rounds of the test wait (fno_test_wait_timeout)
 __device__ int g_tc_error;
+// Test hook: when set, the main loop's first wait for a commit is replaced by a wait on
+// a barrier nothing arrives at, with a short bound, so that the timeout path runs.
+__device__ int g_tc_wait_test;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -163,8 +169,8 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
            ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
-    for (int i = 0; i < (1 << 22); ++i) {
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase, int spin = TC_SPIN) {
+    for (int i = 0; i < spin; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -248,7 +254,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
                                                  float* __restrict__ C, int64_t ldc, int64_t sC,
                                                  const float* __restrict__ bias, int vecA, int vecB, int vecC) {
     extern __shared__ __align__(1024) uint8_t tc_smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[3];   // two stage buffers; [2] never arrived at (test hook)
     __shared__ uint32_t tmem_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t abytes = TC_BM * BK * 2, stage_bytes = abytes + (uint32_t)ntile * BK * 2;
@@ -264,6 +270,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 16) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -279,6 +286,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
     const int64_t nsteps = my_tiles * nk;
     uint32_t phase_bits = 0, pend_bits = 0;   // per stage buffer: mbarrier phase, commit outstanding
     bool ok = true;
+    bool test_wait = *(volatile int*)&g_tc_wait_test != 0;
     auto step_tile = [&](int64_t st, int& tb, int& tm, int& tn, int& kc) {
         const int64_t t = blockIdx.x + (st / nk) * (int64_t)gridDim.x;
         kc = (int)(st % nk);
@@ -317,13 +325,20 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
         pend_bits |= 1u << buf;
     };
     // wait for the commit on buf, if one is outstanding; every thread reaches each call,
-    // and the block agrees on the outcome (a lone timeout must not split the barriers)
+    // and the block agrees on the outcome (a lone timeout must not split the barriers).
+    // The commit counts as consumed only when every thread saw it complete; otherwise it
+    // stays outstanding for the recovery wait below.
     auto drain = [&](int buf) {
         if (pend_bits & (1u << buf)) {
-            const bool got = tc_wait(mb0 + 8 * buf, (phase_bits >> buf) & 1u);
-            ok = __syncthreads_and(ok && got) != 0;
-            phase_bits ^= 1u << buf;
-            pend_bits &= ~(1u << buf);
+            const bool got = test_wait ? tc_wait(mb0 + 16, 0u, TC_TEST_SPIN)
+                                       : tc_wait(mb0 + 8 * buf, (phase_bits >> buf) & 1u);
+            test_wait = false;
+            const bool all = __syncthreads_and(got) != 0;
+            if (all) {
+                phase_bits ^= 1u << buf;
+                pend_bits &= ~(1u << buf);
+            }
+            ok = ok && all;
         }
     };
     if (nsteps > 0) {
@@ -383,9 +398,13 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
         drain(0);
         drain(1);
     } else {
-        if (tid == 0) atomicExch(&g_tc_error, 1);
-        for (int b = 0; b < 2; ++b)    // one more bounded wait for work already committed
-            if (pend_bits & (1u << b)) tc_wait(mb0 + 8 * b, (phase_bits >> b) & 1u);
+        // one more bounded wait for every commit not yet seen complete, before the tensor
+        // memory is freed; error 2 if one of them runs out as well
+        bool clean = true;
+        for (int b = 0; b < 2; ++b)
+            if (pend_bits & (1u << b)) clean = tc_wait(mb0 + 8 * b, (phase_bits >> b) & 1u) && clean;
+        clean = __syncthreads_and(clean) != 0;
+        if (tid == 0) atomicMax(&g_tc_error, clean ? 1 : 2);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -393,7 +412,8 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
-static int g_tc_path = 0;   // 1: route fno_gemm through the tcgen05 kernel
+static int g_tc_path = 0;          // 1: route fno_gemm through the tcgen05 kernel
+static bool g_tc_poisoned = false; // a recovery wait ran out: the tcgen05 path stays off
 static int g_num_sms = 0;
 
 static bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
@@ -699,6 +719,8 @@ int fno_adam(float* w, const float* g, float* m, float* v, int64_t n, float lr, 
 
 int fno_set_tensor_path(int path) {
     if (path != 0 && path != 1) return fno_fail(FNO_ERR_INVALID, "path must be 0 (mma.sync) or 1 (tcgen05)");
+    if (path == 1 && g_tc_poisoned)
+        return fno_fail(FNO_ERR_CUDA, "the tcgen05 path is disabled for this process (a recovery wait ran out)");
     g_tc_path = path;
     return FNO_OK;
 }
@@ -706,11 +728,29 @@ int fno_set_tensor_path(int path) {
 int fno_tensor_path_status(int clear) {
     int v = 0;
     if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess) return -1;
+    if (v >= 2 && !g_tc_poisoned) {
+        // tensor memory may have been freed under an MMA still in flight: results of
+        // later tcgen05 GEMMs could be wrong without any report, so the path stays off
+        g_tc_poisoned = true;
+        g_tc_path = 0;
+    }
     if (clear) {
         const int z = 0;
         if (cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int)) != cudaSuccess) return -1;
     }
-    return v;
+    return g_tc_poisoned ? 2 : v;
+}
+
+int fno_test_wait_timeout(int enable) {
+    const int v = enable ? 1 : 0;
+    FCK(cudaMemcpyToSymbol(g_tc_wait_test, &v, sizeof(int)));
+    return FNO_OK;
+}
+
+int fno_test_set_tc_error(int value) {
+    if (value < 0 || value > 2) return fno_fail(FNO_ERR_INVALID, "value must be 0, 1 or 2");
+    FCK(cudaMemcpyToSymbol(g_tc_error, &value, sizeof(int)));
+    return FNO_OK;
 }
 
 const char* fno_last_error(void) { return g_fno_err.c_str(); }

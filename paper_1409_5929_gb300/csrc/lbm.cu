@@ -21,6 +21,7 @@
 // Both read only the source buffer and write disjoint nodes of the destination.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -1591,9 +1592,48 @@ const char* lbm_last_error(void) { return g_err.c_str(); }
 constexpr int LBM_NOALLOC_ROWS = 1024;
 static __device__ __align__(256) double g_noalloc_scratch[(LBM_NOALLOC_ROWS + 1) * RES_NV];
 
-constexpr int LBM_NOALLOC_MAX_DEVICES = 64;
-static double* g_noalloc_ptr[LBM_NOALLOC_MAX_DEVICES];
-static std::mutex g_noalloc_mutex;
+// cuMemGetAddressRange of the driver, reached through the runtime's entry-point query so
+// that the library does not link libcuda itself; NULL when the driver does not offer it.
+typedef CUresult (*addr_range_fn)(CUdeviceptr* base, size_t* size, CUdeviceptr ptr);
+static addr_range_fn addr_range() {
+    static std::once_flag once;
+    static addr_range_fn fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (addr_range_fn)f;
+        (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// A field-snapshot pointer must be device (or managed) memory of the current device
+// whose allocation holds `bytes` from ptr on; checked without allocating anything.
+static int check_field_ptr(const char* name, const float* ptr, int dev, size_t bytes) {
+    cudaPointerAttributes at;
+    const cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(LBM_ERR_INVALID, "%s: not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(LBM_ERR_INVALID, "%s: host or unregistered memory; device memory required", name);
+    if (at.type == cudaMemoryTypeDevice && at.device != dev)
+        return fail(LBM_ERR_INVALID, "%s: memory of device %d, current device %d", name, at.device, dev);
+    if (addr_range_fn fn = addr_range()) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (fn(&base, &size, (CUdeviceptr)(uintptr_t)ptr) != CUDA_SUCCESS)
+            return fail(LBM_ERR_INVALID, "%s: address range of the allocation unavailable", name);
+        if ((uintptr_t)ptr + bytes > (uintptr_t)base + size)
+            return fail(LBM_ERR_INVALID, "%s: its allocation ends %zu bytes after it, %zu needed", name,
+                        (size_t)((uintptr_t)base + size - (uintptr_t)ptr), bytes);
+    }
+    return LBM_OK;
+}
 
 extern "C" int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t nz, double r0, const float* cur,
                                           const float* prev, int64_t field_stride, double* res, double* mass,
@@ -1603,21 +1643,18 @@ extern "C" int lbm_field_residual_noalloc(int32_t geometry, int32_t nr, int32_t 
     if (nr < 3 || nz < 3 || nr > 65535 || nz > 65535 || (int64_t)nr * nz >= ((int64_t)1 << 31))
         return fail(LBM_ERR_INVALID, "grid %d x %d outside 3..65535 per side with nr*nz < 2^31", nr, nz);
     const int64_t N = (int64_t)nr * nz;
-    if (field_stride < N) return fail(LBM_ERR_INVALID, "field_stride %lld < nr*nz", (long long)field_stride);
+    if (field_stride < N || field_stride > ((int64_t)1 << 40))
+        return fail(LBM_ERR_INVALID, "field_stride %lld outside [nr*nz, 2^40]", (long long)field_stride);
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= LBM_NOALLOC_MAX_DEVICES)
-        return fail(LBM_ERR_INVALID, "device %d beyond the %d supported", dev, LBM_NOALLOC_MAX_DEVICES);
-    double* scratch;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
-            void* p = nullptr;
-            CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-            g_noalloc_ptr[dev] = (double*)p;
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
+    // both snapshots are read over their four planes: 3 * field_stride + nr * nz floats
+    const size_t need = (size_t)(3 * field_stride + N) * sizeof(float);
+    if (int rc = check_field_ptr("cur", cur, dev, need)) return rc;
+    if (int rc = check_field_ptr("prev", prev, dev, need)) return rc;
+    // the array's address in the current device's context, looked up on every call (a
+    // lookup allocates nothing; an address kept from an earlier context could be stale)
+    double* scratch = nullptr;
+    CK(cudaGetSymbolAddress((void**)&scratch, g_noalloc_scratch));
     cudaStream_t s = (cudaStream_t)stream;
     const int blocks = (int)std::min<int64_t>(LBM_NOALLOC_ROWS, (N + 255) / 256);
     double* result = scratch + LBM_NOALLOC_ROWS * RES_NV;

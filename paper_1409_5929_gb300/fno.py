@@ -42,6 +42,8 @@ _SIGS = {
     "fno_adam": [_vp, _vp, _vp, _vp, _i64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, _vp],
     "fno_set_tensor_path": [C.c_int],
     "fno_tensor_path_status": [C.c_int],
+    "fno_test_wait_timeout": [C.c_int],
+    "fno_test_set_tc_error": [C.c_int],
 }
 
 
@@ -124,6 +126,17 @@ def fno_set_tensor_path(path: int):
 
 def fno_tensor_path_status(clear: bool = True) -> int:
     return int(load().fno_tensor_path_status(int(clear)))
+
+
+def fno_test_wait_timeout(enable: bool):
+    """Test hook: tcgen05 GEMM CTAs replace their first commit wait by a short wait that
+    runs out (see include/fno.h)."""
+    _check(load().fno_test_wait_timeout(int(enable)))
+
+
+def fno_test_set_tc_error(value: int):
+    """Test hook: write the device error flag that fno_tensor_path_status reads."""
+    _check(load().fno_test_set_tc_error(int(value)))
 
 
 # ---- the operator -------------------------------------------------------------

@@ -276,12 +276,22 @@ def lbm_kernel_times(h):
     return a.value, b.value, c.value, d.value
 
 
+def _device_ptr(a, name):
+    """Address of a CUDA tensor, or an int taken as a device address (checked by the library)."""
+    if isinstance(a, int):
+        return a
+    if getattr(a, "is_cuda", False):
+        return a.data_ptr()
+    raise TypeError(f"{name}: a CUDA tensor or a device address is required")
+
+
 def lbm_field_residual_noalloc(geometry: int, nr: int, nz: int, r0: float, cur, prev, field_stride: int,
                                stream=None):
     """Residual and mass from device field snapshots without any device allocation."""
     a, b = C.c_double(), C.c_double()
-    _check(load().lbm_field_residual_noalloc(int(geometry), int(nr), int(nz), float(r0), _ptr(cur), _ptr(prev),
-                                             int(field_stride), C.byref(a), C.byref(b), stream))
+    _check(load().lbm_field_residual_noalloc(int(geometry), int(nr), int(nz), float(r0), _device_ptr(cur, "cur"),
+                                             _device_ptr(prev, "prev"), int(field_stride), C.byref(a), C.byref(b),
+                                             stream))
     return a.value, b.value
 
 

@@ -122,6 +122,40 @@ def test_start_state(lbm, oracle):
     assert np.abs(np.stack(gm[1:3]) - np.stack(om[1:3])).max() < 1e-6 * uscale
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("geometry", [0, 2])
+def test_warm_start_init_fields(lbm, oracle, storage, geometry):
+    """lbm_init_fields with caller-given (u_r, u_z, T), u != 0 (the call the learned warm
+    start feeds), against orc_init on the same fields: every stored population, element by
+    element, and the fields of the start state.  Porous field, Ergun drag, buoyancy, walls;
+    FP32 storage to FP32 rounding of the deviations, 16-bit flow storage to its rounding."""
+    nr, nz = 37, 300
+    phi = inputs.porosity_field(nr, nz, 0.3, 0.9, 2.0, seed=13)
+    rng = np.random.default_rng(17)
+    ur = (0.01 * rng.standard_normal((nr, nz))).astype(np.float32)
+    uz = (0.01 * rng.standard_normal((nr, nz))).astype(np.float32)
+    T = (0.5 + 0.2 * rng.standard_normal((nr, nz))).astype(np.float32)
+    kw = dict(nr=nr, nz=nz, geometry=geometry, Ra=1e4, Da=1e-3, Pr=0.71)
+    if geometry == 2:
+        kw.update(body_accel_z=1e-5)
+    s, st0 = _pair(lbm, oracle, storage=storage, phi=phi, **kw)
+    s.init_fields(ur, uz, T)
+    st = oracle.State(st0.p, phi=st0.phi, ur=ur.astype(np.float64), uz=uz.astype(np.float64),
+                      T=T.astype(np.float64))
+    f, g = s.export_populations()
+    r = s.info().r0 + np.arange(nr)
+    dev = st.f - r[None, :, None] * W9[:, None, None]
+    scale = np.abs(dev).max()
+    rel_f = np.abs(f - st.f).max() / scale
+    tol_f = 1e-6 if storage == "f32" else 2.0 ** -10
+    assert rel_f < tol_f, rel_f
+    assert np.abs(g - st.g).max() < 1e-6
+    gm, om = s.moments(), st.moments()
+    errs = _field_errors(gm, om)
+    print(storage, geometry, "start-state populations", rel_f, "fields", errs)
+    assert errs["u"] < (1e-5 if storage == "f32" else 2e-3) and errs["T"] < 1e-6
+
+
 def test_config1_plain_method_10k_steps(lbm, oracle):
     """Porous annulus 48 x 96, R* = 2, eps = 0.6, Da = 1e-2, Ra = 1e3, Pr = 1, Ergun
     F_eps, hot inner / cold outer wall, adiabatic ends, seeded +-1e-3 noise, 10^4
@@ -256,7 +290,7 @@ def test_deterministic(lbm):
 
 def test_largest_domain_runs(lbm):
     """8192 x 8192 (the stress case's size), FP16 storage, tau_nu = 0.51."""
-    phi = inputs.porosity_field(8192, 8192, 0.3, 0.5, 32.0, seed=5)
+    phi = _config5_phi()
     p = lbm.lbm_params_default(nr=8192, nz=8192, Ra=1e7, Da=1e-6, Pr=0.71, tau_nu=0.51, storage="f16",
                                eps_mean=float(phi.mean(dtype=np.float64)))
     s = lbm.Solver(p)
@@ -284,7 +318,10 @@ def test_half_storage_config1(lbm, oracle, storage):
 def test_table2_free_annulus(lbm):
     """Table 2 (Sec. 4.2): free-fluid annulus, phi = 1, Da = 1e8, Pr = 0.7,
     R* = A = 2, 100 x 200, run to steady state: Nu_i within 2 % of the printed
-    values (the paper's own scatter against the literature is about 1 %)."""
+    values (the paper's own scatter against the literature is about 1 %).  With adiabatic
+    top and bottom the steady heat flux through both walls is the same, Nu_i = Nu_o; the
+    non-equilibrium wall rebuild balances neither the mass nor the heat that streams across
+    a wall exactly, so the two agree to the wall scheme's discretisation error, within 1 %."""
     path = os.path.join(os.path.dirname(__file__), "golden", "table2_annulus_nusselt.txt")
     rows = [tuple(map(float, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
     for ra, nu_paper in rows:
@@ -293,16 +330,16 @@ def test_table2_free_annulus(lbm):
         nu_i, nu_o = s.nusselt()
         print("Table 2", ra, nu_i, nu_o, nu_paper, steps, res)
         assert abs(nu_i / nu_paper - 1) < 0.02
+        assert abs(nu_i - nu_o) < 0.01 * nu_i
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_config2_recipe_256x512(lbm, oracle, storage):
     """The single-domain workload's recipe at 256 x 512 (porosity uniform[0.3, 0.9]
     smoothed by sigma = 16, seed 2; Ra = 1e6, Da = 1e-4, Pr = 0.71; tau_nu = 0.5372 at this
-    size), 10^4 steps, per storage type.  FP32: relative L2 <= 2e-5 per field (the
-    developing Ra = 1e6 flow amplifies rounding differences: measured 9.7e-6 in u, 3.3e-6
-    in T) and Nu within the linear bound; 16-bit flow storage: |Delta Nu| <= 1e-3 Nu
-    (measured FP16 4e-6 Nu, BF16 5e-4 Nu) and T within 1e-3, the field errors reported."""
+    size), 10^4 steps, per storage type.  FP32: relative L2 <= 1e-5 per field and Nu within
+    the linear bound; 16-bit flow storage: |Delta Nu| <= 1e-3 and T within 1e-3, the field
+    errors reported."""
     phi = inputs.porosity_field(256, 512, 0.3, 0.9, 16.0, seed=2)
     s, st = _pair(lbm, oracle, storage=storage, phi=phi, nr=256, nz=512, Ra=1e6, Da=1e-4, Pr=0.71)
     assert abs(s.info().tau_nu - 0.5372) < 1e-4
@@ -312,10 +349,10 @@ def test_config2_recipe_256x512(lbm, oracle, storage):
     nu_g, nu_o = s.nusselt(), st.nusselt()
     print(storage, "256x512 field errors", errs, "Nu", nu_g, nu_o)
     if storage == "f32":
-        _fields_close(s, st, 2e-5)
+        _fields_close(s, st, 1e-5)
         _nusselt_within_bound(s, st)
     else:
-        assert abs(nu_g[0] - nu_o[0]) <= 1e-3 * nu_o[0] and abs(nu_g[1] - nu_o[1]) <= 1e-3 * nu_o[1]
+        assert abs(nu_g[0] - nu_o[0]) <= 1e-3 and abs(nu_g[1] - nu_o[1]) <= 1e-3
         assert errs["T"] < 1e-3
 
 
@@ -324,7 +361,7 @@ def test_config5_corner_crop_512(lbm, oracle):
     0.5] smoothed by sigma = 32 at 8192 x 8192, seed 5; crop first, then the annulus built
     at 512 x 512): Ra = 1e7, Da = 1e-6, Pr = 0.71, tau_nu = 0.51, FP16 flow storage, 10^4 steps
     against the FP64 oracle."""
-    phi = inputs.porosity_field(8192, 8192, 0.3, 0.5, 32.0, seed=5)[:512, :512].copy()
+    phi = _config5_phi()[:512, :512].copy()
     s, st = _pair(lbm, oracle, storage="f16", phi=phi, nr=512, nz=512, Ra=1e7, Da=1e-6, Pr=0.71, tau_nu=0.51)
     s.step(10000)
     st.run(10000, THREADS)
@@ -332,17 +369,25 @@ def test_config5_corner_crop_512(lbm, oracle):
     nu_g, nu_o = s.nusselt(), st.nusselt()
     print("config5 crop field errors", errs, "Nu", nu_g, nu_o)
     assert np.isfinite(nu_g).all()
-    assert abs(nu_g[0] - nu_o[0]) <= 1e-3 * abs(nu_o[0]) + 1e-3 and abs(nu_g[1] - nu_o[1]) <= 1e-3 * abs(nu_o[1]) + 1e-3
+    assert abs(nu_g[0] - nu_o[0]) <= 1e-3 and abs(nu_g[1] - nu_o[1]) <= 1e-3
     assert errs["T"] < 1e-3
 
 
-@pytest.mark.slow
-@pytest.mark.skipif(not os.environ.get("LBM_SLOW"), reason="set LBM_SLOW=1 (about 5 min on one GB300)")
-def test_config5_nusselt_drift_fp16_vs_fp32(lbm):
-    """Stress case at full size (8192 x 8192, tau_nu = 0.51): FP16 flow storage against
-    FP32 storage over 10^5 steps, Nu compared every 10^4 steps; both stay finite."""
-    L = lbm
-    phi = inputs.porosity_field(8192, 8192, 0.3, 0.5, 32.0, seed=5)
+_CONFIG5_PHI = {}
+
+
+def _config5_phi():
+    """Porosity of the stress case (uniform[0.3, 0.5] smoothed by sigma = 32 at 8192 x 8192,
+    seed 5), generated once per test session."""
+    if "phi" not in _CONFIG5_PHI:
+        _CONFIG5_PHI["phi"] = inputs.porosity_field(8192, 8192, 0.3, 0.5, 32.0, seed=5)
+    return _CONFIG5_PHI["phi"]
+
+
+def _config5_drift(L, chunks, chunk):
+    """Nu of the full-size stress case (8192 x 8192, tau_nu = 0.51, Ra = 1e7, Da = 1e-6) with
+    FP32 and with FP16 flow storage, every `chunk` steps."""
+    phi = _config5_phi()
     nus = {}
     for storage in ("f32", "f16"):
         p = L.lbm_params_default(nr=8192, nz=8192, Ra=1e7, Da=1e-6, Pr=0.71, tau_nu=0.51, storage=storage,
@@ -351,15 +396,31 @@ def test_config5_nusselt_drift_fp16_vs_fp32(lbm):
         s.set_porosity(phi)
         s.init_fields()
         traj = []
-        for _ in range(10):
-            s.step(10000)
+        for _ in range(chunks):
+            s.step(chunk)
             traj.append(s.nusselt())
         nus[storage] = np.array(traj)
         s.close()
     d = np.abs(nus["f16"] - nus["f32"])
     print("config5 Nu f32", nus["f32"].tolist(), "f16", nus["f16"].tolist(), "max |dNu|", d.max(axis=0).tolist())
     assert np.isfinite(nus["f16"]).all() and np.isfinite(nus["f32"]).all()
-    assert (d <= 1e-3 * np.abs(nus["f32"]) + 1e-3).all()
+    return d
+
+
+def test_config5_nusselt_drift_fp16_vs_fp32(lbm):
+    """Stress case at full size (8192 x 8192, tau_nu = 0.51): FP16 flow storage against FP32
+    storage over 2 x 10^4 steps, Nu compared every 5000 steps: |Delta Nu| <= 1e-3 on both
+    walls, both runs finite."""
+    d = _config5_drift(lbm, 4, 5000)
+    assert (d <= 1e-3).all(), d.max(axis=0)
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not os.environ.get("LBM_SLOW"), reason="set LBM_SLOW=1 (about 5 min on one GB300)")
+def test_config5_nusselt_drift_fp16_vs_fp32_long(lbm):
+    """The same over 10^5 steps, Nu compared every 10^4 steps."""
+    d = _config5_drift(lbm, 10, 10000)
+    assert (d <= 1e-3).all(), d.max(axis=0)
 
 
 def test_async_porosity_upload(lbm):
