@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_pair.cuh"
 #include "lbm_physics.cuh"
 
 using namespace lbm;
@@ -77,39 +78,51 @@ constexpr int BULK_RPT = LBM_BULK_RPT;  // rows per thread of the bulk kernel (3
 constexpr int BULK_RPT_MIN_BLOCKS = LBM_BULK_RPT_MIN_BLOCKS;
 
 // ------------------------------------------------------------- pull (Eq. 22) --
-// Pre-collision deviations at (kr, kz) from the post-collision buffer A: a plain
-// copy of ft_i(x - e_i) (see lbm_physics.cuh).  Periodic z wraps; in the pipe, row 0
-// takes its e_r = +1 populations from the mirror image of itself (the ghost row
-// below the axis, e_r reversed).
-template <int STO, typename R, typename I = int64_t>
-__device__ __forceinline__ void pull_raw(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh,
-                                         R* gh) {
+// Source of each pulled population at (kr, kz): grid index node[i] = (kr - e_ir) nz +
+// (kz - e_iz) and the stored population pop[i] read there.  Periodic z wraps; in the pipe,
+// row 0 takes its e_r = +1 populations from the mirror image of itself (the ghost row
+// below the axis, e_r reversed), i.e. population mirror(i) of row 0.
+template <typename R, typename I>
+__device__ __forceinline__ void pull_sources(const Consts<R>& c, int kr, int kz, I* node, int* pop) {
     const bool pz = c.periodic != 0;
     const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;       // source column for e_z = +1
     const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;       // source column for e_z = -1
     const I row = (I)kr * c.nz;
     const I rowm = row - c.nz, rowp = row + c.nz;
     const bool axis = (kr == 0);                              // reached only in the pipe
-    // e_r = +1 populations: from row kr - 1, or on the axis row from the mirror image
-    const I i1 = axis ? 3 * plane + row + kz : 1 * plane + rowm + kz;
-    const I i5 = axis ? 6 * plane + row + zm : 5 * plane + rowm + zm;
-    const I i8 = axis ? 7 * plane + row + zp : 8 * plane + rowm + zp;
+    node[0] = row + kz;        pop[0] = 0;
+    node[1] = (axis ? row : rowm) + kz;  pop[1] = axis ? 3 : 1;
+    node[2] = row + zm;        pop[2] = 2;
+    node[3] = rowp + kz;       pop[3] = 3;
+    node[4] = row + zp;        pop[4] = 4;
+    node[5] = (axis ? row : rowm) + zm;  pop[5] = axis ? 6 : 5;
+    node[6] = rowp + zm;       pop[6] = 6;
+    node[7] = rowp + zp;       pop[7] = 7;
+    node[8] = (axis ? row : rowm) + zp;  pop[8] = axis ? 7 : 8;
+}
+
+// Flow populations stored against a per-node reference (16-bit storage, see fref_delta).
+template <int STO> __host__ __device__ constexpr bool has_fref() { return STO != LBM_F32; }
+
+// Pre-collision deviations at (kr, kz) from the post-collision buffer A: a plain copy of
+// ft_i(x - e_i) (see lbm_physics.cuh), plus, with 16-bit storage, the reference part
+// D_pop(Q(source)) of the value the source node stored.
+template <int STO, typename R, typename I = int64_t>
+__device__ __forceinline__ void pull_raw(const Consts<R>& c, const Buf<STO>& A, I plane, int kr, int kz, R* fh,
+                                         R* gh) {
+    I node[9];
+    int pop[9];
+    pull_sources<R, I>(c, kr, kz, node, pop);
     const auto* __restrict__ F = A.f;
     const auto* __restrict__ G = A.g;
-    fh[0] = R(ldv(F + row + kz));
-    fh[1] = R(ldv(F + i1));
-    fh[2] = R(ldv(F + 2 * plane + row + zm));
-    fh[3] = R(ldv(F + 3 * plane + rowp + kz));
-    fh[4] = R(ldv(F + 4 * plane + row + zp));
-    fh[5] = R(ldv(F + i5));
-    fh[6] = R(ldv(F + 6 * plane + rowp + zm));
-    fh[7] = R(ldv(F + 7 * plane + rowp + zp));
-    fh[8] = R(ldv(F + i8));
-    gh[0] = R(ldv(G + row + kz));
-    gh[1] = R(ldv(G + (axis ? 3 * plane + row + kz : 1 * plane + rowm + kz)));
-    gh[2] = R(ldv(G + 2 * plane + row + zm));
-    gh[3] = R(ldv(G + 3 * plane + rowp + kz));
-    gh[4] = R(ldv(G + 4 * plane + row + zp));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        float v = ldv(F + pop[i] * plane + node[i]);
+        if constexpr (has_fref<STO>()) v += fref_delta(pop[i], fref_unpack(c.fref[node[i]]));
+        fh[i] = R(v);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) gh[i] = R(ldv(G + pop[i] * plane + node[i]));
 }
 
 // Re-reference pulled thermal deviations to the node's R(x): gh_i += wT_i (R(x - e_i) - R(x))
@@ -149,10 +162,19 @@ __device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I pl
     reref(gh, rref, rm, R(ref_at(c.tref, row + zm)), R(ref_at(c.tref, row + c.nz + kz)), R(ref_at(c.tref, row + zp)));
 }
 
+// Store the post-collision deviations of node n (16-bit storage: against the node's own
+// flow reference Q(n)).
 template <int STO, typename R, typename I = int64_t>
-__device__ __forceinline__ void store(const Buf<STO>& B, I plane, I n, const R* fh, const R* gh) {
+__device__ __forceinline__ void store(const Consts<float>& c, const Buf<STO>& B, I plane, I n, const R* fh,
+                                      const R* gh) {
+    if constexpr (has_fref<STO>()) {
+        const Qf q = fref_unpack(c.fref[n]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) stv(B.f + i * plane + n, float(fh[i]));
+        for (int i = 0; i < 9; ++i) stv(B.f + i * plane + n, float(fh[i]) - fref_delta(i, q));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) stv(B.f + i * plane + n, float(fh[i]));
+    }
 #pragma unroll
     for (int i = 0; i < 5; ++i) stv(B.g + i * plane + n, float(gh[i]));
 }
@@ -272,8 +294,157 @@ __device__ __forceinline__ void update_column(const Consts<float>& c, const Buf<
         porous(c, ph, lin, nl, iph);
         recover(c, r, inv_r, ph, lin, nl, fh, gh, ref, m0, rho, ur, uz, dT);
         collide(c, r, inv_r, ph, lin, nl, iph, fh, gh, ref, m0, rho, ur, uz, dT);
-        store<STO, float, I>(B, plane, n, fh, gh);
+        store<STO, float, I>(c, B, plane, n, fh, gh);
     }
+}
+
+// ------------------------------------------- packed pair update (16-bit storage) --
+// Two z-adjacent nodes (kz0, kz0 + 1) per thread, their arithmetic on the packed FP32
+// instructions of lbm_pair.cuh.  Loads of the node's own columns are single vector loads
+// when the row's first element index is even (VEC: nz even, kz0 even); the shifted
+// columns of the e_z = +-1 populations are two scalar loads.  Flow populations carry the
+// flow reference: the pull adds D_pop(Q(source)), the store subtracts D_i(Q(own)).
+__device__ __forceinline__ V2 ld2(const __half* p, int a, int b, bool vec) {
+    if (vec) return {__half22float2(__ldg(reinterpret_cast<const __half2*>(p + a)))};
+    return v2(__half2float(__ldg(p + a)), __half2float(__ldg(p + b)));
+}
+__device__ __forceinline__ V2 ld2(const __nv_bfloat16* p, int a, int b, bool vec) {
+    if (vec) return {__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p + a)))};
+    return v2(__bfloat162float(__ldg(p + a)), __bfloat162float(__ldg(p + b)));
+}
+__device__ __forceinline__ V2 ld2(const float* p, int a, int b, bool vec) {
+    if (vec) return {__ldg(reinterpret_cast<const float2*>(p + a))};
+    return v2(__ldg(p + a), __ldg(p + b));
+}
+__device__ __forceinline__ Q2 ldq2(const uint2* q, int a, int b, bool vec) {
+    uint2 ua, ub;
+    if (vec) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(q + a));
+        ua = make_uint2(u.x, u.y);
+        ub = make_uint2(u.z, u.w);
+    } else {
+        ua = __ldg(q + a);
+        ub = __ldg(q + b);
+    }
+    const Qf x = fref_unpack(ua), y = fref_unpack(ub);
+    return {v2(x.A, y.A), v2(x.Jr, y.Jr), v2(x.Jz, y.Jz), v2(x.Pn, y.Pn)};
+}
+
+__device__ __forceinline__ void st2(__half* p, int a, V2 v, bool s0, bool s1, bool vec) {
+    const __half2 h = __floats2half2_rn(v.v.x, v.v.y);
+    if (vec && s0 && s1) {
+        *reinterpret_cast<__half2*>(p + a) = h;
+    } else {
+        if (s0) p[a] = __low2half(h);
+        if (s1) p[a + 1] = __high2half(h);
+    }
+}
+__device__ __forceinline__ void st2(__nv_bfloat16* p, int a, V2 v, bool s0, bool s1, bool vec) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.v.x, v.v.y);
+    if (vec && s0 && s1) {
+        *reinterpret_cast<__nv_bfloat162*>(p + a) = h;
+    } else {
+        if (s0) p[a] = __low2bfloat16(h);
+        if (s1) p[a + 1] = __high2bfloat16(h);
+    }
+}
+__device__ __forceinline__ void st2(float* p, int a, V2 v, bool s0, bool s1, bool vec) {
+    if (vec && s0 && s1) {
+        *reinterpret_cast<float2*>(p + a) = v.v;
+    } else {
+        if (s0) p[a] = v.v.x;
+        if (s1) p[a + 1] = v.v.y;
+    }
+}
+
+// Update rows kr0 .. kr0 + rows - 1 (non-wall rows below nr) of the column pair starting
+// at the even column kz0.  VEC: nz is even, so every row's first element index is even
+// and the own-column pairs are aligned for vector loads and stores.
+template <int STO, bool VEC>
+__device__ __forceinline__ void update_pair(const Consts<float>& c, const Buf<STO>& A, const Buf<STO>& B,
+                                            const __half* __restrict__ phi, int plane, int kr0, int rows, int kz0) {
+    static_assert(has_fref<STO>(), "the packed pair update serves 16-bit storage");
+    const int nz = c.nz;
+    const bool pz = c.periodic != 0;
+    // a lane past the last column, or on the end column of a closed geometry (a boundary
+    // node), computes on clamped indices and is not stored
+    const bool in1 = kz0 + 1 < nz;
+    const bool st0 = pz || kz0 > 0;
+    const bool st1 = in1 && (pz || kz0 + 1 < nz - 1);
+    if (!st0 && !st1) return;
+    const int zc1 = in1 ? kz0 + 1 : kz0;
+    const int zm0 = kz0 > 0 ? kz0 - 1 : (pz ? nz - 1 : 0);          // e_z = +1 source, lane 0
+    const int zp0 = in1 ? kz0 + 1 : (pz ? 0 : nz - 1);              // e_z = -1 source, lane 0
+    const int zp1 = kz0 + 2 < nz ? kz0 + 2 : (pz ? kz0 + 2 - nz : nz - 1);   // e_z = -1, lane 1
+    const bool row0_wall = c.geometry == ANNULUS || c.geometry == ANNULUS_PERIODIC_Z;
+    const auto* __restrict__ F = A.f;
+    const float* __restrict__ G = A.g;
+    const uint2* __restrict__ Qp = c.fref;
+#pragma unroll 1
+    for (int j = 0; j < rows; ++j) {
+        const int kr = kr0 + j;
+        if (kr >= c.nr) break;
+        if (kr == c.nr - 1 || (kr == 0 && row0_wall)) continue;
+        const bool axis = kr == 0;   // pipe axis row: e_r = +1 sources are the mirror image
+        const int row = kr * nz, rowp = row + nz, rowm = axis ? row : row - nz;
+        const int p1 = axis ? 3 : 1, p5 = axis ? 6 : 5, p8 = axis ? 7 : 8;
+        // own (kz0, zc1), left (zm0, kz0) and right (zp0, zp1) columns of a row
+        V2 fh[9], gh[5];
+        fh[0] = ld2(F, row + kz0, row + zc1, VEC);
+        fh[1] = ld2(F + p1 * plane, rowm + kz0, rowm + zc1, VEC);
+        fh[2] = ld2(F + 2 * plane, row + zm0, row + kz0, false);
+        fh[3] = ld2(F + 3 * plane, rowp + kz0, rowp + zc1, VEC);
+        fh[4] = ld2(F + 4 * plane, row + zp0, row + zp1, false);
+        fh[5] = ld2(F + p5 * plane, rowm + zm0, rowm + kz0, false);
+        fh[6] = ld2(F + 6 * plane, rowp + zm0, rowp + kz0, false);
+        fh[7] = ld2(F + 7 * plane, rowp + zp0, rowp + zp1, false);
+        fh[8] = ld2(F + p8 * plane, rowm + zp0, rowm + zp1, false);
+        gh[0] = ld2(G, row + kz0, row + zc1, VEC);
+        gh[1] = ld2(G + p1 * plane, rowm + kz0, rowm + zc1, VEC);
+        gh[2] = ld2(G + 2 * plane, row + zm0, row + kz0, false);
+        gh[3] = ld2(G + 3 * plane, rowp + kz0, rowp + zc1, VEC);
+        gh[4] = ld2(G + 4 * plane, row + zp0, row + zp1, false);
+        const V2 ph = ld2(phi, row + kz0, row + zc1, VEC);
+        {   // reference parts of the pulled flow values
+            const Q2 qmo = ldq2(Qp, rowm + kz0, rowm + zc1, VEC), qml = ldq2(Qp, rowm + zm0, rowm + kz0, false);
+            const Q2 qmr = ldq2(Qp, rowm + zp0, rowm + zp1, false);
+            fh[1] += fref_delta2(p1, qmo);
+            fh[5] += fref_delta2(p5, qml);
+            fh[8] += fref_delta2(p8, qmr);
+            const Q2 q0o = ldq2(Qp, row + kz0, row + zc1, VEC), q0l = ldq2(Qp, row + zm0, row + kz0, false);
+            const Q2 q0r = ldq2(Qp, row + zp0, row + zp1, false);
+            fh[0] += fref_delta2(0, q0o);
+            fh[2] += fref_delta2(2, q0l);
+            fh[4] += fref_delta2(4, q0r);
+            const Q2 qpo = ldq2(Qp, rowp + kz0, rowp + zc1, VEC), qpl = ldq2(Qp, rowp + zm0, rowp + kz0, false);
+            const Q2 qpr = ldq2(Qp, rowp + zp0, rowp + zp1, false);
+            fh[3] += fref_delta2(3, qpo);
+            fh[6] += fref_delta2(6, qpl);
+            fh[7] += fref_delta2(7, qpr);
+        }
+        const RowC q = row_consts(c, kr);
+        V2 lin, nl, iph, m0, rho, ur, uz, dT;
+        porous2(c, ph, lin, nl, iph);
+        recover2(c, q, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
+        collide2(c, q, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
+        const Q2 qo = ldq2(Qp, row + kz0, row + zc1, VEC);
+        auto* __restrict__ Fo = B.f;
+        float* __restrict__ Go = B.g;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i] - fref_delta2(i, qo), st0, st1, VEC);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], st0, st1, VEC);
+    }
+}
+
+// Flow reference of a node from its post-collision deviations d_i = f+_i - rest_i:
+// A = sum d_i, J = sum e_i d_i, P = 1024 / (r rho phi) with rho = 1 + A / r, each clamped to
+// the FP16 range (a clamped or otherwise inexact reference only stores larger values).
+__device__ __forceinline__ uint2 fref_make(float A, float Jr, float Jz, float r, float phi) {
+    const float rho = 1.0f + A / r;
+    const float P = fminf(fmaxf(1024.0f / (r * rho * phi), 0.0f), 60000.0f);
+    auto cl = [](float x) { return fminf(fmaxf(x, -60000.0f), 60000.0f); };
+    return fref_pack(cl(A), cl(Jr), cl(Jz), P);
 }
 
 // One thread per column segment of RPT rows: the column's index arithmetic, the
@@ -295,6 +466,15 @@ __global__ void __launch_bounds__(BULK_THREADS, bulk_min_blocks<STO>()) k_bulk(c
     update_column<STO, I>(c, A, B, phi, plane, blockIdx.y * RPT, RPT, kz);
 }
 
+// 16-bit storage: one column pair per thread (2 BULK_THREADS columns per block).
+template <int STO, bool VEC, int RPT>
+__global__ void __launch_bounds__(BULK_THREADS) k_bulk_pair(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
+                                                            const __half* __restrict__ phi, int plane) {
+    const int kz0 = 2 * (blockIdx.x * BULK_THREADS + threadIdx.x);
+    if (kz0 >= c.nz) return;
+    update_pair<STO, VEC>(c, A, B, phi, plane, blockIdx.y * RPT, RPT, kz0);
+}
+
 template <int STO>
 __global__ void k_wall(const Consts<float> c, const Buf<STO> A,
                        const Buf<STO> B, const typename St<STO>::P* __restrict__ phi,
@@ -311,7 +491,7 @@ __global__ void k_wall(const Consts<float> c, const Buf<STO> A,
     float lin, nl, iph;
     porous(c, ph, lin, nl, iph);
     collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, urb, uzb, dTb);
-    store<STO>(B, plane, n, fh, gh);
+    store<STO>(c, B, plane, n, fh, gh);
 }
 
 // Fields of a state at every node (NULL outputs skipped).
@@ -360,7 +540,8 @@ __device__ __forceinline__ double start_T(const Consts<double>& c, const float* 
 template <int STO>
 __global__ void k_init(const Consts<double> c, const Buf<STO> B,
                        const typename St<STO>::P* __restrict__ phi, int64_t plane, const float* ur_in,
-                       const float* uz_in, const float* T_in, double noise, uint64_t seed, __half* __restrict__ tref) {
+                       const float* uz_in, const float* T_in, double noise, uint64_t seed, __half* __restrict__ tref,
+                       uint2* __restrict__ fref) {
     const int kz = blockIdx.x * blockDim.x + threadIdx.x;
     const int kr = blockIdx.y;
     if (kz >= c.nz) return;
@@ -429,7 +610,22 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
         recover(c, r, inv_r, ph, lin, nl, fh, gh, ref, m0, rho, u_r, u_z, dT);
     }
     collide(c, r, inv_r, ph, lin, nl, iphi, fh, gh, ref, m0, rho, u_r, u_z, dT);
-    store<STO>(B, plane, n, fh, gh);
+    if constexpr (has_fref<STO>()) {
+        // the start state's own flow reference: the moments of its deviations
+        double A = 0, Jr = 0, Jz = 0;
+        for (int i = 0; i < 9; ++i) {
+            A += fh[i];
+            Jr += ex9(i) * fh[i];
+            Jz += ez9(i) * fh[i];
+        }
+        const uint2 qw = fref_make((float)A, (float)Jr, (float)Jz, (float)r, (float)ph);
+        fref[n] = qw;
+        const Qf q = fref_unpack(qw);
+        for (int i = 0; i < 9; ++i) stv(B.f + i * plane + n, (float)(fh[i] - (double)fref_delta(i, q)));
+    } else {
+        for (int i = 0; i < 9; ++i) stv(B.f + i * plane + n, (float)fh[i]);
+    }
+    for (int i = 0; i < 5; ++i) stv(B.g + i * plane + n, (float)gh[i]);
 }
 
 template <int STO> __device__ __forceinline__ typename St<STO>::P mkp(float v);
@@ -708,7 +904,11 @@ __global__ void k_export(const Consts<float> c, const Buf<STO> A, int64_t plane,
     const int kr = row0 + j;
     const int64_t n = (int64_t)kr * c.nz + kz, m = (int64_t)j * c.nz + kz, P = (int64_t)nrows * c.nz;
     const double r = r0 + kr;
-    for (int i = 0; i < 9; ++i) out[i * P + m] = (double)ldv(A.f + i * plane + n) + (r + 0.5 * ex9(i)) * w9<double>(i);
+    for (int i = 0; i < 9; ++i) {
+        double ref = 0.0;
+        if constexpr (has_fref<STO>()) ref = (double)fref_delta(i, fref_unpack(c.fref[n]));
+        out[i * P + m] = (double)ldv(A.f + i * plane + n) + ref + (r + 0.5 * ex9(i)) * w9<double>(i);
+    }
     const double wt[5] = {0.6, 0.1, 0.1, 0.1, 0.1};
     const double Tb = T0 + (has_ref<STO>() ? (double)__half2float(c.tref[n]) : 0.0);
     for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)ldv(A.g + i * plane + n) + wt[i] * Tb;
@@ -735,6 +935,39 @@ __global__ void k_rebase(const Buf<STO> A, int64_t plane, int64_t N, __half* __r
             for (int i = 0; i < 5; ++i) stv(A.g + i * plane + n, g[i]);
             tref[n] = h;
         }
+    }
+}
+
+// Flow reference refresh (16-bit storage) of node n in row kr: decode its flow
+// populations with the old Q (as the pull does), take the new Q from their deviation
+// moments (fref_make) and re-encode against it.  The populations, and every field they
+// give, are unchanged up to the storage type's rounding of the re-encoded (now small)
+// values.
+template <int STO, typename I>
+__device__ __forceinline__ void rebase_flow_node(const Consts<float>& c, const Buf<STO>& S,
+                                                 const typename St<STO>::P* __restrict__ phi, I plane, I n, int kr,
+                                                 uint2* __restrict__ fref) {
+    const float r = c.r0 + float(kr);
+    const Qf q0 = fref_unpack(fref[n]);
+    float d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d[i] = ldv(S.f + i * plane + n) + fref_delta(i, q0);
+    const float a = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const float jr = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const float jz = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const uint2 qw = fref_make(a, jr, jz, r, ldv(phi + n));
+    const Qf q1 = fref_unpack(qw);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) stv(S.f + i * plane + n, d[i] - fref_delta(i, q1));
+    fref[n] = qw;
+}
+
+template <int STO>
+__global__ void k_rebase_flow(const Consts<float> c, const Buf<STO> S, const typename St<STO>::P* __restrict__ phi,
+                              int64_t plane, int64_t N, uint2* __restrict__ fref) {
+    if constexpr (has_fref<STO>()) {
+        for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+            rebase_flow_node<STO, int64_t>(c, S, phi, plane, n, (int)(n / c.nz), fref);
     }
 }
 
@@ -775,6 +1008,8 @@ struct lbm_handle {
     int cur = 0;             // buffer holding the current state
     void* phi = nullptr;
     __half* tref = nullptr;  // per-node reference offset R(x) of the thermal deviations
+    uint2* fref = nullptr;   // per-node flow reference Q(x) (16-bit storage)
+    int64_t since_rebase = 0;  // steps since the last flow-reference refresh
     float* fstage = nullptr; // N floats: porosity / init field upload
     // lbm_set_porosity_async: its own copy stream, two staging buffers (the upload into one
     // overlaps the steps that read the other), events and an error count
@@ -848,8 +1083,10 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
     o->T0 = p->heater_len > 0 ? p->T_cold : 0.5 * (p->T_hot + p->T_cold);   // Sec. 4.4: T0 = T_o
     o->Kbar = p->Da * o->L * o->L;
     const int64_t N = (int64_t)p->nr * p->nz;
+    // populations read and written, porosity, and the reference each node's pull reads:
+    // R(x) (FP16) with FP32 storage, Q(x) (4 x FP16) with 16-bit storage
     o->bytes_per_step = N * (int64_t)(2 * (9 * f_size(p->storage) + 5 * g_size(p->storage)) + phi_size(p->storage) +
-                                      (p->storage == LBM_F32 ? sizeof(__half) : 0));
+                                      (p->storage == LBM_F32 ? sizeof(__half) : sizeof(uint2)));
     if (cd) {
         Consts<double>& c = *cd;
         memset(&c, 0, sizeof(c));
@@ -935,6 +1172,13 @@ static dim3 grid2d(const lbm_handle* h, int threads) {
         default: { constexpr int S_ = LBM_BF16; __VA_ARGS__; } break;      \
     }
 
+// Dispatch on the two 16-bit storage types.
+#define DISPATCH_STO16(sto, ...)                                           \
+    switch (sto) {                                                         \
+        case LBM_F16: { constexpr int S_ = LBM_F16; __VA_ARGS__; } break;  \
+        default: { constexpr int S_ = LBM_BF16; __VA_ARGS__; } break;      \
+    }
+
 // rows per thread of the batched kernels: 1, 2 or 4 (the values the tuner tries)
 #define DISPATCH_RPT(rpt, ...)                                             \
     switch (rpt) {                                                         \
@@ -1016,6 +1260,7 @@ int lbm_destroy(lbm_handle* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* b : h->buf) cudaFree(b);
     cudaFree(h->tref);
+    cudaFree(h->fref);
     cudaFree(h->phi);
     cudaFree(h->fstage);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
@@ -1040,10 +1285,11 @@ static int launch_init(lbm_handle* h, const float* ur, const float* uz, const fl
     dim3 g = grid2d(h, 128);
     DISPATCH_STO(h->p.storage,
                  k_init<S_><<<g, 128, 0, h->stream>>>(h->cd, bufp<S_>(h, 0), (const PP<S_>*)h->phi, h->plane, ur, uz,
-                                                      T, h->p.init_noise, h->p.seed, h->tref));
+                                                      T, h->p.init_noise, h->p.seed, h->tref, h->fref));
     CK(cudaGetLastError());
     h->cur = 0;
     h->info.steps = 0;
+    h->since_rebase = 0;
     return LBM_OK;
 }
 
@@ -1078,6 +1324,11 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     ALLOC(h->tref, h->plane * sizeof(__half));
     h->cd.tref = h->tref;
     h->cf.tref = h->tref;
+    if (p->storage != LBM_F32) {
+        ALLOC(h->fref, h->plane * sizeof(uint2));
+        h->cd.fref = h->fref;
+        h->cf.fref = h->fref;
+    }
     ALLOC(h->phi, h->plane * phi_size(p->storage));
     ALLOC(h->partials, (size_t)h->pblocks * RES_NV * sizeof(double));
     ALLOC(h->result, 8 * sizeof(double));
@@ -1211,8 +1462,16 @@ int lbm_init_fields(lbm_handle* h, const float* ur, const float* uz, const float
     return LBM_OK;
 }
 
+// With 16-bit storage the flow reference is refreshed every LBM_FREF_EVERY steps of
+// lbm_step (and before every check interval of lbm_run): the stored values stay of the
+// size of the change since the last refresh however long the run.
+constexpr int64_t LBM_FREF_EVERY = 1024;
+static int launch_rebase(lbm_handle* h);
+
 static int launch_step(lbm_handle* h) {
     if (int rc = wait_phi(h)) return rc;
+    if (h->fref && h->since_rebase >= LBM_FREF_EVERY)
+        if (int rc = launch_rebase(h)) return rc;
     const int nw = wall_count(h->p.geometry, h->p.nr, h->p.nz);
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     if (h->timing) {
@@ -1225,10 +1484,23 @@ static int launch_step(lbm_handle* h) {
     // (9 blocks of 128 threads are resident per SM), else one row per thread so that small
     // grids still fill the device
     const bool i32 = 14 * h->plane < ((int64_t)1 << 31);
-    const int64_t zblocks = (h->p.nz + BULK_THREADS - 1) / BULK_THREADS;
+    const bool pair = h->p.storage != LBM_F32 && i32;   // 16-bit storage: two columns per thread
+    const int cols = pair ? 2 * BULK_THREADS : BULK_THREADS;
+    const int64_t zblocks = (h->p.nz + cols - 1) / cols;
     const int rpt = (i32 && zblocks * ((h->p.nr + BULK_RPT - 1) / BULK_RPT) >= (int64_t)BULK_RPT_MIN_BLOCKS * h->sms) ? BULK_RPT : 1;
-    const dim3 gb((unsigned)((h->p.nz + BULK_THREADS - 1) / BULK_THREADS), (unsigned)((h->p.nr + rpt - 1) / rpt));
-    if (rpt > 1) {
+    const dim3 gb((unsigned)zblocks, (unsigned)((h->p.nr + rpt - 1) / rpt));
+    if (pair) {
+        const bool vec = (h->p.nz & 1) == 0;
+        DISPATCH_STO16(h->p.storage, {
+            auto A = bufp<S_>(h, h->cur);
+            auto B = bufp<S_>(h, h->cur ^ 1);
+            const __half* ph = (const __half*)h->phi;
+            if (vec && rpt > 1) k_bulk_pair<S_, true, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
+            else if (vec) k_bulk_pair<S_, true, 1><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
+            else if (rpt > 1) k_bulk_pair<S_, false, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
+            else k_bulk_pair<S_, false, 1><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
+        });
+    } else if (rpt > 1) {
         DISPATCH_STO(h->p.storage,
                      k_bulk<S_, int, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(
                          h->cf, bufp<S_>(h, h->cur), bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi, (int)h->plane));
@@ -1255,6 +1527,7 @@ static int launch_step(lbm_handle* h) {
     }
     h->cur ^= 1;
     h->info.steps += 1;
+    h->since_rebase += 1;
     return LBM_OK;
 }
 
@@ -1502,14 +1775,26 @@ int lbm_stream_function(lbm_handle* h, float* psi, int on_device, double* psi_ma
     return LBM_OK;
 }
 
+// Refresh the reference of the current state: the temperature reference R(x) with FP32
+// storage, the flow reference Q(x) with 16-bit storage.
+static int launch_rebase(lbm_handle* h) {
+    if (int rc = wait_phi(h)) return rc;
+    const unsigned blocks = (unsigned)std::min<int64_t>((h->N + 255) / 256, (int64_t)h->sms * 16);
+    if (h->p.storage == LBM_F32) {
+        k_rebase<LBM_F32><<<blocks, 256, 0, h->stream>>>(bufp<LBM_F32>(h, h->cur), h->plane, h->N, h->tref);
+    } else {
+        DISPATCH_STO16(h->p.storage, k_rebase_flow<S_><<<blocks, 256, 0, h->stream>>>(
+                                         h->cf, bufp<S_>(h, h->cur), (const PP<S_>*)h->phi, h->plane, h->N, h->fref));
+    }
+    CK(cudaGetLastError());
+    h->since_rebase = 0;
+    return LBM_OK;
+}
+
 int lbm_rebase(lbm_handle* h) {
     if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
-    if (h->p.storage != LBM_F32) return LBM_OK;   // no reference with 16-bit flow storage
     CK(cudaSetDevice(h->device));
-    const unsigned blocks = (unsigned)std::min<int64_t>((h->N + 255) / 256, (int64_t)h->sms * 16);
-    DISPATCH_STO(h->p.storage, k_rebase<S_><<<blocks, 256, 0, h->stream>>>(bufp<S_>(h, h->cur), h->plane, h->N, h->tref));
-    CK(cudaGetLastError());
-    return LBM_OK;
+    return launch_rebase(h);
 }
 
 int lbm_node_class(lbm_handle* h, uint8_t* out) {
@@ -1692,6 +1977,7 @@ struct InstDesc {
     int64_t off_state[2];   // byte offsets of state buffers A and B in the state pool
     int64_t off_phi;        // byte offset of the porosity plane
     int64_t off_tref;       // byte offset of the reference-offset plane R(x) (FP16)
+    int64_t off_fref;       // byte offset of the flow-reference plane Q(x) (16-bit storage)
     int64_t off_mac;        // float offset of the two field snapshots in the snapshot pool
     int64_t plane;          // elements per plane
     double r0, H, dTw;
@@ -1709,18 +1995,50 @@ __device__ __forceinline__ Buf<STO> inst_buf(const InstDesc& d, char* pool, int 
 // RPT consecutive rows of its column (the instance descriptor is read once per thread).
 // The per-node source is the single-problem kernel's (update_column); the two kernels
 // agree to rounding (the compiler may fuse multiply-adds differently in each).
+// Columns a thread of the bulk kernels covers: two with 16-bit storage (update_pair),
+// one with FP32 storage.
+template <int STO> __host__ __device__ constexpr int bulk_cols() { return has_fref<STO>() ? 2 : 1; }
+
 template <int STO, int RPT>
 __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__ desc, char* __restrict__ pool,
                                                     int parity, const int4* __restrict__ tiles) {
     const int4 t = tiles[blockIdx.x];
     const InstDesc& d = desc[t.x];
     const Consts<float> c = d.c;
-    const int kz = t.z + threadIdx.x;
+    const int kz = t.z + bulk_cols<STO>() * threadIdx.x;
     if (kz >= c.nz) return;
     const Buf<STO> A = inst_buf<STO>(d, pool, parity), B = inst_buf<STO>(d, pool, parity ^ 1);
     const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
     const int plane = (int)d.plane;
-    update_column<STO, int>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
+    if constexpr (has_fref<STO>()) {
+        if ((c.nz & 1) == 0) update_pair<STO, true>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
+        else update_pair<STO, false>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
+    } else {
+        update_column<STO, int>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
+    }
+}
+
+// Flow reference refresh of every node the tiles cover (all nodes of the active instances),
+// with the bulk kernels' tiles and block shape.
+template <int STO, int RPT>
+__global__ void __launch_bounds__(256) k_batch_rebase_flow(const InstDesc* __restrict__ desc, char* __restrict__ pool,
+                                                           int parity, const int4* __restrict__ tiles) {
+    if constexpr (has_fref<STO>()) {
+        const int4 t = tiles[blockIdx.x];
+        const InstDesc& d = desc[t.x];
+        const Consts<float> c = d.c;
+        const Buf<STO> S = inst_buf<STO>(d, pool, parity);
+        const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
+        uint2* fref = (uint2*)(pool + d.off_fref);
+#pragma unroll 1
+        for (int q = 0; q < RPT * bulk_cols<STO>(); ++q) {
+            const int kr = t.y + threadIdx.y * RPT + q / bulk_cols<STO>();
+            const int kz = t.z + bulk_cols<STO>() * threadIdx.x + q % bulk_cols<STO>();
+            if (kr >= c.nr) break;
+            if (kz >= c.nz) continue;
+            rebase_flow_node<STO, int>(c, S, phi, (int)d.plane, kr * c.nz + kz, kr, fref);
+        }
+    }
 }
 
 // Wall nodes of all active instances: prefix[k] = first wall thread of active instance k.
@@ -1754,7 +2072,7 @@ __global__ void k_batch_wall(const InstDesc* __restrict__ desc, char* __restrict
     float lin, nl, iph;
     porous(c, ph, lin, nl, iph);
     collide(c, r, rcp_acc(r), ph, lin, nl, iph, fh, gh, refb, m0, rho, urb, uzb, dTb);
-    store<STO>(B, d.plane, n, fh, gh);
+    store<STO>(c, B, d.plane, n, fh, gh);
 }
 
 // Field snapshot `slot` (0 or 1) of every instance the tiles cover, all nodes.
@@ -1765,15 +2083,16 @@ __global__ void __launch_bounds__(256) k_batch_moments(const InstDesc* __restric
     const int4 t = tiles[blockIdx.x];
     const InstDesc& d = desc[t.x];
     const Consts<float> c = d.c;
-    const int kz = t.z + threadIdx.x;
-    if (kz >= c.nz) return;
     const Buf<STO> A = inst_buf<STO>(d, pool, parity);
     const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
     float* m = macpool + d.off_mac + (int64_t)slot * 4 * d.plane;
 #pragma unroll 1
-    for (int j = 0; j < RPT; ++j) {
+    for (int q = 0; q < RPT * bulk_cols<STO>(); ++q) {
+        const int j = q / bulk_cols<STO>();
+        const int kz = t.z + bulk_cols<STO>() * threadIdx.x + q % bulk_cols<STO>();
         const int kr = t.y + threadIdx.y * RPT + j;
         if (kr >= c.nr) break;
+        if (kz >= c.nz) continue;
         const int cls = node_class(c.geometry, c.nr, c.nz, kr, kz);
         const int64_t n = (int64_t)kr * c.nz + kz;
         float fh[9], gh[5], m0, rho, ur = 0.f, uz = 0.f, dT, ref;
@@ -1878,6 +2197,7 @@ struct lbm_batch {
     int64_t max_plane = 0;
     int parity = 0;
     int64_t steps = 0;
+    int64_t since_rebase = 0;         // steps since the last flow-reference refresh (16-bit)
     std::vector<char> active;         // 1 = still stepping
     // tiles and wall lists of the active set
     int bz = 128, rows = 1, rpt = 1;  // bulk block shape and rows per thread
@@ -1913,8 +2233,9 @@ static int batch_rebuild(lbm_batch* b) {
         if (!b->active[i]) continue;
         act.push_back(i);
         prefix.push_back(prefix.back() + wall_count(b->p[i].geometry, b->p[i].nr, b->p[i].nz));
+        const int zstep = b->bz * (b->storage == LBM_F32 ? 1 : 2);   // columns of a tile (bulk_cols)
         for (int kr = 0; kr < b->p[i].nr; kr += b->rows * b->rpt)
-            for (int z0 = 0; z0 < b->p[i].nz; z0 += b->bz) tiles.push_back(make_int4(i, kr, z0, 0));
+            for (int z0 = 0; z0 < b->p[i].nz; z0 += zstep) tiles.push_back(make_int4(i, kr, z0, 0));
     }
     b->ntiles = (int)tiles.size();
     b->nactive = (int)act.size();
@@ -1944,8 +2265,23 @@ template <int STO> static Buf<STO> batch_buf(const lbm_batch* b, int i, int whic
     return r;
 }
 
+// Flow-reference refresh of every active instance (16-bit storage), one launch.
+static int batch_launch_rebase_flow(lbm_batch* b) {
+    if (b->storage != LBM_F32 && b->nactive) {
+        const dim3 blk(b->bz, b->rows);
+        DISPATCH_STO16(b->storage, DISPATCH_RPT(b->rpt, k_batch_rebase_flow<S_, R_><<<b->ntiles, blk, 0, b->stream>>>(
+                                                            b->d_desc, b->pool, b->parity, b->d_tiles)));
+        CK(cudaGetLastError());
+    }
+    b->since_rebase = 0;
+    return LBM_OK;
+}
+
 static int batch_launch_step(lbm_batch* b) {
     if (!b->nactive) return LBM_OK;
+    // 16-bit storage: the refresh of lbm_step, every LBM_FREF_EVERY steps since the last
+    if (b->storage != LBM_F32 && b->since_rebase >= LBM_FREF_EVERY)
+        if (int rc = batch_launch_rebase_flow(b)) return rc;
     const dim3 blk(b->bz, b->rows);
     DISPATCH_STO(b->storage, DISPATCH_RPT(b->rpt, k_batch_bulk<S_, R_><<<b->ntiles, blk, 0, b->stream>>>(
                                                        b->d_desc, b->pool, b->parity, b->d_tiles)));
@@ -1954,6 +2290,7 @@ static int batch_launch_step(lbm_batch* b) {
                                  b->d_desc, b->pool, b->parity, b->d_active, b->d_prefix, b->nactive));
     CK(cudaGetLastError());
     b->parity ^= 1;
+    b->since_rebase += 1;
     return LBM_OK;
 }
 
@@ -2006,6 +2343,8 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
         state_off += (plane * (int64_t)phi_size(b->storage) + 255) / 256 * 256;
         d.off_tref = state_off;
         state_off += (plane * (int64_t)sizeof(__half) + 255) / 256 * 256;
+        d.off_fref = state_off;
+        if (p[i].storage != LBM_F32) state_off += (plane * (int64_t)sizeof(uint2) + 255) / 256 * 256;
         d.off_mac = mac_off;
         mac_off += 8 * plane;
         d.r0 = b->info[i].r0;
@@ -2023,6 +2362,9 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
         for (int i = 0; i < n; ++i) {
             b->desc[i].c.tref = (const __half*)(b->pool + b->desc[i].off_tref);
             b->cd[i].tref = b->desc[i].c.tref;
+            const uint2* fr = b->storage == LBM_F32 ? nullptr : (const uint2*)(b->pool + b->desc[i].off_fref);
+            b->desc[i].c.fref = fr;
+            b->cd[i].fref = fr;
         }
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->macpool, mac_off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, n * sizeof(InstDesc));
@@ -2048,7 +2390,7 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
                                                                                 (float)p[i].eps_mean);
             k_init<S_><<<g, 128, 0, b->stream>>>(b->cd[i], batch_buf<S_>(b, i, 0), (const PP<S_>*)(b->pool + d.off_phi),
                                                  d.plane, nullptr, nullptr, nullptr, p[i].init_noise, p[i].seed,
-                                                 (__half*)(b->pool + d.off_tref));
+                                                 (__half*)(b->pool + d.off_tref), (uint2*)b->cd[i].fref);
         });
     }
     e = cudaGetLastError();
@@ -2118,7 +2460,7 @@ int lbm_batch_init_fields(lbm_batch* b, int32_t i, const float* ur, const float*
     DISPATCH_STO(b->storage, k_init<S_><<<g, 128, 0, b->stream>>>(b->cd[i], batch_buf<S_>(b, i, b->parity),
                                                                    (const PP<S_>*)(b->pool + d.off_phi), d.plane, dur,
                                                                    duz, dT, b->p[i].init_noise, b->p[i].seed,
-                                                                   (__half*)(b->pool + d.off_tref)));
+                                                                   (__half*)(b->pool + d.off_tref), (uint2*)b->cd[i].fref));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(b->stream));
     if (!b->active[i]) {
@@ -2142,12 +2484,17 @@ int lbm_batch_step(lbm_batch* b, int64_t nsteps) {
 // Reference refresh of instance i (the kernel of lbm_rebase, on the instance's current
 // buffer).
 static int batch_rebase_one(lbm_batch* b, int i) {
-    if (b->storage != LBM_F32) return LBM_OK;   // no reference with 16-bit flow storage
     const InstDesc& d = b->desc[i];
     const int64_t N = (int64_t)b->p[i].nr * b->p[i].nz;
     const unsigned blocks = (unsigned)std::min<int64_t>((N + 255) / 256, 4096);
-    DISPATCH_STO(b->storage, k_rebase<S_><<<blocks, 256, 0, b->stream>>>(batch_buf<S_>(b, i, b->cur_parity(i)), d.plane,
-                                                                          N, (__half*)(b->pool + d.off_tref)));
+    if (b->storage == LBM_F32) {
+        k_rebase<LBM_F32><<<blocks, 256, 0, b->stream>>>(batch_buf<LBM_F32>(b, i, b->cur_parity(i)), d.plane, N,
+                                                         (__half*)(b->pool + d.off_tref));
+    } else {
+        DISPATCH_STO16(b->storage, k_rebase_flow<S_><<<blocks, 256, 0, b->stream>>>(
+                                       d.c, batch_buf<S_>(b, i, b->cur_parity(i)), (const PP<S_>*)(b->pool + d.off_phi),
+                                       d.plane, N, (uint2*)(b->pool + d.off_fref)));
+    }
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -2159,6 +2506,7 @@ int lbm_batch_rebase(lbm_batch* b) {
         int rc = batch_rebase_one(b, i);
         if (rc) return rc;
     }
+    b->since_rebase = 0;
     return LBM_OK;
 }
 
@@ -2187,8 +2535,13 @@ int lbm_batch_run(lbm_batch* b, int64_t max_steps, int64_t check_every, double t
     while (total < max_steps && b->nactive > 0) {
         const int64_t k = std::min(check_every, max_steps - total);
         // reference refresh before every check interval, as lbm_run does
-        for (int i = 0; i < b->n; ++i)
-            if (b->active[i] && (rc = batch_rebase_one(b, i))) return rc;
+        if (b->storage == LBM_F32) {
+            for (int i = 0; i < b->n; ++i)
+                if (b->active[i] && (rc = batch_rebase_one(b, i))) return rc;
+        } else if ((rc = batch_launch_rebase_flow(b))) {
+            return rc;
+        }
+        b->since_rebase = 0;
         if (k == check_every) {
             if (b->graph_dirty || b->graph_steps != k || b->graph_parity != b->parity) {
                 batch_free_graph(b);
