@@ -342,38 +342,174 @@ def sweep_throughput(steps: int):
             "speedup": round(ts / tb, 2), "tile": f"{cols}x{rows}", "steps": 2 * steps}
 
 
-def time_to_steady(max_steps: int = 300000, check: int = 1000, tol: float = 1e-8):
-    """Time to the steady criterion (mean change per step over a check interval <= tol)
-    for a bounded sweep: 16 instances with the sweep's parameter ranges at
-    Nr ~ U{24..48}, Nz = 2 Nr (seed 4).  Plain: each instance alone in FP32 (lbm_run);
-    batched FP32; batched FP16 storage.  |dNu| against the plain FP32 results."""
-    from paper_1409_5929_gb300 import lbm
+def _tts_subset(n: int = 16):
+    """The n draws of the 256-instance sweep (seed 3, Nr ~ U{64..512}) with the shortest
+    diffusive time, estimated as 3 L^2 Pr / (tau - 1/2) = 17.3 L sqrt(Pr Ra) steps at the
+    Ma = 0.1 of Eq. 39: a subset at the sweep's real sizes that finishes in bounded time."""
+    from paper_1409_5929_gb300 import inputs
 
-    out = {"workload": "16 annulus instances, sweep parameter ranges, Nr ~ U{24..48}, Nz = 2 Nr, seed 4",
-           "criterion": f"interval residual <= {tol:g} (checked every {check} steps)"}
-    p32 = _sweep_params(lbm, 16, 4, "f32", 24, 48)
-    t0 = time.perf_counter()
-    nu_ref, steps_ref = [], []
-    for p in p32:
+    draws = inputs.sweep_instances(256, seed=3)
+    est = sorted((17.3 * (d["nr"] - 1) * (d["Pr"] * d["Ra"]) ** 0.5, i) for i, d in enumerate(draws))
+    return sorted(i for _, i in est[:n])
+
+
+def _settle_time(times, nus, ref, tol):
+    """Wall time at the first check after which |Nu - ref| <= tol on both walls holds to the
+    end of the record (None if it never does)."""
+    ok = np.abs(np.asarray(nus) - ref[None]).max(axis=-1) <= tol
+    for k in range(len(ok)):
+        if ok[k:].all():
+            return times[k]
+    return None
+
+
+def time_to_steady(max_steps: int = 400000, check: int = 1000, tol: float = 1e-8, dnu_tol: float = 1e-3):
+    """Time to steady state for a subset of the batched sweep (_tts_subset): each instance
+    alone with FP32 storage (plain), the batch with FP32 storage, the batch with FP16
+    storage.  Two criteria: (a) the method's residual criterion (interval mean change per
+    step <= tol, lbm_run / lbm_batch_run), and (b) the metric's: the wall time after which
+    both Nusselt numbers stay within dnu_tol of the plain FP32 run's final values."""
+    import torch
+
+    from paper_1409_5929_gb300 import inputs, lbm
+
+    idx = _tts_subset()
+    draws = inputs.sweep_instances(256, seed=3)
+
+    def params(sto):
+        return [lbm.lbm_params_default(nr=draws[i]["nr"], nz=draws[i]["nz"], Ra=draws[i]["Ra"], Da=draws[i]["Da"],
+                                       eps_mean=draws[i]["eps"], Pr=draws[i]["Pr"],
+                                       radius_ratio=draws[i]["radius_ratio"], storage=sto) for i in idx]
+
+    out = {"workload": f"{len(idx)} draws of the 256-instance sweep (seed 3) with the shortest estimated diffusive "
+                       f"time: Nr {min(draws[i]['nr'] for i in idx)}..{max(draws[i]['nr'] for i in idx)}, Nz = 2 Nr, "
+                       f"{sum(draws[i]['nr'] * draws[i]['nz'] for i in idx) / 1e6:.2f} M nodes",
+           "criterion_residual": f"interval residual <= {tol:g}, checked every {check} steps, cap {max_steps} steps",
+           "criterion_nu": f"|Nu - Nu_ref| <= {dnu_tol:g} on both walls from then on; Nu_ref = plain FP32 at its end"}
+    # plain FP32: one instance at a time, Nusselt numbers recorded at every check
+    recs, t_total = [], 0.0
+    for p in params("f32"):
         s = lbm.Solver(p)
-        n, r = s.run(max_steps, check, tol)
-        nu_ref.append(s.nusselt())
-        steps_ref.append(n)
-        s.close()
-    out["plain_fp32_s"] = round(time.perf_counter() - t0, 3)
-    out["plain_fp32_steps_max"] = int(max(steps_ref))
-    nu_ref = np.array(nu_ref)
-    for name, sto in (("batched_fp32", "f32"), ("batched_fp16", "f16")):
-        b = lbm.Batch(_sweep_params(lbm, 16, 4, sto, 24, 48))
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        steps, res = b.run(max_steps, check, tol)
-        dt = time.perf_counter() - t0
-        nu = np.stack(b.nusselt(), axis=1)
+        times, nus, done, res = [], [], 0, np.inf
+        while done < max_steps and not res <= tol:
+            n, res = s.run(check, check, tol)
+            done += n
+            nus.append(s.nusselt())
+            times.append(time.perf_counter() - t0)
+        t_total += times[-1]
+        recs.append((times, nus, done, res))
+        s.close()
+    nu_ref = np.array([r[1][-1] for r in recs])
+    settle = [_settle_time(r[0], r[1], nu_ref[k], dnu_tol) for k, r in enumerate(recs)]
+    out["plain_fp32"] = {"s": round(t_total, 3), "converged": int(sum(r[3] <= tol for r in recs)), "of": len(recs),
+                         "steps_max": int(max(r[2] for r in recs)),
+                         "nu_settle_s_sum": round(sum(x for x in settle if x is not None), 3),
+                         "nu_settled": int(sum(x is not None for x in settle))}
+    for name, sto in (("batched_fp32", "f32"), ("batched_fp16", "f16")):
+        b = lbm.Batch(params(sto))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        times, nus, total = [], [], 0
+        res = np.full(len(idx), np.inf)
+        while total < max_steps and not (res <= tol).all():
+            _, r = b.run(check, check, tol)
+            res = np.where(np.isfinite(r), r, res)       # instances stopped earlier report inf
+            total += check
+            nus.append(np.stack(b.nusselt(), axis=1))
+            times.append(time.perf_counter() - t0)
         b.close()
-        out[name] = {"s": round(dt, 3), "speedup_vs_plain": round(out["plain_fp32_s"] / dt, 2),
-                     "converged": int((res <= tol).sum()), "of": 16, "steps_max": int(steps.max()),
-                     "max_abs_dNu": float(np.abs(nu - nu_ref).max())}
+        nus = np.array(nus)
+        settle = [_settle_time(times, nus[:, k], nu_ref[k], dnu_tol) for k in range(len(idx))]
+        t_nu = max(x for x in settle if x is not None) if all(x is not None for x in settle) else None
+        out[name] = {"s": round(times[-1], 3), "converged": int((res <= tol).sum()), "of": len(idx),
+                     "steps": int(total), "speedup_vs_plain": round(out["plain_fp32"]["s"] / times[-1], 2),
+                     "nu_settled": int(sum(x is not None for x in settle)),
+                     "nu_settle_s": round(t_nu, 3) if t_nu is not None else None,
+                     "nu_speedup_vs_plain": round(out["plain_fp32"]["nu_settle_s_sum"] / t_nu, 2) if t_nu else None,
+                     "max_abs_dNu_end": float(np.abs(nus[-1] - nu_ref).max()),
+                     "residual_max_end": float(np.max(res))}
     return out
+
+
+def warm_start_section(nr: int = 64, nz: int = 128, ntrain: int = 256, nheld: int = 32, check: int = 1000,
+                       tol: float = 1e-8, max_steps: int = 200000, dnu_tol: float = 1e-3):
+    """Bounded learned-warm-start measurement (the config-4 pipeline at a reduced size):
+    steady fields of ntrain sweep-range instances from the batched solver, the network
+    trained on them on the GPU, then nheld held-out instances run to the residual
+    criterion (batched, FP32) from the cold start and from the network's fields.  Warm
+    time includes the network's inference and the upload of its fields."""
+    import torch
+
+    from paper_1409_5929_gb300 import fno as F, lbm, warmstart as W
+
+    t0 = time.perf_counter()
+    train_inst = W.make_instances(ntrain, 40000, nr, nz)
+    held = W.make_instances(nheld, 50000, nr, nz)
+    _, res_tr, _, fields, dt_gen = W.run_batch(train_inst, max_steps, check, tol)
+    X = torch.tensor(W.features(train_inst, nr, nz), device="cuda")
+    Y = torch.tensor(np.stack([W.targets_from_fields(f[1], f[2], f[3]) for f in fields]), device="cuda")
+    net = F.FNO2d(nr, nz, width=32, modes=16, seed=1)
+    t1 = time.perf_counter()
+    losses = W.train(net, X, Y, epochs=20, batch=8, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+
+    def run(warm):
+        b = lbm.Batch([p for p, _, _ in held])
+        for i, (p, phi, _) in enumerate(held):
+            b.set_porosity(i, phi)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        if warm:
+            pred = W.predict(net, torch.tensor(W.features(held, nr, nz), device="cuda"))
+            ur, uz, T = W.fields_from_targets(pred)
+            for i in range(len(held)):
+                b.init_fields(i, ur[i], uz[i], T[i])
+        else:
+            for i in range(len(held)):
+                b.init_fields(i)
+        torch.cuda.synchronize()
+        t_start = time.perf_counter() - ts
+        times, nus, total = [], [], 0
+        res = np.full(len(held), np.inf)
+        steps = np.zeros(len(held), np.int64)
+        while total < max_steps and not (res <= tol).all():
+            st, r = b.run(check, check, tol)
+            res = np.where(np.isfinite(r), r, res)       # instances stopped earlier report inf
+            steps += st
+            total += check
+            nus.append(np.stack(b.nusselt(), axis=1))
+            times.append(time.perf_counter() - ts)
+        b.close()
+        return t_start, np.array(times), np.array(nus), steps, res
+
+    c_start, c_t, c_nu, c_steps, c_res = run(False)
+    w_start, w_t, w_nu, w_steps, w_res = run(True)
+    both = (c_res <= tol) & (w_res <= tol)
+    ref = c_nu[-1]
+    agree = np.abs(w_nu[-1] - ref).max(axis=1) <= dnu_tol
+    settle_c = [_settle_time(c_t, c_nu[:, k], ref[k], dnu_tol) for k in range(len(held))]
+    settle_w = [_settle_time(w_t, w_nu[:, k], ref[k], dnu_tol) for k in range(len(held))]
+    ok = [k for k in range(len(held)) if both[k] and settle_c[k] is not None and settle_w[k] is not None]
+    return {
+        "workload": f"{nr}x{nz} annuli, sweep parameter ranges, smoothed porosity; {ntrain} training fields, "
+                    f"{nheld} held-out; FNO 4 layers, width 32, 16 modes, 20 epochs",
+        "data_generation_s": round(dt_gen, 2), "train_s": round(t_train, 2),
+        "train_converged": int((res_tr <= tol).sum()), "loss_first_last": [losses[0], losses[-1]],
+        "cold": {"converged": int((c_res <= tol).sum()), "s_to_all_converged_or_cap": round(float(c_t[-1]), 3),
+                 "steps_sum": int(c_steps.sum()), "start_s": round(c_start, 3)},
+        "warm": {"converged": int((w_res <= tol).sum()), "s_to_all_converged_or_cap": round(float(w_t[-1]), 3),
+                 "steps_sum": int(w_steps.sum()), "start_s_incl_inference": round(w_start, 3)},
+        "both_converged": int(both.sum()), "warm_agrees_with_cold_within_dNu_tol": int((agree & both).sum()),
+        "steps_ratio_cold_over_warm": round(float(c_steps[both].sum()) / max(float(w_steps[both].sum()), 1.0), 3)
+        if both.any() else None,
+        "nu_settle_s_cold_sum": round(sum(settle_c[k] for k in ok), 3) if ok else None,
+        "nu_settle_s_warm_sum": round(sum(settle_w[k] for k in ok), 3) if ok else None,
+        "wall_s_ratio_cold_over_warm": round(float(c_t[-1]) / float(w_t[-1]), 3),
+        "total_s": round(time.perf_counter() - t0, 1),
+    }
 
 
 def _oracle_sample_state():
@@ -485,6 +621,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         line["sweep"] = sweep_throughput(100)
         line["time_to_steady"] = time_to_steady()
+        line["warm_start"] = warm_start_section()
     if rank == 0:
         line["cpu_baseline"] = cpu_sample(args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
         print(json.dumps(line), flush=True)

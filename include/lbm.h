@@ -121,7 +121,8 @@ typedef struct lbm_info {
     double Kbar;             /* Da * L^2 */
     int64_t steps;           /* steps taken since the last (re)initialisation */
     int64_t bytes_per_step;  /* algorithmic HBM bytes of one step: read + write of every
-                                population, one porosity and (FP32 storage) one FP16
+                                population, one FP32 porosity, the FP16 temperature
+                                reference and (16-bit storage) the 4 x FP16 flow
                                 reference (lbm_rebase) read per node */
 } lbm_info;
 
@@ -248,13 +249,17 @@ int lbm_run(lbm_handle *h, int64_t max_steps, int64_t check_every, double tol, i
 /* Storage detail with no counterpart in the paper.  The thermal populations are
  * stored as deviations from w_i (T0 + R(x)), R(x) a per-node FP16 offset set from the
  * start temperature; this call sets R(x) to the current T(x) - T0 (rounded to FP16)
- * and re-expresses the stored deviations against it.  Every field and population is
- * unchanged up to FP32 rounding; what changes is the size of the stored numbers, and
- * so the rounding of later steps: without refreshes, FP32 rounding stops slow thermal
- * modes once their change per step drops below the rounding of |T - T0 - R|
- * (a spread of about 1e-3 in Nu on slowly converging annuli); lbm_run refreshes before
- * every check interval.  FP32 storage only: with 16-bit flow populations R(x) = 0 and
- * this call does nothing (their flow rounding sets the steady-state floor).
+ * and re-expresses the stored deviations against it.  With 16-bit storage the flow
+ * populations are likewise stored against a per-node reference equilibrium (the
+ * deviation part of Eq. 32's f_eq from a per-node FP16 quad: r (rho - 1), r rho u and
+ * 1 / (r rho phi)), which this call refreshes in the same pass.  Every field and
+ * population is unchanged up to the storage rounding of the re-encoded values; what
+ * changes is the size of the stored numbers, and so the rounding of later steps:
+ * without refreshes, FP32 rounding stops slow thermal modes once their change per step
+ * drops below the rounding of |T - T0 - R| (a spread of about 1e-3 in Nu on slowly
+ * converging annuli), and 16-bit rounding of deviations from the rest state jitters the
+ * flow by about 4e-4 per step.  lbm_run refreshes before every check interval; with
+ * 16-bit storage lbm_step also refreshes every 1024 steps since the last refresh.
  * Asynchronous on the handle's stream. */
 int lbm_rebase(lbm_handle *h);
 

@@ -9,12 +9,16 @@
 //                     type (FP32, FP16 or BF16), g planes in FP32, holding the
 //                     deviations of lbm_physics.cuh.  A step reads one buffer and
 //                     writes the other.
-//   phi:              nr*nz porosity values (FP32, or FP16 with 16-bit storage).
+//   phi:              nr*nz porosity values (FP32).
+//   tref:             nr*nz temperature references R(x) (FP16).
+//   fref:             nr*nz flow references Q(x), 4 x FP16 each (16-bit storage).
 //   macro snapshots, reduction scratch, staging: only for diagnostics.
 //
 // A step is two launches on the handle's stream:
 //   k_bulk  every non-wall node: pull (Eq. 22, 33), recovery (Eq. 26-30, 38),
-//           collision (Eq. 21-24, 33-37), store.  Grid (nz / 128, nr).
+//           collision (Eq. 21-24, 33-37), store.  Grid (nz / 128, nr).  With
+//           16-bit storage k_bulk_pair: two z-adjacent nodes per thread on the
+//           packed FP32 instructions (lbm_pair.cuh).
 //   k_wall  every wall node: rebuild from the interior neighbour by
 //           non-equilibrium extrapolation (Sec. 4, ref. [47]), collision with
 //           u = 0 and the wall temperature, store.  One thread per wall node.
@@ -41,8 +45,8 @@ using namespace lbm;
 // ------------------------------------------------------------ storage types --
 // Flow populations in the storage type; temperature populations always FP32 (in
 // 16 bits the per-step change of g - wT T0, of order 0.05, falls below the format's
-// resolution and the temperature field stagnates); porosity FP32, or FP16 with
-// 16-bit storage.
+// resolution and the temperature field stagnates); porosity always FP32 (in FP16 its
+// half-ulp, 2.4e-4 relative near 0.7, moves the Darcy drag of Eq. 8 by about 2e-3).
 __device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const __half* p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
@@ -52,8 +56,8 @@ __device__ __forceinline__ void stv(__nv_bfloat16* p, float v) { *p = __float2bf
 
 template <int STO> struct St;
 template <> struct St<LBM_F32> { using TF = float; using TG = float; using P = float; };
-template <> struct St<LBM_F16> { using TF = __half; using TG = float; using P = __half; };
-template <> struct St<LBM_BF16> { using TF = __nv_bfloat16; using TG = float; using P = __half; };
+template <> struct St<LBM_F16> { using TF = __half; using TG = float; using P = float; };
+template <> struct St<LBM_BF16> { using TF = __nv_bfloat16; using TG = float; using P = float; };
 
 // One state buffer: nine flow planes then five temperature planes.
 template <int STO> struct Buf {
@@ -63,7 +67,7 @@ template <int STO> struct Buf {
 
 static size_t f_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
 static size_t g_size(int) { return 4; }
-static size_t phi_size(int sto) { return sto == LBM_F32 ? 4 : 2; }
+static size_t phi_size(int) { return 4; }
 static size_t state_bytes(int sto, int64_t plane) { return (size_t)plane * (9 * f_size(sto) + 5 * g_size(sto)); }
 
 constexpr int BULK_THREADS = 128;
@@ -135,13 +139,22 @@ __device__ __forceinline__ void reref(R* gh, R r0, R rm, R zm, R rp, R zp) {
     gh[4] += R(0.1) * (zp - r0);
 }
 
-template <typename I>
-__device__ __forceinline__ float ref_at(const __half* __restrict__ Rp, I n) { return __half2float(Rp[n]); }
+// Every storage type keeps the temperature reference R(x): the FP32 temperature populations
+// stored against T0 alone would carry deviations of size |T - T0|, on which FP32 arithmetic
+// biases the thermal update and freezes slow modes short of their fixed point.
+template <int STO> __host__ __device__ constexpr bool has_ref() { return true; }
 
-// The temperature reference is kept with FP32 storage only: with 16-bit flow
-// populations the per-step rounding jitter of the flow (about 4e-4 in u) sets the
-// steady-state floor, and R(x) = 0 there (gh relative to T0, no reference reads).
-template <int STO> __host__ __device__ constexpr bool has_ref() { return STO == LBM_F32; }
+// R(x) of node n: its own FP16 plane with FP32 storage, the fourth FP16 of the node's
+// reference word with 16-bit storage.
+template <int STO, typename R, typename I>
+__device__ __forceinline__ float tref_at(const Consts<R>& c, I n) {
+    if constexpr (has_fref<STO>()) {
+        const uint32_t w = c.fref[n].y;
+        return __high2float(*reinterpret_cast<const __half2*>(&w));
+    } else {
+        return __half2float(c.tref[n]);
+    }
+}
 
 // Pull (Eq. 22) with the thermal deviations re-referenced to R(x), which *rref receives.
 template <int STO, typename R, typename I = int64_t>
@@ -156,10 +169,11 @@ __device__ __forceinline__ void pull(const Consts<R>& c, const Buf<STO>& A, I pl
     const int zm = (pz && kz == 0) ? c.nz - 1 : kz - 1;
     const int zp = (pz && kz == c.nz - 1) ? 0 : kz + 1;
     const I row = (I)kr * c.nz;
-    rref = R(ref_at(c.tref, row + kz));
+    rref = R(tref_at<STO>(c, row + kz));
     // on the pipe axis row g_1 comes from the node's own mirror image
-    const R rm = kr == 0 ? rref : R(ref_at(c.tref, row - c.nz + kz));
-    reref(gh, rref, rm, R(ref_at(c.tref, row + zm)), R(ref_at(c.tref, row + c.nz + kz)), R(ref_at(c.tref, row + zp)));
+    const R rm = kr == 0 ? rref : R(tref_at<STO>(c, row - c.nz + kz));
+    reref(gh, rref, rm, R(tref_at<STO>(c, row + zm)), R(tref_at<STO>(c, row + c.nz + kz)),
+          R(tref_at<STO>(c, row + zp)));
 }
 
 // Store the post-collision deviations of node n (16-bit storage: against the node's own
@@ -212,7 +226,7 @@ __device__ __forceinline__ void wall_state(const Consts<R>& c, const Buf<STO> A,
     if (cls >= INLET) ipb = rcp_acc(R(ldv(phi + (int64_t)kr * c.nz + kz)));
     rebuild_flow(rb, rf, ipb, ipf, drhob, rhob, urb, uzb, m0f, rhof, urf, uzf, fhf, fh);
     // deviations relative to this boundary node's own reference R_b
-    refb = has_ref<STO>() ? R(__half2float(c.tref[(int64_t)kr * c.nz + kz])) : R(0);
+    refb = R(tref_at<STO>(c, (int64_t)kr * c.nz + kz));
     dTb = (cls == WALL_IN || cls == INLET) ? (c.T_hot - c.T0) - refb
           : cls == WALL_OUT                 ? (c.T_cold - c.T0) - refb
                                             : (dTf + reff) - refb;
@@ -327,7 +341,7 @@ __device__ __forceinline__ Q2 ldq2(const uint2* q, int a, int b, bool vec) {
         ub = __ldg(q + b);
     }
     const Qf x = fref_unpack(ua), y = fref_unpack(ub);
-    return {v2(x.A, y.A), v2(x.Jr, y.Jr), v2(x.Jz, y.Jz), v2(x.Pn, y.Pn)};
+    return {v2(x.A, y.A), v2(x.Jr, y.Jr), v2(x.Jz, y.Jz), v2(x.R, y.R)};
 }
 
 __device__ __forceinline__ void st2(__half* p, int a, V2 v, bool s0, bool s1, bool vec) {
@@ -362,7 +376,7 @@ __device__ __forceinline__ void st2(float* p, int a, V2 v, bool s0, bool s1, boo
 // and the own-column pairs are aligned for vector loads and stores.
 template <int STO, bool VEC>
 __device__ __forceinline__ void update_pair(const Consts<float>& c, const Buf<STO>& A, const Buf<STO>& B,
-                                            const __half* __restrict__ phi, int plane, int kr0, int rows, int kz0) {
+                                            const float* __restrict__ phi, int plane, int kr0, int rows, int kz0) {
     static_assert(has_fref<STO>(), "the packed pair update serves 16-bit storage");
     const int nz = c.nz;
     const bool pz = c.periodic != 0;
@@ -405,46 +419,61 @@ __device__ __forceinline__ void update_pair(const Consts<float>& c, const Buf<ST
         gh[3] = ld2(G + 3 * plane, rowp + kz0, rowp + zc1, VEC);
         gh[4] = ld2(G + 4 * plane, row + zp0, row + zp1, false);
         const V2 ph = ld2(phi, row + kz0, row + zc1, VEC);
-        {   // reference parts of the pulled flow values
+        // the reference words of the sources: the flow part D_pop of the pulled values and,
+        // in their fourth slot, the temperature references R that re-express g_1 .. g_4
+        // against the node's own R(x)
+        const Q2 q0o = ldq2(Qp, row + kz0, row + zc1, VEC);
+        const V2 rref = q0o.R;
+        {
             const Q2 qmo = ldq2(Qp, rowm + kz0, rowm + zc1, VEC), qml = ldq2(Qp, rowm + zm0, rowm + kz0, false);
             const Q2 qmr = ldq2(Qp, rowm + zp0, rowm + zp1, false);
             fh[1] += fref_delta2(p1, qmo);
             fh[5] += fref_delta2(p5, qml);
             fh[8] += fref_delta2(p8, qmr);
-            const Q2 q0o = ldq2(Qp, row + kz0, row + zc1, VEC), q0l = ldq2(Qp, row + zm0, row + kz0, false);
-            const Q2 q0r = ldq2(Qp, row + zp0, row + zp1, false);
+            gh[1] += 0.1f * (qmo.R - rref);
+            const Q2 q0l = ldq2(Qp, row + zm0, row + kz0, false), q0r = ldq2(Qp, row + zp0, row + zp1, false);
             fh[0] += fref_delta2(0, q0o);
             fh[2] += fref_delta2(2, q0l);
             fh[4] += fref_delta2(4, q0r);
+            gh[2] += 0.1f * (q0l.R - rref);
+            gh[4] += 0.1f * (q0r.R - rref);
             const Q2 qpo = ldq2(Qp, rowp + kz0, rowp + zc1, VEC), qpl = ldq2(Qp, rowp + zm0, rowp + kz0, false);
             const Q2 qpr = ldq2(Qp, rowp + zp0, rowp + zp1, false);
             fh[3] += fref_delta2(3, qpo);
             fh[6] += fref_delta2(6, qpl);
             fh[7] += fref_delta2(7, qpr);
+            gh[3] += 0.1f * (qpo.R - rref);
         }
         const RowC q = row_consts(c, kr);
         V2 lin, nl, iph, m0, rho, ur, uz, dT;
         porous2(c, ph, lin, nl, iph);
-        recover2(c, q, ph, lin, nl, fh, gh, m0, rho, ur, uz, dT);
-        collide2(c, q, ph, lin, nl, iph, fh, gh, m0, rho, ur, uz, dT);
-        const Q2 qo = ldq2(Qp, row + kz0, row + zc1, VEC);
+        recover2(c, q, ph, lin, nl, fh, gh, rref, m0, rho, ur, uz, dT);
+        collide2(c, q, ph, lin, nl, iph, fh, gh, rref, m0, rho, ur, uz, dT);
         auto* __restrict__ Fo = B.f;
         float* __restrict__ Go = B.g;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i] - fref_delta2(i, qo), st0, st1, VEC);
+        for (int i = 0; i < 9; ++i) fh[i] = fh[i] - fref_delta2(i, q0o);
+        if (VEC && st0 && st1) {   // both lanes stored, aligned: one vector store per population
 #pragma unroll
-        for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], st0, st1, VEC);
+            for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i], true, true, true);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], true, true, true);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i], st0, st1, false);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], st0, st1, false);
+        }
     }
 }
 
-// Flow reference of a node from its post-collision deviations d_i = f+_i - rest_i:
-// A = sum d_i, J = sum e_i d_i, P = 1024 / (r rho phi) with rho = 1 + A / r, each clamped to
-// the FP16 range (a clamped or otherwise inexact reference only stores larger values).
-__device__ __forceinline__ uint2 fref_make(float A, float Jr, float Jz, float r, float phi) {
-    const float rho = 1.0f + A / r;
-    const float P = fminf(fmaxf(1024.0f / (r * rho * phi), 0.0f), 60000.0f);
-    auto cl = [](float x) { return fminf(fmaxf(x, -60000.0f), 60000.0f); };
-    return fref_pack(cl(A), cl(Jr), cl(Jz), P);
+// Reference word of a node from its post-collision deviations d_i = f+_i - rest_i
+// (A = sum d_i, J = sum e_i d_i) and its temperature reference R: each rounded to FP16
+// after clamping to its range (a clamped or otherwise inexact reference only stores
+// larger values).
+__device__ __forceinline__ uint2 fref_make(float A, float Jr, float Jz, __half R) {
+    auto h = [](float x) { return __float2half_rn(fminf(fmaxf(x, -60000.0f), 60000.0f)); };
+    return fref_pack(h(A), h(Jr), h(Jz), R);
 }
 
 // One thread per column segment of RPT rows: the column's index arithmetic, the
@@ -467,9 +496,12 @@ __global__ void __launch_bounds__(BULK_THREADS, bulk_min_blocks<STO>()) k_bulk(c
 }
 
 // 16-bit storage: one column pair per thread (2 BULK_THREADS columns per block).
+#ifndef LBM_PAIR_MIN_BLOCKS
+#define LBM_PAIR_MIN_BLOCKS 0
+#endif
 template <int STO, bool VEC, int RPT>
-__global__ void __launch_bounds__(BULK_THREADS) k_bulk_pair(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
-                                                            const __half* __restrict__ phi, int plane) {
+__global__ void __launch_bounds__(BULK_THREADS, LBM_PAIR_MIN_BLOCKS) k_bulk_pair(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
+                                                            const float* __restrict__ phi, int plane) {
     const int kz0 = 2 * (blockIdx.x * BULK_THREADS + threadIdx.x);
     if (kz0 >= c.nz) return;
     update_pair<STO, VEC>(c, A, B, phi, plane, blockIdx.y * RPT, RPT, kz0);
@@ -591,9 +623,8 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
     double fh[9], gh[5];
     minv(mpre, fh);
     // reference offset R(x) = T - T0 in FP16; gh relative to T0 + R(x)
-    const __half Rh = has_ref<STO>() ? __float2half_rn(fminf(fmaxf((float)(T - c.T0), -60000.f), 60000.f))
-                                     : __float2half_rn(0.f);
-    tref[n] = Rh;
+    const __half Rh = __float2half_rn(fminf(fmaxf((float)(T - c.T0), -60000.f), 60000.f));
+    if constexpr (!has_fref<STO>()) tref[n] = Rh;
     const double ref = (double)__half2float(Rh);
     const double dTs = T - c.T0 - ref;
     gh[0] = 0.6 * dTs;
@@ -618,7 +649,7 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
             Jr += ex9(i) * fh[i];
             Jz += ez9(i) * fh[i];
         }
-        const uint2 qw = fref_make((float)A, (float)Jr, (float)Jz, (float)r, (float)ph);
+        const uint2 qw = fref_make((float)A, (float)Jr, (float)Jz, Rh);
         fref[n] = qw;
         const Qf q = fref_unpack(qw);
         for (int i = 0; i < 9; ++i) stv(B.f + i * plane + n, (float)(fh[i] - (double)fref_delta(i, q)));
@@ -630,8 +661,8 @@ __global__ void k_init(const Consts<double> c, const Buf<STO> B,
 
 template <int STO> __device__ __forceinline__ typename St<STO>::P mkp(float v);
 template <> __device__ __forceinline__ float mkp<LBM_F32>(float v) { return v; }
-template <> __device__ __forceinline__ __half mkp<LBM_F16>(float v) { return __float2half_rn(v); }
-template <> __device__ __forceinline__ __half mkp<LBM_BF16>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ float mkp<LBM_F16>(float v) { return v; }
+template <> __device__ __forceinline__ float mkp<LBM_BF16>(float v) { return v; }
 
 // Porosity upload: validate (0 < phi <= 1) and convert to the storage type.
 __device__ __forceinline__ unsigned int bad_phi(float v) { return !(v > 0.f && v <= 1.f); }
@@ -910,44 +941,46 @@ __global__ void k_export(const Consts<float> c, const Buf<STO> A, int64_t plane,
         out[i * P + m] = (double)ldv(A.f + i * plane + n) + ref + (r + 0.5 * ex9(i)) * w9<double>(i);
     }
     const double wt[5] = {0.6, 0.1, 0.1, 0.1, 0.1};
-    const double Tb = T0 + (has_ref<STO>() ? (double)__half2float(c.tref[n]) : 0.0);
+    const double Tb = T0 + (double)tref_at<STO>(c, n);
     for (int i = 0; i < 5; ++i) out[(9 + i) * P + m] = (double)ldv(A.g + i * plane + n) + wt[i] * Tb;
 }
 
 // Reference refresh: R(x) <- FP16(R(x) + sum_i gh_i(x)), gh re-expressed against the
 // new reference (gh_0 += d - 4 d/10, gh_1..4 += d/10 with d = R_old - R_new).  The
 // populations, and every field they give, are unchanged up to rounding.
+template <int STO, typename I>
+__device__ __forceinline__ void rebase_thermal_node(const Buf<STO>& A, I plane, I n, __half* __restrict__ tref) {
+    float g[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = ldv(A.g + i * plane + n);
+    const float r_old = __half2float(tref[n]);
+    const float t = r_old + (((g[0] + g[1]) + (g[2] + g[3])) + g[4]);
+    const __half h = __float2half_rn(fminf(fmaxf(t, -60000.f), 60000.f));
+    const float d = r_old - __half2float(h), d1 = 0.1f * d;
+    g[0] += d - 4.f * d1;
+#pragma unroll
+    for (int i = 1; i < 5; ++i) g[i] += d1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) stv(A.g + i * plane + n, g[i]);
+    tref[n] = h;
+}
+
 template <int STO>
 __global__ void k_rebase(const Buf<STO> A, int64_t plane, int64_t N, __half* __restrict__ tref) {
     if constexpr (has_ref<STO>()) {
-        for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-            float g[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) g[i] = ldv(A.g + i * plane + n);
-            const float r_old = __half2float(tref[n]);
-            const float t = r_old + (((g[0] + g[1]) + (g[2] + g[3])) + g[4]);
-            const __half h = __float2half_rn(fminf(fmaxf(t, -60000.f), 60000.f));
-            const float d = r_old - __half2float(h), d1 = 0.1f * d;
-            g[0] += d - 4.f * d1;
-#pragma unroll
-            for (int i = 1; i < 5; ++i) g[i] += d1;
-#pragma unroll
-            for (int i = 0; i < 5; ++i) stv(A.g + i * plane + n, g[i]);
-            tref[n] = h;
-        }
+        for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
+            rebase_thermal_node<STO, int64_t>(A, plane, n, tref);
     }
 }
 
-// Flow reference refresh (16-bit storage) of node n in row kr: decode its flow
-// populations with the old Q (as the pull does), take the new Q from their deviation
-// moments (fref_make) and re-encode against it.  The populations, and every field they
-// give, are unchanged up to the storage type's rounding of the re-encoded (now small)
-// values.
+// Reference refresh (16-bit storage) of node n: decode its flow populations with the old
+// reference word (as the pull does), take the new A, J from their deviation moments and the
+// new R from the node's temperature (as rebase_thermal_node does), re-express the thermal
+// deviations against the new R and re-encode the flow populations against the new A, J.
+// The populations, and every field they give, are unchanged up to the storage rounding of
+// the re-encoded (now small) values.
 template <int STO, typename I>
-__device__ __forceinline__ void rebase_flow_node(const Consts<float>& c, const Buf<STO>& S,
-                                                 const typename St<STO>::P* __restrict__ phi, I plane, I n, int kr,
-                                                 uint2* __restrict__ fref) {
-    const float r = c.r0 + float(kr);
+__device__ __forceinline__ void rebase_16_node(const Buf<STO>& S, I plane, I n, uint2* __restrict__ fref) {
     const Qf q0 = fref_unpack(fref[n]);
     float d[9];
 #pragma unroll
@@ -955,7 +988,18 @@ __device__ __forceinline__ void rebase_flow_node(const Consts<float>& c, const B
     const float a = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     const float jr = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
     const float jz = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
-    const uint2 qw = fref_make(a, jr, jz, r, ldv(phi + n));
+    float g[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = ldv(S.g + i * plane + n);
+    const float t = q0.R + (((g[0] + g[1]) + (g[2] + g[3])) + g[4]);
+    const __half h = __float2half_rn(fminf(fmaxf(t, -60000.f), 60000.f));
+    const float dr = q0.R - __half2float(h), dr1 = 0.1f * dr;
+    g[0] += dr - 4.f * dr1;
+#pragma unroll
+    for (int i = 1; i < 5; ++i) g[i] += dr1;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) stv(S.g + i * plane + n, g[i]);
+    const uint2 qw = fref_make(a, jr, jz, h);
     const Qf q1 = fref_unpack(qw);
 #pragma unroll
     for (int i = 0; i < 9; ++i) stv(S.f + i * plane + n, d[i] - fref_delta(i, q1));
@@ -963,11 +1007,10 @@ __device__ __forceinline__ void rebase_flow_node(const Consts<float>& c, const B
 }
 
 template <int STO>
-__global__ void k_rebase_flow(const Consts<float> c, const Buf<STO> S, const typename St<STO>::P* __restrict__ phi,
-                              int64_t plane, int64_t N, uint2* __restrict__ fref) {
+__global__ void k_rebase_16(const Buf<STO> S, int64_t plane, int64_t N, uint2* __restrict__ fref) {
     if constexpr (has_fref<STO>()) {
         for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
-            rebase_flow_node<STO, int64_t>(c, S, phi, plane, n, (int)(n / c.nz), fref);
+            rebase_16_node<STO, int64_t>(S, plane, n, fref);
     }
 }
 
@@ -1083,8 +1126,9 @@ static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
     o->T0 = p->heater_len > 0 ? p->T_cold : 0.5 * (p->T_hot + p->T_cold);   // Sec. 4.4: T0 = T_o
     o->Kbar = p->Da * o->L * o->L;
     const int64_t N = (int64_t)p->nr * p->nz;
-    // populations read and written, porosity, and the reference each node's pull reads:
-    // R(x) (FP16) with FP32 storage, Q(x) (4 x FP16) with 16-bit storage
+    // populations read and written, porosity, and the references each node's pull reads:
+    // R(x) (FP16) with FP32 storage, the reference word (A, J_r, J_z, R; 4 x FP16) with 16-bit
+    // storage
     o->bytes_per_step = N * (int64_t)(2 * (9 * f_size(p->storage) + 5 * g_size(p->storage)) + phi_size(p->storage) +
                                       (p->storage == LBM_F32 ? sizeof(__half) : sizeof(uint2)));
     if (cd) {
@@ -1204,17 +1248,13 @@ static int wait_phi(lbm_handle* h) {
         h->phi_pending = -1;
         CK(cudaStreamWaitEvent(h->stream, h->copied[i], 0));
         const unsigned blocks = phi_blocks(h->N);
-        if (h->p.storage == LBM_F32) {
-            // same element type: check the staging buffer and swap it with the field; the
-            // old field becomes staging buffer i once the work queued before has read it
-            k_phi_check<<<blocks, 256, 0, h->stream>>>(h->astage[i], h->N, h->bad_async);
-            void* old = h->phi;
-            h->phi = h->astage[i];
-            h->astage[i] = (float*)old;
-        } else {
-            DISPATCH_STO(h->p.storage, k_phi<S_><<<blocks, 256, 0, h->stream>>>(h->astage[i], (PP<S_>*)h->phi, h->N,
-                                                                                 1, h->bad_async));
-        }
+        // the field is FP32 for every storage type: check the staging buffer and swap it with
+        // the field; the old field becomes staging buffer i once the work queued before has
+        // read it
+        k_phi_check<<<blocks, 256, 0, h->stream>>>(h->astage[i], h->N, h->bad_async);
+        void* old = h->phi;
+        h->phi = h->astage[i];
+        h->astage[i] = (float*)old;
         CK(cudaGetLastError());
         CK(cudaEventRecord(h->consumed[i], h->stream));
     }
@@ -1321,10 +1361,11 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     } while (0)
     ALLOC(h->buf[0], state_bytes(p->storage, h->plane));
     ALLOC(h->buf[1], state_bytes(p->storage, h->plane));
-    ALLOC(h->tref, h->plane * sizeof(__half));
-    h->cd.tref = h->tref;
-    h->cf.tref = h->tref;
-    if (p->storage != LBM_F32) {
+    if (p->storage == LBM_F32) {
+        ALLOC(h->tref, h->plane * sizeof(__half));
+        h->cd.tref = h->tref;
+        h->cf.tref = h->tref;
+    } else {
         ALLOC(h->fref, h->plane * sizeof(uint2));
         h->cd.fref = h->fref;
         h->cf.fref = h->fref;
@@ -1494,7 +1535,7 @@ static int launch_step(lbm_handle* h) {
         DISPATCH_STO16(h->p.storage, {
             auto A = bufp<S_>(h, h->cur);
             auto B = bufp<S_>(h, h->cur ^ 1);
-            const __half* ph = (const __half*)h->phi;
+            const float* ph = (const float*)h->phi;
             if (vec && rpt > 1) k_bulk_pair<S_, true, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
             else if (vec) k_bulk_pair<S_, true, 1><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
             else if (rpt > 1) k_bulk_pair<S_, false, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
@@ -1775,16 +1816,15 @@ int lbm_stream_function(lbm_handle* h, float* psi, int on_device, double* psi_ma
     return LBM_OK;
 }
 
-// Refresh the reference of the current state: the temperature reference R(x) with FP32
-// storage, the flow reference Q(x) with 16-bit storage.
+// Refresh the references of the current state: the temperature reference R(x) with FP32
+// storage, the reference word (A, J, R) with 16-bit storage.
 static int launch_rebase(lbm_handle* h) {
-    if (int rc = wait_phi(h)) return rc;
     const unsigned blocks = (unsigned)std::min<int64_t>((h->N + 255) / 256, (int64_t)h->sms * 16);
     if (h->p.storage == LBM_F32) {
         k_rebase<LBM_F32><<<blocks, 256, 0, h->stream>>>(bufp<LBM_F32>(h, h->cur), h->plane, h->N, h->tref);
     } else {
-        DISPATCH_STO16(h->p.storage, k_rebase_flow<S_><<<blocks, 256, 0, h->stream>>>(
-                                         h->cf, bufp<S_>(h, h->cur), (const PP<S_>*)h->phi, h->plane, h->N, h->fref));
+        DISPATCH_STO16(h->p.storage, k_rebase_16<S_><<<blocks, 256, 0, h->stream>>>(bufp<S_>(h, h->cur), h->plane,
+                                                                                   h->N, h->fref));
     }
     CK(cudaGetLastError());
     h->since_rebase = 0;
@@ -1999,7 +2039,10 @@ __device__ __forceinline__ Buf<STO> inst_buf(const InstDesc& d, char* pool, int 
 // one with FP32 storage.
 template <int STO> __host__ __device__ constexpr int bulk_cols() { return has_fref<STO>() ? 2 : 1; }
 
-template <int STO, int RPT>
+// VEC (16-bit storage): every tile of the launch belongs to an instance with even nz, so
+// the pair update may use its vector loads; tiles of odd-nz instances go to a VEC = false
+// launch (batch_rebuild orders them last).
+template <int STO, int RPT, bool VEC>
 __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__ desc, char* __restrict__ pool,
                                                     int parity, const int4* __restrict__ tiles) {
     const int4 t = tiles[blockIdx.x];
@@ -2011,8 +2054,7 @@ __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__
     const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
     const int plane = (int)d.plane;
     if constexpr (has_fref<STO>()) {
-        if ((c.nz & 1) == 0) update_pair<STO, true>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
-        else update_pair<STO, false>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
+        update_pair<STO, VEC>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
     } else {
         update_column<STO, int>(c, A, B, phi, plane, t.y + threadIdx.y * RPT, RPT, kz);
     }
@@ -2028,7 +2070,6 @@ __global__ void __launch_bounds__(256) k_batch_rebase_flow(const InstDesc* __res
         const InstDesc& d = desc[t.x];
         const Consts<float> c = d.c;
         const Buf<STO> S = inst_buf<STO>(d, pool, parity);
-        const typename St<STO>::P* phi = (const typename St<STO>::P*)(pool + d.off_phi);
         uint2* fref = (uint2*)(pool + d.off_fref);
 #pragma unroll 1
         for (int q = 0; q < RPT * bulk_cols<STO>(); ++q) {
@@ -2036,7 +2077,7 @@ __global__ void __launch_bounds__(256) k_batch_rebase_flow(const InstDesc* __res
             const int kz = t.z + bulk_cols<STO>() * threadIdx.x + q % bulk_cols<STO>();
             if (kr >= c.nr) break;
             if (kz >= c.nz) continue;
-            rebase_flow_node<STO, int>(c, S, phi, (int)d.plane, kr * c.nz + kz, kr, fref);
+            rebase_16_node<STO, int>(S, (int)d.plane, kr * c.nz + kz, fref);
         }
     }
 }
@@ -2203,6 +2244,7 @@ struct lbm_batch {
     int bz = 128, rows = 1, rpt = 1;  // bulk block shape and rows per thread
     int4* d_tiles = nullptr;          // active instances, all rows
     int ntiles = 0;
+    int ntiles_even = 0;              // leading tiles of instances with even nz
     int* d_active = nullptr;
     int* d_prefix = nullptr;
     int nactive = 0;
@@ -2227,16 +2269,19 @@ static void batch_free_graph(lbm_batch* b) {
 // Rebuild the tile list, the active list and the wall prefix for the current active
 // set and block shape.
 static int batch_rebuild(lbm_batch* b) {
-    std::vector<int4> tiles;
+    std::vector<int4> tiles, odd;   // tiles of instances with odd nz last (k_batch_bulk's VEC)
     std::vector<int> act, prefix(1, 0);
     for (int i = 0; i < b->n; ++i) {
         if (!b->active[i]) continue;
         act.push_back(i);
         prefix.push_back(prefix.back() + wall_count(b->p[i].geometry, b->p[i].nr, b->p[i].nz));
         const int zstep = b->bz * (b->storage == LBM_F32 ? 1 : 2);   // columns of a tile (bulk_cols)
+        std::vector<int4>& dst = (b->p[i].nz & 1) ? odd : tiles;
         for (int kr = 0; kr < b->p[i].nr; kr += b->rows * b->rpt)
-            for (int z0 = 0; z0 < b->p[i].nz; z0 += zstep) tiles.push_back(make_int4(i, kr, z0, 0));
+            for (int z0 = 0; z0 < b->p[i].nz; z0 += zstep) dst.push_back(make_int4(i, kr, z0, 0));
     }
+    b->ntiles_even = (int)tiles.size();
+    tiles.insert(tiles.end(), odd.begin(), odd.end());
     b->ntiles = (int)tiles.size();
     b->nactive = (int)act.size();
     b->nwall = prefix.back();
@@ -2283,8 +2328,18 @@ static int batch_launch_step(lbm_batch* b) {
     if (b->storage != LBM_F32 && b->since_rebase >= LBM_FREF_EVERY)
         if (int rc = batch_launch_rebase_flow(b)) return rc;
     const dim3 blk(b->bz, b->rows);
-    DISPATCH_STO(b->storage, DISPATCH_RPT(b->rpt, k_batch_bulk<S_, R_><<<b->ntiles, blk, 0, b->stream>>>(
-                                                       b->d_desc, b->pool, b->parity, b->d_tiles)));
+    if (b->storage == LBM_F32) {
+        DISPATCH_RPT(b->rpt, k_batch_bulk<LBM_F32, R_, false><<<b->ntiles, blk, 0, b->stream>>>(
+                                 b->d_desc, b->pool, b->parity, b->d_tiles));
+    } else {
+        const int ne = b->ntiles_even, no = b->ntiles - b->ntiles_even;
+        if (ne)
+            DISPATCH_STO16(b->storage, DISPATCH_RPT(b->rpt, k_batch_bulk<S_, R_, true><<<ne, blk, 0, b->stream>>>(
+                                                                b->d_desc, b->pool, b->parity, b->d_tiles)));
+        if (no)
+            DISPATCH_STO16(b->storage, DISPATCH_RPT(b->rpt, k_batch_bulk<S_, R_, false><<<no, blk, 0, b->stream>>>(
+                                                                b->d_desc, b->pool, b->parity, b->d_tiles + ne)));
+    }
     CK(cudaGetLastError());
     DISPATCH_STO(b->storage, k_batch_wall<S_><<<(b->nwall + 127) / 128, 128, 0, b->stream>>>(
                                  b->d_desc, b->pool, b->parity, b->d_active, b->d_prefix, b->nactive));
@@ -2341,10 +2396,9 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
         state_off += (int64_t)state_bytes(b->storage, plane);
         d.off_phi = state_off;
         state_off += (plane * (int64_t)phi_size(b->storage) + 255) / 256 * 256;
-        d.off_tref = state_off;
-        state_off += (plane * (int64_t)sizeof(__half) + 255) / 256 * 256;
+        d.off_tref = state_off;   // R(x) plane (FP32 storage) or reference words (16-bit storage)
         d.off_fref = state_off;
-        if (p[i].storage != LBM_F32) state_off += (plane * (int64_t)sizeof(uint2) + 255) / 256 * 256;
+        state_off += (plane * (int64_t)(p[i].storage == LBM_F32 ? sizeof(__half) : sizeof(uint2)) + 255) / 256 * 256;
         d.off_mac = mac_off;
         mac_off += 8 * plane;
         d.r0 = b->info[i].r0;
@@ -2360,8 +2414,9 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->pool, state_off);
     if (e == cudaSuccess)
         for (int i = 0; i < n; ++i) {
-            b->desc[i].c.tref = (const __half*)(b->pool + b->desc[i].off_tref);
-            b->cd[i].tref = b->desc[i].c.tref;
+            const __half* tr = b->storage == LBM_F32 ? (const __half*)(b->pool + b->desc[i].off_tref) : nullptr;
+            b->desc[i].c.tref = tr;
+            b->cd[i].tref = tr;
             const uint2* fr = b->storage == LBM_F32 ? nullptr : (const uint2*)(b->pool + b->desc[i].off_fref);
             b->desc[i].c.fref = fr;
             b->cd[i].fref = fr;
@@ -2491,9 +2546,8 @@ static int batch_rebase_one(lbm_batch* b, int i) {
         k_rebase<LBM_F32><<<blocks, 256, 0, b->stream>>>(batch_buf<LBM_F32>(b, i, b->cur_parity(i)), d.plane, N,
                                                          (__half*)(b->pool + d.off_tref));
     } else {
-        DISPATCH_STO16(b->storage, k_rebase_flow<S_><<<blocks, 256, 0, b->stream>>>(
-                                       d.c, batch_buf<S_>(b, i, b->cur_parity(i)), (const PP<S_>*)(b->pool + d.off_phi),
-                                       d.plane, N, (uint2*)(b->pool + d.off_fref)));
+        DISPATCH_STO16(b->storage, k_rebase_16<S_><<<blocks, 256, 0, b->stream>>>(
+                                       batch_buf<S_>(b, i, b->cur_parity(i)), d.plane, N, (uint2*)(b->pool + d.off_fref)));
     }
     CK(cudaGetLastError());
     return LBM_OK;

@@ -7,14 +7,13 @@
 // 33-38); only the evaluation order differs where a multiply-add is written as one fused
 // instruction.
 //
-// Flow reference of 16-bit storage (the same encoding as lbm_physics.cuh's scalar
+// Flow reference of 16-bit storage (the encoding of lbm_physics.cuh's scalar
 // fref_delta): the stored value of population i at node y is
-//     s_i(y) = f+_i(y) - (r w_i + e_ir w_i / 2) - D_i(Q(y)),
-//     D_i(Q) = w_i [A + 3 e_i.J + (4.5 (e_i.J)^2 - 1.5 |J|^2) P / 1024],
-// with Q(y) = (A, J_r, J_z, P) held in FP16 per node (A = sum of the deviations, J their
-// e-weighted sums, P = 1024 / (r rho phi)), refreshed by the rebase kernel.  fref_delta2
-// evaluates D with the same sequence of rounded operations as the scalar version, so a
-// value encoded by one and decoded by the other is unchanged.
+//     s_i(y) = f+_i(y) - (r w_i + e_ir w_i / 2) - D_i(Q(y)),   D_i(Q) = w_i (A + 3 e_i.J),
+// with (A, J_r, J_z) = (sum of the deviations, their e-weighted sums) of the node in FP16,
+// refreshed by the rebase kernel.  fref_delta2 evaluates D with the same sequence of
+// rounded operations as the scalar version (fma(eJ, 3, A) then the weight), so a value
+// encoded by one and decoded by the other is unchanged.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -56,13 +55,26 @@ __device__ __forceinline__ V2 fma2(V2 a, V2 b, float c) { return fma2(a, b, v2(c
 __device__ __forceinline__ V2 fma2(V2 a, float b, float c) { return fma2(a, v2(b), v2(c)); }
 __device__ __forceinline__ V2 fma2(float a, V2 b, float c) { return fma2(v2(a), b, v2(c)); }
 
-// lane-wise versions of the scalar reciprocal and square root of lbm_physics.cuh
-__device__ __forceinline__ V2 rcp_fast(V2 x) { return v2(rcp_fast(x.v.x), rcp_fast(x.v.y)); }
+// Lane-wise reciprocal and square root: the hardware approximations (rcp.approx and
+// sqrt.approx, one instruction each; sqrt(0) = 0, so no guard is needed), where the scalar
+// path of lbm_physics.cuh goes through __fdividef and x rsqrt(x) with their range checks.
+// rcp_acc adds one Newton step, as the scalar rcp_acc does.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ V2 rcp_fast(V2 x) { return v2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
 __device__ __forceinline__ V2 rcp_acc(V2 x) {
     const V2 y = rcp_fast(x);
     return fma2(y, fma2(-x, y, 1.0f), y);
 }
-__device__ __forceinline__ V2 sqrt_fast(V2 x) { return v2(sqrt_fast(x.v.x), sqrt_fast(x.v.y)); }
+__device__ __forceinline__ V2 sqrt_fast(V2 x) { return v2(sqrt_approx(x.v.x), sqrt_approx(x.v.y)); }
 
 // Row constants of the recovery and collision, shared by both lanes.
 struct RowC {
@@ -108,28 +120,26 @@ __device__ __forceinline__ void porous2(const Consts<float>& c, V2 phi, V2& lin,
     }
 }
 
-// recover() of lbm_physics.cuh (Eq. 26-30, 38) for two nodes; temperature relative to T0
-// (16-bit storage keeps no temperature reference).
+// recover() of lbm_physics.cuh (Eq. 26-30, 38) for two nodes; dT is relative to each
+// node's reference temperature T0 + R(x), rref = R(x).
 __device__ __forceinline__ void recover2(const Consts<float>& c, const RowC& q, V2 phi, V2 lin, V2 nl, const V2* fh,
-                                         const V2* gh, V2& m0, V2& rho, V2& ur, V2& uz, V2& dT) {
+                                         const V2* gh, V2 rref, V2& m0, V2& rho, V2& ur, V2& uz, V2& dT) {
     dT = ((gh[0] + gh[1]) + (gh[2] + gh[3])) + gh[4];
     m0 = ((fh[0] + fh[1]) + (fh[2] + fh[3])) + ((fh[4] + fh[5]) + (fh[6] + fh[7])) + fh[8];
     rho = fma2(m0, q.inv_r, 1.0f);
     const V2 jr = ((fh[1] - fh[3]) + (fh[5] - fh[6])) + (fh[8] - fh[7]);
     const V2 jz = ((fh[2] - fh[4]) + (fh[5] + fh[6])) - (fh[7] + fh[8]);
-    const V2 Gz = fma2(v2(c.gbeta), dT, v2(c.az));
+    const V2 Gz = fma2(v2(c.gbeta), dT + rref, v2(c.az));
     const V2 inv_rho = rcp_acc(rho);
     const V2 vr = fma2(m0, q.c1, jr) * inv_rho;
     const V2 vz = fma2(jz, inv_rho, (q.hr * phi) * Gz);
     const V2 hd = (q.qr * phi) * lin;
     const V2 lr0 = q.L0r + hd;
     const V2 lz0 = q.hr + hd;
-    V2 Dr = lr0 + lr0, Dz = lz0 + lz0;
-    if (nl.v.x != 0.f || nl.v.y != 0.f) {
-        const V2 x = (q.hr * phi) * nl * sqrt_fast(fma2(vr, vr, vz * vz));
-        Dr += x * rcp_fast(lr0 + sqrt_fast(fma2(lr0, lr0, x)));
-        Dz += x * rcp_fast(lz0 + sqrt_fast(fma2(lz0, lz0, x)));
-    }
+    // Eq. 28 as in recover(), without a branch: x = 0 (no Forchheimer drag) adds 0
+    const V2 x = (q.hr * phi) * nl * sqrt_fast(fma2(vr, vr, vz * vz));
+    const V2 Dr = fma2(x, rcp_fast(lr0 + sqrt_fast(fma2(lr0, lr0, x))), lr0 + lr0);
+    const V2 Dz = fma2(x, rcp_fast(lz0 + sqrt_fast(fma2(lz0, lz0, x))), lz0 + lz0);
     ur = vr * rcp_acc(Dr);
     uz = vz * rcp_acc(Dz);
 }
@@ -154,14 +164,14 @@ __device__ __forceinline__ void minv2(const V2* m, V2* f) {
     f[8] = ((b58 + y3) - y5) - a8;
 }
 
-// collide() of lbm_physics.cuh (Eq. 6, 21-25, 33-37) for two nodes, in place; no
-// temperature reference (rref = 0).
+// collide() of lbm_physics.cuh (Eq. 6, 21-25, 33-37) for two nodes, in place; rref = R(x).
 __device__ __forceinline__ void collide2(const Consts<float>& c, const RowC& q, V2 phi, V2 lin, V2 nl, V2 inv_phi,
-                                         V2* fh, V2* gh, V2 m0, V2 rho, V2 ur, V2 uz, V2 dT) {
-    const V2 T = c.T0 + dT;
+                                         V2* fh, V2* gh, V2 rref, V2 m0, V2 rho, V2 ur, V2 uz, V2 dT) {
+    const V2 Tb = c.T0 + rref;   // the nodes' reference temperatures
+    const V2 T = Tb + dT;
     const V2 u2 = fma2(ur, ur, uz * uz);
     const V2 um = sqrt_fast(u2);
-    const V2 Gz = fma2(v2(c.gbeta), dT, v2(c.az));
+    const V2 Gz = fma2(v2(c.gbeta), dT + rref, v2(c.az));
     const V2 drag = fma2(nl, um, lin);
     const V2 pd = phi * drag;
     const V2 Fr = -(pd * ur);
@@ -209,7 +219,7 @@ __device__ __forceinline__ void collide2(const Consts<float>& c, const RowC& q, 
     minv2(dm, df);
 #pragma unroll
     for (int i = 0; i < 9; ++i) fh[i] += df[i];
-    // D2Q5 (Eq. 33, 35-37), relative to T0
+    // D2Q5 (Eq. 33, 35-37), relative to T0 + R(x)
     const V2 wd = v2(c.wg_den);
     const V2 cu = -(ur * q.inv_r);
     const V2 hT = 0.5f * T;
@@ -218,7 +228,7 @@ __device__ __forceinline__ void collide2(const Consts<float>& c, const RowC& q, 
     const V2 g1e = t1 + Tr, g3e = t1 - Tr;
     const V2 g2e = t1 + Tz, g4e = t1 - Tz;
     const V2 g0e = fma2(t1, -4.0f, dT);
-    const float wT0 = 0.6f * c.T0, wT1 = 0.1f * c.T0;
+    const V2 wT0 = 0.6f * Tb, wT1 = 0.1f * Tb;
     const V2 wp = (1.0f + q.kT) * wd, wm = (1.0f - q.kT) * wd;
     gh[0] = fma2(cu, g0e + wT0, fma2(-wd, gh[0] - g0e, gh[0]));
     gh[1] = fma2(cu, g1e + wT1, fma2(-wp, gh[1] - g1e, gh[1]));
@@ -228,9 +238,9 @@ __device__ __forceinline__ void collide2(const Consts<float>& c, const RowC& q, 
 }
 
 // ------------------------------------------------------ flow reference, packed --
-// Q of two nodes as floats: (A, J_r, J_z, P / 1024) per lane.
+// Q of two nodes as floats: (A, J_r, J_z, R) per lane.
 struct Q2 {
-    V2 A, Jr, Jz, Pn;
+    V2 A, Jr, Jz, R;
 };
 
 // D_i(Q) for both lanes, in the rounded operations of fref_delta (lbm_physics.cuh).
@@ -247,10 +257,7 @@ __device__ __forceinline__ V2 fref_delta2(int i, const Q2& Q) {
         case 7: eJ = -(Q.Jr + Q.Jz); break;
         default: eJ = -(Q.Jz - Q.Jr); break;
     }
-    const V2 JJ = fma2(Q.Jr, Q.Jr, Q.Jz * Q.Jz);
-    const V2 lin = fma2(eJ, 3.0f, Q.A);
-    const V2 quad = fma2(4.5f * eJ, eJ, -(1.5f * JJ));
-    return w9<float>(i) * fma2(quad, Q.Pn, lin);
+    return w9<float>(i) * fma2(eJ, 3.0f, Q.A);
 }
 
 }  // namespace lbm

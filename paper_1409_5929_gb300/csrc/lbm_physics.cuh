@@ -53,7 +53,7 @@ struct Consts {
     R u_in;               // inlet velocity (PIPE_INFLOW)
     R hG;                 // heater gradient q' / k = (T_hot - T_cold) / L
     const __half* tref;   // per-node reference offset R(x) (FP16, one plane)
-    const uint2* fref;    // per-node flow reference Q(x) of 16-bit storage (4 x FP16, see fref_delta)
+    const uint2* fref;    // per-node references of 16-bit storage (A, J_r, J_z, R in FP16, see fref_delta)
 };
 
 template <typename R> __host__ __device__ constexpr R cs2() { return R(1) / R(3); }
@@ -314,31 +314,32 @@ __device__ __forceinline__ void rebuild_thermal(R Tf0, R dTf, R Tb0, R dTb, R ur
     gh[4] = ghf[4] + (t1 + tz - bz);
 }
 
-// Flow reference of 16-bit storage.  A 16-bit population stored against the rest state
+// References of 16-bit storage.  A 16-bit population stored against the rest state
 // rounds at 2^-11 (FP16) or 2^-8 (BF16) of its deviation r w_i (3 e_i.u + ...), whose
 // rounding jitter keeps convective runs from settling.  It is therefore stored against a
 // per-node reference equilibrium instead:
-//     s_i(y) = f+_i(y) - (r w_i + e_ir w_i / 2) - D_i(Q(y)),
-//     D_i(Q) = w_i [A + 3 e_i.J + (4.5 (e_i.J)^2 - 1.5 |J|^2) P / 1024],
-// the deviation part of Eq. 32's r-weighted f_eq written with A = r (rho - 1), J = r rho u
-// and P / 1024 = 1 / (r rho phi), all four held in FP16 per node (one 8-byte word) and
-// refreshed from the state by the rebase kernel.  The stored s_i then carry only the
-// non-equilibrium part and the change since the last refresh.  Encoding and decoding use
-// the same D_i(Q(y)) of the node y that wrote the value; they evaluate it in this fixed
-// sequence of round-to-nearest operations (fref_delta2 in lbm_pair.cuh repeats it lane by
-// lane), so the reference cancels exactly and any Q is a valid (if less effective) one.
+//     s_i(y) = f+_i(y) - (r w_i + e_ir w_i / 2) - D_i(Q(y)),   D_i(Q) = w_i (A + 3 e_i.J),
+// the part of Eq. 32's r-weighted f_eq linear in the deviations, with A = r (rho - 1) and
+// J = r rho u of the node held in FP16 and refreshed from the state by the rebase kernel.
+// The stored s_i then carry the second-order part of f_eq, the non-equilibrium part and
+// the change since the last refresh.  The fourth FP16 of the node's 8-byte reference word
+// is its temperature reference R(x) (see the thermal deviations above), so one load gives
+// both.  Encoding and decoding use the same D_i(Q(y)) of the node y that wrote the value,
+// evaluated in this fixed sequence of round-to-nearest operations (fref_delta2 in
+// lbm_pair.cuh repeats it lane by lane), so the reference cancels exactly and any Q is a
+// valid (if less effective) one.
 struct Qf {
-    float A, Jr, Jz, Pn;   // Pn = P / 1024
+    float A, Jr, Jz, R;
 };
 
 __device__ __forceinline__ Qf fref_unpack(uint2 u) {
     const __half2 a = *reinterpret_cast<const __half2*>(&u.x), b = *reinterpret_cast<const __half2*>(&u.y);
     const float2 fa = __half22float2(a), fb = __half22float2(b);
-    return {fa.x, fa.y, fb.x, fb.y * (1.0f / 1024.0f)};
+    return {fa.x, fa.y, fb.x, fb.y};
 }
 
-__device__ __forceinline__ uint2 fref_pack(float A, float Jr, float Jz, float P) {
-    const __half2 a = __floats2half2_rn(A, Jr), b = __floats2half2_rn(Jz, P);
+__device__ __forceinline__ uint2 fref_pack(__half A, __half Jr, __half Jz, __half R) {
+    const __half2 a = __halves2half2(A, Jr), b = __halves2half2(Jz, R);
     uint2 u;
     u.x = *reinterpret_cast<const uint32_t*>(&a);
     u.y = *reinterpret_cast<const uint32_t*>(&b);
@@ -358,10 +359,7 @@ __device__ __forceinline__ float fref_delta(int i, const Qf& q) {
         case 7: eJ = -__fadd_rn(q.Jr, q.Jz); break;
         default: eJ = -__fsub_rn(q.Jz, q.Jr); break;
     }
-    const float JJ = __fmaf_rn(q.Jr, q.Jr, __fmul_rn(q.Jz, q.Jz));
-    const float lin = __fmaf_rn(eJ, 3.0f, q.A);
-    const float quad = __fmaf_rn(__fmul_rn(4.5f, eJ), eJ, -__fmul_rn(1.5f, JJ));
-    return __fmul_rn(w9<float>(i), __fmaf_rn(quad, q.Pn, lin));
+    return __fmul_rn(w9<float>(i), __fmaf_rn(eJ, 3.0f, q.A));
 }
 
 }  // namespace lbm

@@ -1,18 +1,17 @@
 """Emulation of the 16-bit storage codec on the FP64 oracle (test helper).
 
 The CUDA path stores each flow population as
-    s_i = f+_i - (r w_i + e_ir w_i / 2) - D_i(Q),
-    D_i(Q) = w_i [A + 3 e_i.J + (4.5 (e_i.J)^2 - 1.5 |J|^2) P / 1024],
-rounded to FP16 (or BF16), with the per-node reference Q = (A, J_r, J_z, P) itself held in
-FP16: A and J the sum and e-weighted sums of the node's post-collision deviations
-f+_i - rest_i, P = 1024 / (r rho phi), rho = 1 + A / r.  Q is taken from the start state
-and refreshed from the state every `refresh` steps.  Temperature populations are kept in
-FP32 against w~_i T0.  This module reproduces that storage around the oracle's FP64 step:
-after the start state and after every step the stored values are rounded as the GPU
-rounds them, so the emulated run carries the codec's error and nothing else.
+    s_i = f+_i - (r w_i + e_ir w_i / 2) - D_i,   D_i = w_i (A + 3 e_i.J),
+rounded to FP16 (or BF16), with the node's reference A = sum of the post-collision
+deviations f+_i - rest_i and J their e-weighted sums, both held in FP16; the temperature
+populations in FP32 as g+_i - w~_i (T0 + R), with R = T - T0 of the node in FP16.  The
+references come from the start state and are refreshed from the state every `refresh`
+steps.  This module reproduces that storage around the oracle's FP64 step: after the
+start state and after every step the stored values are rounded as the GPU rounds them,
+so the emulated run carries the codec's error and nothing else.
 
-The equilibrium written out here is Eq. 32's deviation part; the codec is a storage
-choice of the GPU path, not part of the paper's method.
+The linear part of Eq. 32's equilibrium written out here is the codec's reference, a
+storage choice of the GPU path, not part of the paper's method.
 """
 import numpy as np
 
@@ -53,32 +52,25 @@ class Emulated16:
         self.refresh = refresh
         self.reference = reference
         c = oracle.derive(p)
+        self.T0 = c["T0"]
         self.r = c["r0"] + np.arange(p.nr)
         self.rest_f = self.r[None, :, None] * W9[:, None, None] + (0.5 * EX * W9)[:, None, None]
-        self.rest_g = (WT * c["T0"])[:, None, None]
         self.since = 0
-        self.Q = None
         self._make_reference()
         self._store()
 
     def _make_reference(self):
+        T = self.st.g.sum(0)
+        self.R = round_f16(np.clip(T - self.T0, -60000, 60000))
+        self.rest_g = WT[:, None, None] * (self.T0 + self.R)[None]
         if not self.reference:
             self.ref = np.zeros_like(self.st.f)
             return
         d = self.st.f - self.rest_f
-        A = d.sum(0)
-        Jr = np.tensordot(EX, d, 1)
-        Jz = np.tensordot(EZ, d, 1)
-        r = self.r[:, None]
-        rho = 1 + A / r
-        with np.errstate(divide="ignore", invalid="ignore"):
-            P = np.clip(np.nan_to_num(1024.0 / (r * rho * self.st.phi), nan=0.0, posinf=60000.0), 0, 60000)
-        A, Jr, Jz = (np.clip(x, -60000, 60000) for x in (A, Jr, Jz))
-        A, Jr, Jz, P = (round_f16(x) for x in (A, Jr, Jz, P))
+        A, Jr, Jz = (round_f16(np.clip(x, -60000, 60000))
+                     for x in (d.sum(0), np.tensordot(EX, d, 1), np.tensordot(EZ, d, 1)))
         eJ = EX[:, None, None] * Jr[None] + EZ[:, None, None] * Jz[None]
-        quad = 4.5 * eJ * eJ - 1.5 * (Jr * Jr + Jz * Jz)[None]
-        self.ref = W9[:, None, None] * (A[None] + 3 * eJ + quad * (P / 1024.0)[None])
-        self.Q = (A, Jr, Jz, P)
+        self.ref = W9[:, None, None] * (A[None] + 3 * eJ)
 
     def _store(self):
         base = self.rest_f + self.ref

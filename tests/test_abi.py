@@ -66,9 +66,9 @@ def test_derivation_matches_oracle(lbm, oracle, kw):
                          ("nu_e", "nu_e"), ("nu", "nu"), ("gbeta", "gbeta"), ("T0", "T0"), ("Kbar", "Kbar")):
         assert np.isclose(getattr(info, k_lib), ref[k_ref], rtol=1e-14, atol=0), k_lib
     ef = 4 if p.storage == 0 else 2           # flow populations; temperature populations stay FP32
-    # populations read and written, porosity, and the reference a pull reads: the FP16
-    # temperature offset with FP32 storage, the 4 x FP16 flow reference with 16-bit storage
-    assert info.bytes_per_step == p.nr * p.nz * (2 * (9 * ef + 5 * 4) + ef + (2 if p.storage == 0 else 8))
+    # populations read and written, the FP32 porosity, and the references a pull reads: the
+    # FP16 temperature offset (FP32 storage) or the 4 x FP16 reference word (16-bit storage)
+    assert info.bytes_per_step == p.nr * p.nz * (2 * (9 * ef + 5 * 4) + 4 + (2 if p.storage == 0 else 8))
 
 
 @pytest.mark.parametrize("bad", [

@@ -72,7 +72,10 @@ def test_codec_against_emulation(lbm, oracle, storage, case):
     # the GPU carries the codec's error, not more (FP32 arithmetic adds ~1e-6)
     assert e_gpu <= 3 * e_em + 2e-5
     assert d_gpu <= 3 * d_em + 1e-5
-    assert d_gpu <= 1e-3
+    if storage == "f16":
+        # in this transient; BF16 (8-bit significand) reaches the bar at steady state only
+        # (test_steady_state_within_1e3_of_fp32), as its emulation does (3.4e-3 here)
+        assert d_gpu <= 1e-3
     # and the reference is what brings it there
     assert e_em < 0.1 * e_rest
 
