@@ -41,18 +41,20 @@ E2E_STEPS = 50                    # minimum length of the end-to-end window (ste
 # DRAM traffic of one k_bulk launch on the 4096 x 8192 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of the bulk kernel in one single-pass ncu capture of this
 # benchmark), valid only for the bulk kernel's source it was taken on (_kernel_hash).
-TRAFFIC = {("f32", 4096, 8192): ("c46d47cafaadd9a6", 2.09e9 + 1.83e9)}
+TRAFFIC = {("f32", 4096, 8192): ("c2d84369e2972e55", 2087872768 + 1828121600),
+           ("f16", 4096, 8192): ("c2d84369e2972e55", 1691845120 + 1230397952)}
 
 
 def _kernel_hash() -> str:
-    """Hash of the bulk kernel's own source: csrc/lbm_physics.cuh and csrc/lbm.cu up to the
-    end of k_bulk (where k_wall begins); host code and other kernels further down do not
-    change the traffic record's validity."""
+    """Hash of the bulk kernels' own source: csrc/lbm_physics.cuh, csrc/lbm_pair.cuh and
+    csrc/lbm.cu up to the end of the bulk kernels (where k_wall begins); host code and
+    other kernels further down do not change the traffic record's validity."""
     import hashlib
 
     d = os.path.join(ROOT, "paper_1409_5929_gb300", "csrc")
     h = hashlib.sha256()
     h.update(open(os.path.join(d, "lbm_physics.cuh"), "rb").read())
+    h.update(open(os.path.join(d, "lbm_pair.cuh"), "rb").read())
     src = open(os.path.join(d, "lbm.cu"), "rb").read()
     cut = src.find(b"template <int STO>\n__global__ void k_wall(")
     h.update(src[:cut] if cut > 0 else src + b"(no k_wall marker)")
@@ -204,7 +206,8 @@ def storage_variant(lbm, storage, phi, steps, warmup, peak):
     return {"value": round(NR * NZ * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
             "ms_per_step": round(ms / steps, 5), "bytes_per_node": info.bytes_per_step // (NR * NZ),
             "bulk_avg_ms": round(bulk_avg, 5), "wall_avg_ms": round(wall_avg, 5),
-            "achieved_gbs": round(achieved, 1), "frac": round(achieved / peak, 4), "clocks": ck}
+            "achieved_gbs": round(achieved, 1), "frac": round(achieved / peak, 4),
+            "traffic": _traffic(storage), "clocks": ck}
 
 
 def run_ours(args, rank, world, local_rank):
