@@ -41,8 +41,8 @@ E2E_STEPS = 50                    # minimum length of the end-to-end window (ste
 # DRAM traffic of one k_bulk launch on the 4096 x 8192 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of the bulk kernel in one single-pass ncu capture of this
 # benchmark), valid only for the bulk kernel's source it was taken on (_kernel_hash).
-TRAFFIC = {("f32", 4096, 8192): ("c2d84369e2972e55", 2087872768 + 1828121600),
-           ("f16", 4096, 8192): ("c2d84369e2972e55", 1691845120 + 1230397952)}
+TRAFFIC = {("f32", 4096, 8192): ("00835f3f7241bf06", 2089972224 + 1827687424),
+           ("f16", 4096, 8192): ("00835f3f7241bf06", 1692685568 + 1230361856)}
 
 
 def _kernel_hash() -> str:
@@ -56,7 +56,8 @@ def _kernel_hash() -> str:
     h.update(open(os.path.join(d, "lbm_physics.cuh"), "rb").read())
     h.update(open(os.path.join(d, "lbm_pair.cuh"), "rb").read())
     src = open(os.path.join(d, "lbm.cu"), "rb").read()
-    cut = src.find(b"template <int STO>\n__global__ void k_wall(")
+    k = src.find(b"__global__ void k_wall(")
+    cut = src.rfind(b"template <", 0, k) if k > 0 else -1
     h.update(src[:cut] if cut > 0 else src + b"(no k_wall marker)")
     return h.hexdigest()[:16]
 
@@ -175,8 +176,9 @@ def _time_steps(lbm, s, stream, steps):
     return ms, bulk_ms / max(bulk_n, 1), wall_ms / max(wall_n, 1), clocks.stop()
 
 
-def _solver(lbm, storage, phi, stream):
-    p = lbm.lbm_params_default(storage=storage, eps_mean=float(phi.mean(dtype=np.float64)), **WORKLOAD)
+def _solver(lbm, storage, phi, stream, inplace=0):
+    p = lbm.lbm_params_default(storage=storage, eps_mean=float(phi.mean(dtype=np.float64)), inplace=inplace,
+                               **WORKLOAD)
     s = lbm.Solver(p)
     s.set_stream(stream.cuda_stream)
     s.set_porosity(phi)
@@ -191,13 +193,14 @@ def _bulk_bytes(info):
     return (NR - 2) * (NZ - 2) * (info.bytes_per_step // (NR * NZ))
 
 
-def storage_variant(lbm, storage, phi, steps, warmup, peak):
-    """Single-domain line for another storage type: MLUPS, the bulk kernel's roofline
-    fraction on its own bytes per node, and each kernel's mean launch time."""
+def storage_variant(lbm, storage, phi, steps, warmup, peak, inplace=0):
+    """Single-domain line for another storage type (or in-place storage): MLUPS, the bulk
+    kernel's roofline fraction on its own bytes per node, and each kernel's mean launch
+    time."""
     import torch
 
     stream = torch.cuda.Stream()
-    s = _solver(lbm, storage, phi, stream)
+    s = _solver(lbm, storage, phi, stream, inplace)
     s.step(warmup)
     ms, bulk_avg, wall_avg, ck = _time_steps(lbm, s, stream, steps)
     info = s.info()
@@ -207,7 +210,7 @@ def storage_variant(lbm, storage, phi, steps, warmup, peak):
             "ms_per_step": round(ms / steps, 5), "bytes_per_node": info.bytes_per_step // (NR * NZ),
             "bulk_avg_ms": round(bulk_avg, 5), "wall_avg_ms": round(wall_avg, 5),
             "achieved_gbs": round(achieved, 1), "frac": round(achieved / peak, 4),
-            "traffic": _traffic(storage), "clocks": ck}
+            "traffic": None if inplace else _traffic(storage), "clocks": ck}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -219,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     phi = inputs.porosity_field(NR, NZ, PHI_RECIPE["lo"], PHI_RECIPE["hi"], PHI_RECIPE["sigma"], PHI_RECIPE["seed"])
     stream = torch.cuda.Stream()
-    s = _solver(lbm, args.storage, phi, stream)
+    s = _solver(lbm, args.storage, phi, stream, int(args.inplace))
     info = s.info()
     nodes = NR * NZ
     bulk_bytes = _bulk_bytes(info)
@@ -283,9 +286,10 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": _workload_name(args.storage), "storage": args.storage, "nodes": nodes,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "state larger than L2 (no flush)",
-                   "bytes_per_step": info.bytes_per_step},
+                   "bytes_per_step": info.bytes_per_step, "inplace": bool(args.inplace)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": _traffic(args.storage),
+                     "frac": round(achieved / peak, 4),
+                     "traffic": None if args.inplace else _traffic(args.storage),
                      "kernel": f"k_bulk<{args.storage}>", "peak_source": f"{peak_kind} hbm_gbs",
                      "avg_launch_ms": round(bulk_avg, 5), "bytes_per_launch": bulk_bytes,
                      "wall_kernel_avg_ms": round(wall_avg, 5)},
@@ -297,6 +301,9 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_extras:
         line["storage_variants"] = {sto: storage_variant(lbm, sto, phi, args.steps, args.warmup, peak)
                                     for sto in ("f32", "f16", "bf16") if sto != args.storage}
+        # one state buffer updated in place: half the state memory, one node per thread
+        line["inplace_variants"] = {sto: storage_variant(lbm, sto, phi, args.steps, args.warmup, peak, 1)
+                                    for sto in ("f32", "f16")}
     return line
 
 
@@ -592,6 +599,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the sweep and time-to-steady sections")
     ap.add_argument("--nr", type=int, default=NR, help="override the grid (profiling of small cases only)")
     ap.add_argument("--nz", type=int, default=NZ)
+    ap.add_argument("--inplace", action="store_true", help="one state buffer updated in place (AA pattern)")
     args = ap.parse_args()
     _set_grid(args.nr, args.nz)
     args.warmup = max(args.warmup, 3)

@@ -107,7 +107,14 @@ typedef struct lbm_params {
                                 |kz - h H| <= l H / 2); heater_len <= 1 */
     int32_t collision;       /* LBM_MRT (Eq. 21 with the rates of Sec. 4) or LBM_BGK (every rate
                                 1/tau_nu: the BGK limit of Sec. 3.1) */
-    int32_t reserved;        /* 0 */
+    int32_t inplace;         /* 0: two state buffers (A/B, read one, write the other);
+                                1: one state buffer updated in place (AA pattern: the
+                                populations alternate between two layouts from step to
+                                step), half the state memory for the same bytes per
+                                step; lbm_create only (lbm_batch_create rejects it),
+                                lbm_residual then returns LBM_ERR_INVALID (no previous
+                                state is kept; lbm_run works); one node per thread for
+                                every storage type */
 } lbm_params;
 
 /* Derived lattice constants (Eq. 9, 31, 39), for checks and reporting. */
@@ -260,6 +267,8 @@ int lbm_run(lbm_handle *h, int64_t max_steps, int64_t check_every, double tol, i
  * converging annuli), and 16-bit rounding of deviations from the rest state jitters the
  * flow by about 4e-4 per step.  lbm_run refreshes before every check interval; with
  * 16-bit storage lbm_step also refreshes every 1024 steps since the last refresh.
+ * With in-place storage after an odd number of steps, boundary nodes whose outgoing
+ * populations that layout drops (they leave the domain) keep their old references.
  * Asynchronous on the handle's stream. */
 int lbm_rebase(lbm_handle *h);
 
@@ -270,6 +279,8 @@ int lbm_node_class(lbm_handle *h, uint8_t *out);
  * [row0, row0 + nrows) in FP64, undoing the storage encoding: f[i][row][kz]
  * (9 planes of nrows*nz) and g[i][row][kz] (5 planes), host memory, r-weighted
  * as in Eq. 17.  For checks against an FP64 reference and for inspection.
+ * With in-place storage after an odd number of steps, populations that leave the
+ * domain from boundary nodes are not kept and export as NaN (no step reads them).
  * Synchronises. */
 int lbm_export_populations(lbm_handle *h, int32_t row0, int32_t nrows, double *f, double *g);
 

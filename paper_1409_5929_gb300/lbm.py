@@ -40,7 +40,7 @@ class lbm_params(C.Structure):
         ("T_hot", C.c_double), ("T_cold", C.c_double), ("body_accel_z", C.c_double),
         ("init_noise", C.c_double), ("seed", C.c_uint64), ("u_in", C.c_double),
         ("heater_len", C.c_double), ("heater_center", C.c_double),
-        ("collision", C.c_int32), ("reserved", C.c_int32),
+        ("collision", C.c_int32), ("inplace", C.c_int32),
     ]
 
 

@@ -18,9 +18,9 @@ def test_traffic_record_keyed_on_bulk_kernel_source(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h0 = bench._kernel_hash()
     src = (dst / "lbm.cu").read_text()
-    marker = "template <int STO>\n__global__ void k_wall("
+    marker = "__global__ void k_wall("
     assert src.count(marker) == 1
-    cut = src.index(marker)
+    cut = src.rindex("template <", 0, src.index(marker))
     (dst / "lbm.cu").write_text(src + "\n// a later host-side edit\n")
     assert bench._kernel_hash() == h0
     (dst / "lbm.cu").write_text(src[:cut] + "// an edit of the bulk kernel\n" + src[cut:])
