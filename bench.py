@@ -460,7 +460,7 @@ def warm_start_section(nr: int = 64, nz: int = 128, ntrain: int = 256, nheld: in
     _, res_tr, _, fields, dt_gen = W.run_batch(train_inst, max_steps, check, tol)
     X = torch.tensor(W.features(train_inst, nr, nz), device="cuda")
     Y = torch.tensor(np.stack([W.targets_from_fields(f[1], f[2], f[3]) for f in fields]), device="cuda")
-    net = F.FNO2d(nr, nz, width=32, modes=16, seed=1)
+    net = F.make_fno(nr, nz, width=32, modes=16, seed=1)
     t1 = time.perf_counter()
     losses = W.train(net, X, Y, epochs=20, batch=8, lr=2e-3)
     torch.cuda.synchronize()

@@ -2,6 +2,7 @@
 
     liblbm.so  the lattice Boltzmann solver (include/lbm.h)
     libfno.so  the kernels of the learned warm start (include/fno.h)
+    libfnonet.so  the fused tensor-core kernels of that network (include/fno_net.h)
 
     python -m paper_1409_5929_gb300.build [--force] [-v]
 """
@@ -22,6 +23,7 @@ TARGETS = {
     "liblbm.so": ([os.path.join(CSRC, "lbm.cu")],
                   [os.path.join(CSRC, "lbm_physics.cuh"), os.path.join(INC, "lbm.h")]),
     "libfno.so": ([os.path.join(CSRC, "fno.cu")], [os.path.join(INC, "fno.h")]),
+    "libfnonet.so": ([os.path.join(CSRC, "fno_net.cu")], [os.path.join(CSRC, "tc.cuh"), os.path.join(INC, "fno_net.h")]),
 }
 LIB = os.path.join(HERE, "liblbm.so")
 FNO_LIB = os.path.join(HERE, "libfno.so")

@@ -160,13 +160,21 @@ __device__ int g_tc_wait_test;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor of a K-major tile whose rows hold BK elements: LBO =
-// 128 B between the core matrices along K, SBO = BK / 8 x 128 B between 8-row groups.
-template <int BK>
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    const uint64_t lbo = 128, sbo = (uint64_t)(BK / 8) * 128;
+// Shared-memory matrix descriptor (no swizzle): start address, leading-dimension byte
+// offset (LBO) and stride-dimension byte offset (SBO).  Tiles are kept in the canonical
+// layout of 8 x 16-byte core matrices, each 128 contiguous bytes.  Without swizzling LBO is
+// the stride between core matrices adjacent along K and SBO the stride between those
+// adjacent along M (N), whether the operand is K-major (8 consecutive k per 16-byte row)
+// or MN-major (8 consecutive m (n) per 16-byte row, the 8 rows being 8 consecutive k).
+__device__ __forceinline__ uint64_t tc_desc_raw(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
            ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// K-major tile whose rows hold BK elements: LBO = 128 B, SBO = BK / 8 x 128 B.
+template <int BK>
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return tc_desc_raw(saddr, 128, (BK / 8) * 128);
 }
 
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase, int spin = TC_SPIN) {
@@ -186,6 +194,13 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase, int spin 
 template <int BK>
 __device__ __forceinline__ uint32_t tc_off(int row, int k) {
     return (uint32_t)((((row >> 3) * (BK / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+// byte offset of element (row, k) of a [rows x BK] MN-major tile (rows contiguous within a
+// 16-byte core-matrix row): core matrices adjacent along the rows 128 B apart, groups of 8
+// k rows / 8 x 128 B apart
+__device__ __forceinline__ uint32_t tc_off_mn(int rows, int row, int k) {
+    return (uint32_t)((((k >> 3) * (rows >> 3) + (row >> 3)) << 7) + ((k & 7) << 4) + ((row & 7) << 1));
 }
 
 __device__ __forceinline__ void st_bf16x4(uint8_t* p, float a, float b, float c, float d) {
@@ -223,7 +238,7 @@ __device__ __forceinline__ void tc_stage(uint8_t* T, const float* __restrict__ X
             }
             st_bf16x4(T + tc_off<BK>(r, kq), v[0], v[1], v[2], v[3]);
         }
-    } else {        // rows / 4 float4 along the row index per k
+    } else {        // MN-major tile: rows / 4 float4 along the row index per k, 8-byte stores
         const int rq = rows >> 2;
         for (int f = tid; f < rq * BK; f += 128) {
             const int k = f / rq, r = (f - k * rq) << 2;
@@ -240,9 +255,7 @@ __device__ __forceinline__ void tc_stage(uint8_t* T, const float* __restrict__ X
                         if (gr + i < R) v[i] = src[i];
                 }
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                *reinterpret_cast<__nv_bfloat16*>(T + tc_off<BK>(r + i, k)) = __float2bfloat16_rn(v[i]);
+            st_bf16x4(T + tc_off_mn(rows, r, k), v[0], v[1], v[2], v[3]);
         }
     }
 }
@@ -277,8 +290,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_sh;
-    // kind::f16 instruction descriptor: D F32, A and B BF16, both K-major, N, M = 128
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+    // kind::f16 instruction descriptor: D F32, A and B BF16, N, M = 128; an operand stored
+    // with its M (N) index contiguous (A transposed, B not) is staged MN-major (bits 15, 16)
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (TA ? (1u << 15) : 0u) | (TB ? 0u : (1u << 16)) |
+                           ((uint32_t)(ntile >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
     const int nk = (K + BK - 1) / BK;
     const int64_t ntiles = (int64_t)ntm * ntn * batch;
     // this CTA's steps: tiles t = blockIdx.x + j gridDim.x, each in nk chunks of K
@@ -310,7 +325,12 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int ntile,
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < BK / 16; ++j) {
-                const uint64_t ad = tc_desc<BK>(a0 + j * 256), bd = tc_desc<BK>(a0 + abytes + j * 256);
+                // K step j (16 k): K-major tiles advance two core matrices along K (256 B),
+                // MN-major tiles two groups of 8 k rows (2 x rows / 8 x 128 B)
+                const uint64_t ad = TA ? tc_desc_raw(a0 + j * 2 * TC_BM * 16, TC_BM * 16, 128)
+                                       : tc_desc<BK>(a0 + j * 256);
+                const uint64_t bd = TB ? tc_desc<BK>(a0 + abytes + j * 256)
+                                       : tc_desc_raw(a0 + abytes + j * 2 * ntile * 16, ntile * 16, 128);
                 const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"

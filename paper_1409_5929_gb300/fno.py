@@ -389,3 +389,278 @@ class FNO2d:
         self.step_count += 1
         for k in self.w:
             fno_adam(self.w[k], self.g[k], self.adam_m[k], self.adam_v[k], lr, b1, b2, eps, self.step_count)
+
+
+# ---- fused tensor-core network (libfnonet.so, include/fno_net.h) --------------------
+FNO_NET_LIB_PATH = os.path.join(HERE, "libfnonet.so")
+_net_lib = None
+_NET_SIGS = {
+    "fno_net_supported": [_vp],
+    "fno_net_parts": [_vp],
+    "fno_net_pack": [_vp, _i64, _i64, C.c_int, C.c_int, _vp, C.c_int, C.c_int, _vp],
+    "fno_net_fwd": [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "fno_net_proj": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "fno_net_bwd": [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "fno_net_r2k": [_vp, _vp, _vp, _vp, _vp],
+    "fno_net_k2r": [_vp, _vp, _vp, _vp, _vp],
+    "fno_net_mix_fwd": [_vp, _vp, _vp, _vp, _vp],
+    "fno_net_mix_bwd": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp],
+    "fno_net_reduce": [_vp, C.c_int, _i64, C.c_int, _vp, C.c_int, _vp],
+    "fno_net_status": [C.c_int],
+}
+
+
+class fno_net_dims(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("batch", "nr", "nz", "width", "modes", "hidden", "in_ch", "out_ch")]
+
+
+def load_net():
+    global _net_lib
+    with _lock:
+        if _net_lib is None:
+            if not os.path.exists(FNO_NET_LIB_PATH):
+                from . import build as _b
+
+                _b.build()
+            lib = C.CDLL(FNO_NET_LIB_PATH)
+            for name, args in _NET_SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = C.c_int
+                fn.argtypes = args
+            lib.fno_net_last_error.restype = C.c_char_p
+            _net_lib = lib
+    return _net_lib
+
+
+def _ncheck(rc):
+    if rc != 0:
+        raise RuntimeError(f"fno_net error {rc}: {load_net().fno_net_last_error().decode()}")
+
+
+def net_supported(batch, nr, nz, width, modes, hidden, in_ch, out_ch) -> bool:
+    d = fno_net_dims(batch, nr, nz, width, modes, hidden, in_ch, out_ch)
+    return bool(load_net().fno_net_supported(C.byref(d)))
+
+
+def fno_net_status(clear: bool = True) -> int:
+    return int(load_net().fno_net_status(int(clear)))
+
+
+class FusedFNO2d:
+    """The operator of FNO2d on the fused tcgen05 kernels of libfnonet.so: BF16
+    activations, FP32 master weights and Adam state (same layouts as FNO2d), BF16 operand
+    images of the weights refreshed after every update.  Torch provides device buffers
+    only; every step runs in libfnonet.so (and Adam in libfno.so)."""
+
+    def __init__(self, nr, nz, width=32, modes=16, layers=4, in_ch=8, out_ch=3, hidden=128, seed=0, params=None):
+        import torch
+
+        self.nr, self.nz, self.width, self.m, self.L = nr, nz, width, modes, layers
+        self.in_ch, self.out_ch, self.hidden = in_ch, out_ch, hidden
+        self.nkr, self.nkz = 2 * modes, modes
+        if not net_supported(1, nr, nz, width, modes, hidden, in_ch, out_ch):
+            raise ValueError("sizes outside the fused kernels' range (include/fno_net.h)")
+        P = params if params is not None else init_params(nr, nz, width, modes, layers, in_ch, out_ch, hidden, seed)
+        dev = "cuda"
+        self.w = {k: torch.tensor(np.ascontiguousarray(v, dtype=np.float32), device=dev) for k, v in P.items()}
+        self.g = {k: torch.zeros_like(v) for k, v in self.w.items()}
+        self.adam_m = {k: torch.zeros_like(v) for k, v in self.w.items()}
+        self.adam_v = {k: torch.zeros_like(v) for k, v in self.w.items()}
+        self.step_count = 0
+        load()
+        load_net()
+        Fz, Cr, Sr, Gz = dft_matrices(nr, nz, modes)
+        f32 = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+        F2 = np.block([[Cr, Sr], [-Sr, Cr]])                 # [W_re; W_im] = F2 [Z_re; Z_im]
+        F2i = np.block([[Cr.T, -Sr.T], [Sr.T, Cr.T]])        # [V_re; V_im] = F2i [Y_re; Y_im]
+        m2 = 2 * modes
+        self.img = {}
+        self.img["fz"] = self._pack(f32(Fz), m2, 1, nz, m2, nz, m2)
+        self.img["gzt"] = self._pack(f32(Gz), 1, nz, nz, m2, nz, m2)
+        self.img["f2"] = self._pack(f32(F2), 2 * nr, 1, 2 * m2, 2 * nr, 128, 2 * nr)
+        self.img["f2i"] = self._pack(f32(F2i), 2 * m2, 1, 2 * nr, 2 * m2, 2 * nr, 2 * m2)
+        self._dirty = True
+        self._buf = {}
+        self._parts = None
+
+    # -- helpers ------------------------------------------------------------------
+    def _pack(self, src, so, si, O, I, Opad, Ipad, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty(Opad * Ipad, dtype=torch.bfloat16, device="cuda")
+        _ncheck(load_net().fno_net_pack(src.data_ptr(), so, si, O, I, out.data_ptr(), Opad, Ipad, _stream()))
+        return out
+
+    def _refresh_images(self):
+        """BF16 operand images of the current FP32 weights (after every update)."""
+        if not self._dirty:
+            return
+        C, H, CI, CO, w = self.width, self.hidden, self.in_ch, self.out_ch, self.w
+        im = self.img
+        im["P"] = self._pack(w["P"], 1, C, C, CI, C, 16, im.get("P"))                  # P^T: (c, ci)
+        for l in range(self.L):
+            W = w[f"W{l}"]
+            im[f"Wf{l}"] = self._pack(W, 1, C, C, C, C, C, im.get(f"Wf{l}"))          # W^T: (c_out, c_in)
+            im[f"Wn{l}"] = self._pack(W, C, 1, C, C, C, C, im.get(f"Wn{l}"))          # W: (c_in, c_out)
+        im["q1w"] = self._pack(w["Q1"], 1, H, H, C, H, C, im.get("q1w"))              # Q1^T: (j, c)
+        im["q1n"] = self._pack(w["Q1"], H, 1, C, H, C, H, im.get("q1n"))              # Q1: (c, j)
+        im["q2w"] = self._pack(w["Q2"], 1, CO, CO, H, 16, H, im.get("q2w"))           # Q2^T: (o, j)
+        im["q2n"] = self._pack(w["Q2"], CO, 1, H, CO, H, 16, im.get("q2n"))           # Q2: (j, o)
+        self._dirty = False
+
+    def _dims(self, B):
+        return fno_net_dims(B, self.nr, self.nz, self.width, self.m, self.hidden, self.in_ch, self.out_ch)
+
+    def _b(self, name, shape, dtype=None):
+        import torch
+
+        dtype = dtype or torch.bfloat16
+        t = self._buf.get(name)
+        if t is None or tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+            t = torch.empty(shape, dtype=dtype, device="cuda")
+            self._buf[name] = t
+        return t
+
+    def params_numpy(self):
+        return {k: v.detach().cpu().numpy() for k, v in self.w.items()}
+
+    # -- forward ------------------------------------------------------------------
+    def forward(self, x, train=False, t=None):
+        """x: [B, nr, nz, in_ch] float32 CUDA tensor -> y [B, nr, nz, out_ch] (float32).
+        With t (targets) also the loss and the projection's backward (see loss_and_grad)."""
+        import torch
+
+        lib = load_net()
+        B = x.shape[0]
+        d = self._dims(B)
+        dp = C.byref(d)
+        nr, nz, Cw, M, L = self.nr, self.nz, self.width, self.m, self.L
+        s = _stream()
+        self._refresh_images()
+        im, w = self.img, self.w
+        x = x.contiguous()
+        act = (B, nr, nz, Cw)
+        zs = (B, M, 2, nr, Cw)
+        ks = (M, 2 * M, 2, B, Cw)
+        h = [self._b(f"h{l}", act) for l in range(L + 1)]
+        Z = [self._b(f"Z{l}", zs) for l in range(L)]
+        V = [self._b(f"V{l}", zs) for l in range(L)]
+        Wk = [self._b(f"Wk{l}", ks, torch.float32) for l in range(L)]
+        Yk = self._b("Yk", ks, torch.float32)
+        _ncheck(lib.fno_net_fwd(0, dp, x.data_ptr(), None, im["P"].data_ptr(), w["p"].data_ptr(), None,
+                                im["fz"].data_ptr(), None, h[0].data_ptr(), None, Z[0].data_ptr(), s))
+        for l in range(L):
+            _ncheck(lib.fno_net_r2k(dp, Z[l].data_ptr(), im["f2"].data_ptr(), Wk[l].data_ptr(), s))
+            _ncheck(lib.fno_net_mix_fwd(dp, Wk[l].data_ptr(), w[f"R{l}"].data_ptr(), Yk.data_ptr(), s))
+            _ncheck(lib.fno_net_k2r(dp, Yk.data_ptr(), im["f2i"].data_ptr(), V[l].data_ptr(), s))
+            if l < L - 1:
+                pre = self._b(f"pre{l}", act)
+                _ncheck(lib.fno_net_fwd(1, dp, None, h[l].data_ptr(), im[f"Wf{l}"].data_ptr(), w[f"b{l}"].data_ptr(),
+                                        im["gzt"].data_ptr(), im["fz"].data_ptr(), V[l].data_ptr(), pre.data_ptr(),
+                                        h[l + 1].data_ptr(), Z[l + 1].data_ptr(), s))
+            else:
+                _ncheck(lib.fno_net_fwd(2, dp, None, h[l].data_ptr(), im[f"Wf{l}"].data_ptr(), w[f"b{l}"].data_ptr(),
+                                        im["gzt"].data_ptr(), None, V[l].data_ptr(), h[L].data_ptr(), None, None, s))
+        y = self._b("y", (B, nr, nz, self.out_ch), torch.float32)
+        if t is None:
+            _ncheck(lib.fno_net_proj(dp, h[L].data_ptr(), im["q1w"].data_ptr(), None, w["q1"].data_ptr(),
+                                     im["q2w"].data_ptr(), None, w["q2"].data_ptr(), None, y.data_ptr(), None, None,
+                                     None, None, None, None, s))
+            return y
+        parts = lib.fno_net_parts(dp)
+        H, CO = self.hidden, self.out_ch
+        pQ1 = self._b("pQ1", (parts, H, Cw), torch.float32)
+        pq1 = self._b("pq1", (parts, H), torch.float32)
+        pQ2 = self._b("pQ2", (parts, H, CO), torch.float32)
+        pq2 = self._b("pq2", (parts, CO), torch.float32)
+        dhL = self._b("dhL", act)
+        lbuf = self._b("lossd", (1,), torch.float64)
+        lbuf.zero_()
+        _ncheck(lib.fno_net_proj(dp, h[L].data_ptr(), im["q1w"].data_ptr(), im["q1n"].data_ptr(), w["q1"].data_ptr(),
+                                 im["q2w"].data_ptr(), im["q2n"].data_ptr(), w["q2"].data_ptr(), t.data_ptr(),
+                                 y.data_ptr(), dhL.data_ptr(), lbuf.data_ptr(), pQ1.data_ptr(), pq1.data_ptr(),
+                                 pQ2.data_ptr(), pq2.data_ptr(), s))
+        g = self.g
+        _ncheck(lib.fno_net_reduce(pQ1.data_ptr(), parts, H * Cw, H, g["Q1"].data_ptr(), 1, s))
+        _ncheck(lib.fno_net_reduce(pq1.data_ptr(), parts, H, 0, g["q1"].data_ptr(), 1, s))
+        _ncheck(lib.fno_net_reduce(pQ2.data_ptr(), parts, H * CO, 0, g["Q2"].data_ptr(), 1, s))
+        _ncheck(lib.fno_net_reduce(pq2.data_ptr(), parts, CO, 0, g["q2"].data_ptr(), 1, s))
+        return y
+
+    def zero_grad(self):
+        for g in self.g.values():
+            g.zero_()
+
+    def _backward_layers(self, x, B):
+        import torch
+
+        lib = load_net()
+        d = self._dims(B)
+        dp = C.byref(d)
+        nr, nz, Cw, M, L = self.nr, self.nz, self.width, self.m, self.L
+        s = _stream()
+        im, w, g = self.img, self.w, self.g
+        act = (B, nr, nz, Cw)
+        zs = (B, M, 2, nr, Cw)
+        ks = (M, 2 * M, 2, B, Cw)
+        parts = lib.fno_net_parts(dp)
+        pdW = self._b("pdW", (parts, Cw, Cw), torch.float32)
+        pdb = self._b("pdb", (parts, Cw), torch.float32)
+        dV = self._b("dV", zs)
+        dZ = self._b("dZ", zs)
+        dYk = self._b("dYk", ks, torch.float32)
+        dWk = self._b("dWk", ks, torch.float32)
+        dpre = [self._b("dpre_a", act), self._b("dpre_b", act)]
+        h = [self._buf[f"h{l}"] for l in range(L + 1)]
+
+        def red(name_w, name_b, rows):
+            _ncheck(lib.fno_net_reduce(pdW.data_ptr(), parts, rows * Cw, 0, g[name_w].data_ptr(), 1, s))
+            _ncheck(lib.fno_net_reduce(pdb.data_ptr(), parts, Cw, 0, g[name_b].data_ptr(), 1, s))
+
+        cur = self._buf["dhL"]   # dL/dpre_{L-1} (h_L = pre_{L-1})
+        _ncheck(lib.fno_net_bwd(0, dp, cur.data_ptr(), None, None, None, None, h[L - 1].data_ptr(), None,
+                                im["gzt"].data_ptr(), None, dV.data_ptr(), pdW.data_ptr(), pdb.data_ptr(), s))
+        red(f"W{L - 1}", f"b{L - 1}", Cw)
+        for l in range(L - 1, -1, -1):
+            _ncheck(lib.fno_net_r2k(dp, dV.data_ptr(), im["f2"].data_ptr(), dYk.data_ptr(), s))
+            _ncheck(lib.fno_net_mix_bwd(dp, self._buf[f"Wk{l}"].data_ptr(), w[f"R{l}"].data_ptr(), dYk.data_ptr(),
+                                        dWk.data_ptr(), g[f"R{l}"].data_ptr(), 1, s))
+            _ncheck(lib.fno_net_k2r(dp, dWk.data_ptr(), im["f2i"].data_ptr(), dZ.data_ptr(), s))
+            if l > 0:
+                nxt = dpre[l % 2]
+                _ncheck(lib.fno_net_bwd(1, dp, cur.data_ptr(), dZ.data_ptr(), im[f"Wn{l}"].data_ptr(),
+                                        im["fz"].data_ptr(), self._buf[f"pre{l - 1}"].data_ptr(), h[l - 1].data_ptr(),
+                                        None, im["gzt"].data_ptr(), nxt.data_ptr(), dV.data_ptr(), pdW.data_ptr(),
+                                        pdb.data_ptr(), s))
+                red(f"W{l - 1}", f"b{l - 1}", Cw)
+                cur = nxt
+            else:
+                _ncheck(lib.fno_net_bwd(2, dp, cur.data_ptr(), dZ.data_ptr(), im["Wn0"].data_ptr(),
+                                        im["fz"].data_ptr(), None, None, x.data_ptr(), None, None, None,
+                                        pdW.data_ptr(), pdb.data_ptr(), s))
+                red("P", "p", self.in_ch)
+
+    def loss_and_grad(self, x, t):
+        """MSE loss (device double) and parameter gradients (accumulated into self.g) of
+        one batch."""
+        x = x.contiguous()
+        t = t.contiguous()
+        self.forward(x, train=True, t=t)
+        self._backward_layers(x, x.shape[0])
+        return self._buf["lossd"]
+
+    def adam_step(self, lr, b1=0.9, b2=0.999, eps=1e-8):
+        self.step_count += 1
+        for k in self.w:
+            fno_adam(self.w[k], self.g[k], self.adam_m[k], self.adam_v[k], lr, b1, b2, eps, self.step_count)
+        self._dirty = True
+
+
+def make_fno(nr, nz, width=32, modes=16, layers=4, in_ch=8, out_ch=3, hidden=128, seed=0, params=None, fused=None):
+    """The warm-start network: the fused tcgen05 kernels where they cover the sizes (the
+    default), else FNO2d on the batched GEMM."""
+    if fused is None:
+        fused = net_supported(1, nr, nz, width, modes, hidden, in_ch, out_ch)
+    cls = FusedFNO2d if fused else FNO2d
+    return cls(nr, nz, width, modes, layers, in_ch, out_ch, hidden, seed, params)

@@ -134,7 +134,62 @@ def main():
             "tensor_path_status": F.fno_tensor_path_status(True),
         }
     F.fno_set_tensor_path(0)
+    out["paths"]["fused"] = fused_step(a, x, t, hbm)
     print(json.dumps(out), flush=True)
+
+
+def fused_bytes(B, nr, nz, width=32, in_ch=8, out_ch=3, layers=4):
+    """Algorithmic HBM bytes of one fused training step's pixel-space kernels (BF16
+    activations): lift reads x and writes h0; each layer reads h and writes pre and
+    GELU(pre) (the last only pre); the projection reads hL and the targets and writes y and
+    dL/dhL; the backward kernels read dL/dpre, pre and h and write the next dL/dpre (the
+    last layer's kernel reads two of them, the lift's dL/dpre and x).  The spectra and
+    weights (under 1 %) are left out."""
+    P = B * nr * nz
+    act = 2 * P * width
+    return (P * in_ch * 4 + act                                   # lift
+            + (layers - 1) * 3 * act + 2 * act                    # layers
+            + act + P * out_ch * 8 + act                          # projection
+            + 2 * act + (layers - 1) * 4 * act + act + P * in_ch * 4)   # backward
+
+
+def fused_step(a, x, t, hbm):
+    """The fused tcgen05 network: training step (forward, loss, backward, Adam) and its
+    forward and backward halves timed with CUDA events."""
+    import torch
+
+    if not F.net_supported(a.batch, a.nr, a.nz, 32, 16, 128, 8, 3):
+        return {"unsupported": True}
+    net = F.FusedFNO2d(a.nr, a.nz, seed=1)
+    for _ in range(3):
+        net.zero_grad()
+        net.loss_and_grad(x, t)
+        net.adam_step(1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        net.zero_grad()
+        net.loss_and_grad(x, t)
+        net.adam_step(1e-3)
+    torch.cuda.synchronize()
+    step_ms = (time.perf_counter() - t0) / a.steps * 1e3
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fw = bw = 0.0
+    for _ in range(a.steps):
+        ev[0].record()
+        net.forward(x, train=True, t=t)
+        ev[1].record()
+        net._backward_layers(x, x.shape[0])
+        ev[2].record()
+        torch.cuda.synchronize()
+        fw += ev[0].elapsed_time(ev[1])
+        bw += ev[1].elapsed_time(ev[2])
+    fw, bw = fw / a.steps, bw / a.steps
+    byt = fused_bytes(a.batch, a.nr, a.nz)
+    return {"train_step_ms": round(step_ms, 3), "forward_loss_ms": round(fw, 4), "backward_ms": round(bw, 4),
+            "pixel_bytes_per_step": byt, "fwd_bwd_gbs": round(byt / ((fw + bw) * 1e-3) / 1e9, 1),
+            "fwd_bwd_frac_of_hbm": round(byt / ((fw + bw) * 1e-3) / 1e9 / hbm, 4),
+            "status": F.fno_net_status(True)}
 
 
 if __name__ == "__main__":

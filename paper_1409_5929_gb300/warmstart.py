@@ -281,7 +281,7 @@ def main():
     Y = np.stack([targets_from_fields(f[1], f[2], f[3]) for f in fields])
     X = features(train_inst, nr, nz)
     Xd, Yd = torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda")
-    net = F.FNO2d(nr, nz, width=a.width, modes=a.modes, seed=1)
+    net = F.make_fno(nr, nz, width=a.width, modes=a.modes, seed=1)
     t1 = time.perf_counter()
     losses = train(net, Xd, Yd, a.epochs, a.batch, a.lr, log=log)
     torch.cuda.synchronize()

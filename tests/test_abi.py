@@ -39,6 +39,32 @@ def test_every_declared_symbol_is_exported(lbm):
     assert not missing, missing
 
 
+@pytest.mark.parametrize("header,lib_name", [("fno.h", "libfno.so"), ("fno_net.h", "libfnonet.so")])
+def test_network_libraries_export_their_headers(lbm, header, lib_name):
+    """The warm-start network's libraries (built by the same build step) load without a
+    GPU and export every function their header declares."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", header)).read(), flags=re.S)
+    names = sorted({m.group(1) for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(fno_\w+)\s*\(", text, flags=re.M)})
+    assert len(names) >= 8
+    lib = C.CDLL(os.path.join(ROOT, "paper_1409_5929_gb300", lib_name))
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_fused_network_size_checks(lbm):
+    """Host-side size checks of the fused network (no device call)."""
+    from paper_1409_5929_gb300 import fno as F
+
+    assert F.net_supported(8, 128, 256, 32, 16, 128, 8, 3)
+    assert F.net_supported(8, 64, 128, 32, 8, 128, 8, 3)
+    assert F.net_supported(2, 64, 128, 64, 8, 128, 8, 3)
+    assert not F.net_supported(2, 16, 32, 8, 4, 16, 8, 3)      # width, nz, hidden
+    assert not F.net_supported(2, 16, 128, 32, 8, 128, 8, 3)   # 2 nr not a multiple of 128
+    assert not F.net_supported(2, 64, 100, 32, 8, 128, 8, 3)   # nz
+    assert not F.net_supported(2, 64, 128, 32, 12, 128, 8, 3)  # 2 modes not 16 or 32
+    assert not F.net_supported(2, 64, 128, 32, 8, 64, 8, 3)    # hidden
+
+
 def _oracle_params(oracle, p):
     return oracle.params(nr=p.nr, nz=p.nz, geometry=p.geometry, radius_ratio=p.radius_ratio, Ra=p.Ra, Da=p.Da,
                          Pr=p.Pr, J=p.J, lam=p.lam, Ma=p.Ma, tau_nu=p.tau_nu, F_eps=p.F_eps, eps_mean=p.eps_mean,

@@ -103,3 +103,100 @@ def test_adam_step_matches_formula(fno):
         w = w - 1e-2 * (m / (1 - 0.9 ** step)) / (np.sqrt(v / (1 - 0.999 ** step)) + 1e-8)
     torch.cuda.synchronize()
     assert np.allclose(wd.cpu().numpy(), w, rtol=1e-5, atol=1e-6)
+
+
+# ---- fused tcgen05 network (libfnonet.so) -------------------------------------------
+def _fused_case(fno, nr, nz, width, modes, batch, seed=3, scale_r=True):
+    layers, hidden = 4, 128
+    P = fno.init_params(nr, nz, width, modes, layers, in_ch=8, out_ch=3, hidden=hidden, seed=seed)
+    if scale_r:   # larger spectral weights so the spectral path carries a visible share
+        for l in range(layers):
+            P[f"R{l}"] = (P[f"R{l}"] * width).astype(np.float32)
+    rng = np.random.default_rng(seed + 2)
+    x = rng.normal(size=(batch, nr, nz, 8)).astype(np.float32)
+    t = rng.normal(size=(batch, nr, nz, 3)).astype(np.float32)
+    return P, x, t, layers, hidden
+
+
+@pytest.mark.parametrize("width,modes", [(32, 8), (32, 16), (64, 8)])
+def test_fused_operator_and_gradients_against_fp64_oracle(fno, width, modes):
+    """The fused path (BF16 activations, tcgen05 MMAs, MN-major operand images) against
+    the FP64 autograd oracle: output, loss and every parameter gradient on a 64 x 128 grid
+    (two row tiles of the inverse r transform, one z tile), batch 2."""
+    import torch
+
+    from oracle import fno_oracle
+
+    nr, nz = 64, 128
+    P, x, t, layers, hidden = _fused_case(fno, nr, nz, width, modes, 2)
+    net = fno.FusedFNO2d(nr, nz, width, modes, layers, 8, 3, hidden, params=P)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    net.zero_grad()
+    loss = net.loss_and_grad(xd, td)
+    torch.cuda.synchronize()
+    assert fno.fno_net_status(True) == 0
+    y_ref, loss_ref, g_ref = fno_oracle.loss_and_grads(P, x, t, modes, layers)
+    y = net._buf["y"].cpu().numpy()
+    print("y", _bf16_tol(y, y_ref), "loss", float(loss.item()), loss_ref)
+    assert _bf16_tol(y, y_ref) < 2e-2
+    assert abs(float(loss.item()) - loss_ref) < 2e-2 * loss_ref
+    errs = {k: _bf16_tol(net.g[k].cpu().numpy(), g_ref[k]) for k in P}
+    print("grad rel L2", errs)
+    for k, e in errs.items():
+        assert e < 5e-2, (k, e)
+    # the forward alone (no targets) gives the same output
+    y2 = net.forward(xd).cpu().numpy()
+    assert np.array_equal(y2, y)
+
+
+def test_fused_matches_gemm_path_at_training_size(fno):
+    """128 x 256, width 32, 16 modes (the warm start's training size), batch 2: the fused
+    path's loss and gradients against FNO2d on the batched GEMM (FP32 activations, BF16
+    operands) -- the two differ by BF16 activation rounding only."""
+    import torch
+
+    nr, nz, width, modes = 128, 256, 32, 16
+    P, x, t, layers, hidden = _fused_case(fno, nr, nz, width, modes, 2, seed=7)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    fno.fno_set_tensor_path(0)
+    ref = fno.FNO2d(nr, nz, width, modes, layers, 8, 3, hidden, params=P)
+    ref.zero_grad()
+    lr_ = float(ref.loss_and_grad(xd, td).item())
+    net = fno.FusedFNO2d(nr, nz, width, modes, layers, 8, 3, hidden, params=P)
+    net.zero_grad()
+    lf = float(net.loss_and_grad(xd, td).item())
+    torch.cuda.synchronize()
+    assert fno.fno_net_status(True) == 0
+    print("loss gemm", lr_, "fused", lf)
+    assert abs(lf - lr_) < 1e-2 * lr_
+    for k in P:
+        e = _bf16_tol(net.g[k].cpu().numpy(), ref.g[k].cpu().numpy())
+        assert e < 5e-2, (k, e)
+
+
+def test_fused_training_follows_gemm_path(fno):
+    """Fifteen Adam steps on one batch with learnable targets (a fixed linear map of the
+    input channels): the fused path's loss falls and stays within 2 % of the GEMM path's
+    trajectory from the same parameters (the weight images follow every update)."""
+    import torch
+
+    nr, nz, width, modes = 64, 128, 32, 16
+    P, x, _, layers, hidden = _fused_case(fno, nr, nz, width, modes, 4, seed=11, scale_r=False)
+    A = np.random.default_rng(12).normal(size=(8, 3)).astype(np.float32) / np.sqrt(8)
+    t = (x @ A).astype(np.float32)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    runs = {}
+    fno.fno_set_tensor_path(0)
+    for name, net in (("gemm", fno.FNO2d(nr, nz, width, modes, layers, 8, 3, hidden, params=P)),
+                      ("fused", fno.make_fno(nr, nz, width, modes, layers, 8, 3, hidden, params=P))):
+        losses = []
+        for _ in range(15):
+            net.zero_grad()
+            losses.append(float(net.loss_and_grad(xd, td).item()))
+            net.adam_step(2e-3)
+        runs[name] = np.array(losses)
+    assert isinstance(net, fno.FusedFNO2d)
+    assert fno.fno_net_status(True) == 0
+    print("losses gemm", runs["gemm"][[0, -1]], "fused", runs["fused"][[0, -1]])
+    assert runs["fused"][-1] < 0.85 * runs["fused"][0]
+    assert np.all(np.abs(runs["fused"] / runs["gemm"] - 1) < 2e-2)
