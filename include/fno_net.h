@@ -27,8 +27,10 @@
  *
  * Every call is asynchronous on `stream` and returns 0, FNO_NET_ERR_INVALID (bad
  * argument) or FNO_NET_ERR_CUDA (launch failure); fno_net_last_error() gives the message.
- * No call allocates device memory.  Weight-gradient kernels write one partial sum per
- * CTA into caller buffers of fno_net_parts() slots, summed by fno_net_reduce.
+ * No call allocates device memory.  Gradients are added to the caller's FP32 buffers:
+ * each CTA sums its share in tensor or shared memory and adds the sum with FP32 atomics
+ * (the order of those additions, and so the last bits of a gradient, may vary from run
+ * to run).
  */
 #ifndef FNO_NET_H
 #define FNO_NET_H
@@ -49,14 +51,23 @@ typedef struct fno_net_dims {
 
 /* 1 if the fused kernels cover these sizes, else 0. */
 int fno_net_supported(const fno_net_dims *d);
-/* Number of partial-sum slots (one per CTA) the weight-gradient kernels write. */
-int fno_net_parts(const fno_net_dims *d);
 
 /* Operand image (BF16, tc.cuh layout) of an FP32 matrix: element (outer o, inner i) =
  * src[o * so + i * si] for o < O, i < I, zero for o < Opad, i < Ipad outside it.
  * Opad and Ipad multiples of 8. */
 int fno_net_pack(const float *src, int64_t so, int64_t si, int O, int I, void *dst, int Opad, int Ipad,
                  void *stream);
+
+/* Up to FNO_NET_PACK_MAX fno_net_pack jobs in one launch; `jobs` is host memory (copied
+ * into the launch), the pointers in it device memory. */
+#define FNO_NET_PACK_MAX 16
+typedef struct fno_net_pack_job {
+    const float *src;
+    int64_t so, si;
+    int32_t O, I, Opad, Ipad;
+    void *dst;
+} fno_net_pack_job;
+int fno_net_pack_many(const fno_net_pack_job *jobs, int n, void *stream);
 
 /* Forward pixel kernels, one CTA per group of 128 / C rows, nz / 128 tiles of 128 z each.
  * mode 0 (lift):  out = x P + p (x FP32 [batch][nr][nz][in_ch]; w_img = image of P^T,
@@ -72,26 +83,26 @@ int fno_net_fwd(int mode, const fno_net_dims *d, const float *x, const void *h, 
 
 /* Projection, one CTA per SM over tiles of 128 pixels: q = GELU(hL Q1 + q1), y = q Q2 + q2.
  * With t != NULL also the loss and the projection's backward: *loss (device double) +=
- * sum (y - t)^2 / (P out_ch); dhL = dL/dhL (BF16); per-CTA partials of dL/dQ1 (stored
- * transposed, [parts][hidden][C]), dL/dq1 [parts][hidden], dL/dQ2 [parts][hidden][out_ch]
- * and dL/dq2 [parts][out_ch].  Images: q1w (Q1^T: outer hidden, inner C), q1n (Q1: outer
- * C, inner hidden), q2w (Q2^T: outer 16, inner hidden), q2n (Q2: outer hidden, inner 16). */
+ * sum (y - t)^2 / (P out_ch); dhL = dL/dhL (BF16); dL/dQ1 ([C][hidden]), dL/dq1, dL/dQ2
+ * ([hidden][out_ch]) and dL/dq2 added to dQ1, dq1, dQ2, dq2.  Images: q1w (Q1^T: outer
+ * hidden, inner C), q1n (Q1: outer C, inner hidden), q2w (Q2^T: outer 16, inner hidden),
+ * q2n (Q2: outer hidden, inner 16). */
 int fno_net_proj(const fno_net_dims *d, const void *hL, const void *q1w, const void *q1n, const float *q1,
                  const void *q2w, const void *q2n, const float *q2, const float *t, float *y, void *dhL,
-                 double *loss, float *p_dQ1T, float *p_dq1, float *p_dQ2, float *p_dq2, void *stream);
+                 double *loss, float *dQ1, float *dq1, float *dQ2, float *dq2, void *stream);
 
 /* Backward pixel kernels (one CTA per SM over row groups).
  * mode 0 (last layer):  dpre = dpre_in (= dL/dh_L); dV = izDFT^T(dpre) (BF16 z-spectrum);
- *                       partials of dL/dW = h^T dpre [parts][C][C] and dL/db [parts][C].
+ *                       dL/dW = h^T dpre ([C][C]) and dL/db added to dW, db.
  * mode 1 (layer l > 0): dh = dpre_in W^T + zDFT^T(dZ) (dpre_in = dL/dpre_l, dZ the
  *                       z-spectrum gradient of layer l, wn_img = image of W_l: outer C
  *                       (c_in), inner C (c_out)); dpre_out = dh * GELU'(pre) (pre = pre_{l-1}),
  *                       then as mode 0 with h = h_{l-1} for layer l - 1.
- * mode 2 (layer 0):     dh0 = dpre_in W_0^T + zDFT^T(dZ); partials of dL/dP = x^T dh0
- *                       [parts][in_ch][C] (x FP32) and dL/dp [parts][C]. */
+ * mode 2 (layer 0):     dh0 = dpre_in W_0^T + zDFT^T(dZ); dL/dP = x^T dh0 ([in_ch][C], x
+ *                       FP32) and dL/dp added to dW, db. */
 int fno_net_bwd(int mode, const fno_net_dims *d, const void *dpre_in, const void *dZ, const void *wn_img,
                 const void *fz_img, const void *pre, const void *h, const float *x, const void *gzt_img,
-                void *dpre_out, void *dV, float *p_dW, float *p_db, void *stream);
+                void *dpre_out, void *dV, float *dW, float *db, void *stream);
 
 /* r transforms of one z-spectrum per (batch, kz):
  * fno_net_r2k: out (k-spectrum, FP32) = F2 in (in: BF16 z-spectrum), F2 = [[Cr, Sr], [-Sr, Cr]]
@@ -109,10 +120,6 @@ int fno_net_k2r(const fno_net_dims *d, const float *in, const void *f2i_img, voi
 int fno_net_mix_fwd(const fno_net_dims *d, const float *W, const float *R, float *Y, void *stream);
 int fno_net_mix_bwd(const fno_net_dims *d, const float *W, const float *R, const float *dY, float *dW, float *dR,
                     int accumulate, void *stream);
-
-/* out[i] (+)= sum over p < parts of part[p * n + i], i < n, or, with rows > 0, the
- * transposed sum out[c * rows + r] (+)= sum_p part[p * n + r * (n / rows) + c]. */
-int fno_net_reduce(const float *part, int parts, int64_t n, int rows, float *out, int accumulate, void *stream);
 
 /* Status of the bounded tensor-core waits, synchronous: 0 none ran out since the last
  * clear, 1 one ran out (that launch's output is invalid; each CTA waited for its issued

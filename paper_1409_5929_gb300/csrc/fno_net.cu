@@ -126,6 +126,23 @@ __global__ void k_pack(const float* __restrict__ src, int64_t so, int64_t si, in
     }
 }
 
+// Up to FNO_NET_PACK_MAX images in one launch (blockIdx.y = the job), jobs passed by value.
+struct PackJobs {
+    fno_net_pack_job j[FNO_NET_PACK_MAX];
+};
+
+__global__ void k_pack_many(const PackJobs jobs) {
+    const fno_net_pack_job& jb = jobs.j[blockIdx.y];
+    const int64_t n = (int64_t)jb.Opad * jb.Ipad;
+    const float* src = jb.src;
+    bf16* dst = (bf16*)jb.dst;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(idx / jb.Ipad), i = (int)(idx % jb.Ipad);
+        const float v = (o < jb.O && i < jb.I) ? src[o * jb.so + i * jb.si] : 0.f;
+        dst[tc::img_off(i, o, jb.Ipad) >> 1] = __float2bfloat16_rn(v);
+    }
+}
+
 // --------------------------------------------------------------- forward --
 struct FwdP {
     int nrows, nr, nz, ci;
@@ -325,10 +342,10 @@ struct ProjP {
     float* y;
     bf16* dhL;
     double* loss;
-    float* pQ1T;
-    float* pq1;
-    float* pQ2;
-    float* pq2;
+    float* gQ1;   // dL/dQ1 [C][H], added to
+    float* gq1;
+    float* gQ2;   // dL/dQ2 [H][CO]
+    float* gq2;
 };
 
 template <int C>
@@ -511,33 +528,23 @@ __global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
     }
     if (!ok) {
         recover(mbar, phase, pend, 1);
-    } else if (TRAIN) {
-        // this CTA's partial sums (zero if it had no tile)
-        const int j = 32 * q + lane, part = blockIdx.x;
+    } else if (TRAIN && !first) {
+        // this CTA's sums over its tiles, added to the gradients (FP32 atomics)
+        const int j = 32 * q + lane;
         for (int c0 = 32 * hh; c0 < HI; c0 += 64) {
             float v[32];
-            if (first) {
-#pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = 0.f;
-            } else {
-                tc::ld32(tc::taddr(tmem, q, D5 + c0), v);
-            }
+            tc::ld32(tc::taddr(tmem, q, D5 + c0), v);
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
                 const int c = c0 + i;
-                if (c < C) a.pQ1T[((int64_t)part * H + j) * C + c] = v[i];
-                else if (c == C) a.pq1[(int64_t)part * H + j] = v[i];
+                if (c < C) atomicAdd(&a.gQ1[(int64_t)c * H + j], v[i]);   // D5 holds dQ1^T
+                else if (c == C) atomicAdd(&a.gq1[j], v[i]);
             }
         }
         if (hh == 0) {
             float v[16];
-            if (first) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = 0.f;
-            } else {
-                tc::ld16(tc::taddr(tmem, q, D6), v);
-            }
-            for (int o = 0; o < a.CO; ++o) a.pQ2[((int64_t)part * H + j) * a.CO + o] = v[o];
+            tc::ld16(tc::taddr(tmem, q, D6), v);
+            for (int o = 0; o < a.CO; ++o) atomicAdd(&a.gQ2[(int64_t)j * a.CO + o], v[o]);
         }
 #pragma unroll
         for (int o = 0; o < 16; ++o) {
@@ -549,7 +556,7 @@ __global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
         for (int w = 16; w > 0; w >>= 1) l += __shfl_xor_sync(0xffffffffu, l, w);
         if (lane == 0) atomicAdd(&sloss, (double)l);
         __syncthreads();
-        if (tid < a.CO) a.pq2[(int64_t)part * a.CO + tid] = sdq2[tid];
+        if (tid < a.CO) atomicAdd(&a.gq2[tid], sdq2[tid]);
         if (tid == 0) atomicAdd(a.loss, sloss / ((double)a.P * a.CO));
     }
     tc::fence_before();
@@ -571,8 +578,8 @@ struct BwdP {
     const bf16* gzt;
     bf16* dpre_out;
     bf16* dV;
-    float* pdW;
-    float* pdb;
+    float* gW;   // dL/dW [C][C] (dL/dP [ci][C] for the lift), added to
+    float* gb;
 };
 
 template <int C, int KZ2, int MODE>
@@ -776,10 +783,11 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
         }
         if (HA && hh == 0) atomicAdd(&sdb[m % C], dbacc * a.db_scale);
         __syncthreads();
-        const int part = blockIdx.x;
-        const int rows = MODE == 2 ? a.ci : C;
-        for (int i = tid; i < rows * C; i += 256) a.pdW[(int64_t)part * rows * C + i] = sacc[i];
-        for (int i = tid; i < C; i += 256) a.pdb[(int64_t)part * C + i] = sdb[i];
+        if (!first) {   // this CTA's sums, added to the gradients (FP32 atomics)
+            const int rows = MODE == 2 ? a.ci : C;
+            for (int i = tid; i < rows * C; i += 256) atomicAdd(&a.gW[i], sacc[i]);
+            for (int i = tid; i < C; i += 256) atomicAdd(&a.gb[i], sdb[i]);
+        }
     }
     tc::fence_before();
     __syncthreads();
@@ -939,7 +947,11 @@ __global__ void k_mixb(const float* __restrict__ W, const float* __restrict__ R,
     float* sY = sW + 2 * B * C;
     const int kz = blockIdx.x / (2 * M), kr = blockIdx.x % (2 * M);
     const int64_t mode = (int64_t)kr * M + kz, slab = ((int64_t)kz * 2 * M + kr) * 2 * B * C;
-    for (int i = threadIdx.x; i < 2 * C * C; i += blockDim.x) sR[i] = R[mode * C * C * 2 + i];
+    // R[c][o] kept as [o][c]: the dW sums run over o with c across the threads
+    for (int i = threadIdx.x; i < 2 * C * C; i += blockDim.x) {
+        const int part = i & 1, co = i >> 1, c = co / C, o = co % C;
+        sR[(o * C + c) * 2 + part] = R[mode * C * C * 2 + i];
+    }
     for (int i = threadIdx.x; i < 2 * B * C; i += blockDim.x) {
         sW[i] = W[slab + i];
         sY[i] = dY[slab + i];
@@ -950,7 +962,7 @@ __global__ void k_mixb(const float* __restrict__ W, const float* __restrict__ R,
         float gr = 0.f, gi = 0.f;
         for (int o = 0; o < C; ++o) {
             const float yr = sY[bb * C + o], yi = sY[(B + bb) * C + o];
-            const float rr = sR[(c * C + o) * 2], ri = sR[(c * C + o) * 2 + 1];
+            const float rr = sR[(o * C + c) * 2], ri = sR[(o * C + c) * 2 + 1];
             gr += yr * rr + yi * ri;
             gi += -yr * ri + yi * rr;
         }
@@ -969,20 +981,6 @@ __global__ void k_mixb(const float* __restrict__ W, const float* __restrict__ R,
         float* d = dR + (mode * C * C + i) * 2;
         d[0] = accumulate ? d[0] + gr : gr;
         d[1] = accumulate ? d[1] + gi : gi;
-    }
-}
-
-__global__ void k_reduce(const float* __restrict__ part, int parts, int64_t n, int rows, float* __restrict__ out,
-                         int accumulate) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int p = 0; p < parts; ++p) s += part[(int64_t)p * n + i];
-        int64_t o = i;
-        if (rows > 0) {
-            const int64_t cols = n / rows, r = i / cols, c = i % cols;
-            o = c * rows + r;
-        }
-        out[o] = accumulate ? out[o] + s : s;
     }
 }
 
@@ -1028,12 +1026,6 @@ extern "C" {
 
 int fno_net_supported(const fno_net_dims* d) { return dims_ok(d, nullptr) ? 1 : 0; }
 
-int fno_net_parts(const fno_net_dims* d) {
-    (void)d;
-    const int n = sms();
-    return n > 0 ? n : 1;
-}
-
 int fno_net_pack(const float* src, int64_t so, int64_t si, int O, int I, void* dst, int Opad, int Ipad, void* stream) {
     if (!src || !dst || O < 0 || I < 0 || O > Opad || I > Ipad || Opad % 8 || Ipad % 8)
         return fail(FNO_NET_ERR_INVALID, "fno_net_pack: bad arguments");
@@ -1050,6 +1042,24 @@ int fno_net_pack(const float* src, int64_t so, int64_t si, int O, int I, void* d
 // tcgen05.alloc until another one on the SM finishes.  k_fwd: 256 columns, at most two CTAs
 // per SM; k_proj, k_bwd: 512 columns, one; k_k2r: up to 64 columns, at most seven.
 constexpr size_t SMEM_2_PER_SM = 80 * 1024, SMEM_1_PER_SM = 120 * 1024, SMEM_7_PER_SM = 32 * 1024;
+
+int fno_net_pack_many(const fno_net_pack_job* jobs, int n, void* stream) {
+    if (!jobs || n < 1 || n > FNO_NET_PACK_MAX) return fail(FNO_NET_ERR_INVALID, "fno_net_pack_many: 1 <= n <= %d", FNO_NET_PACK_MAX);
+    PackJobs pj{};
+    int64_t most = 0;
+    for (int k = 0; k < n; ++k) {
+        const fno_net_pack_job& j = jobs[k];
+        if (!j.src || !j.dst || j.O < 0 || j.I < 0 || j.O > j.Opad || j.I > j.Ipad || j.Opad % 8 || j.Ipad % 8)
+            return fail(FNO_NET_ERR_INVALID, "fno_net_pack_many: bad job %d", k);
+        pj.j[k] = j;
+        most = std::max(most, (int64_t)j.Opad * j.Ipad);
+    }
+    if (most == 0) return FNO_NET_OK;
+    const dim3 grid((unsigned)std::min<int64_t>((most + 255) / 256, 256), (unsigned)n);
+    k_pack_many<<<grid, 256, 0, (cudaStream_t)stream>>>(pj);
+    NCK(cudaGetLastError());
+    return FNO_NET_OK;
+}
 
 #define FWD_CASE(C_, K_, MODE_)                                                                         \
     if (d->width == C_ && 2 * d->modes == K_ && mode == MODE_) {                                       \
@@ -1083,18 +1093,17 @@ int fno_net_fwd(int mode, const fno_net_dims* d, const float* x, const void* h, 
 
 int fno_net_proj(const fno_net_dims* d, const void* hL, const void* q1w, const void* q1n, const float* q1,
                  const void* q2w, const void* q2n, const float* q2, const float* t, float* y, void* dhL, double* loss,
-                 float* p_dQ1T, float* p_dq1, float* p_dQ2, float* p_dq2, void* stream) {
+                 float* dQ1, float* dq1, float* dQ2, float* dq2, void* stream) {
     std::string why;
     if (!dims_ok(d, &why)) return fail(FNO_NET_ERR_INVALID, "fno_net_proj: %s", why.c_str());
     if (!hL || !q1w || !q1 || !q2w || !q2 || !y ||
-        (t && (!q1n || !q2n || !dhL || !loss || !p_dQ1T || !p_dq1 || !p_dQ2 || !p_dq2)))
+        (t && (!q1n || !q2n || !dhL || !loss || !dQ1 || !dq1 || !dQ2 || !dq2)))
         return fail(FNO_NET_ERR_INVALID, "fno_net_proj: missing argument");
     const int64_t P = (int64_t)d->batch * d->nr * d->nz;
     ProjP p{(int)P, d->out_ch, (float)(2.0 / ((double)P * d->out_ch)), (const bf16*)hL, (const bf16*)q1w,
             (const bf16*)q1n, q1, (const bf16*)q2w, (const bf16*)q2n, q2, t, y, (bf16*)dhL, loss,
-            p_dQ1T, p_dq1, p_dQ2, p_dq2};
-    // every partial slot is written: one CTA per slot
-    const unsigned grid = t ? (unsigned)fno_net_parts(d) : (unsigned)std::min<int64_t>(P / 128, sms());
+            dQ1, dq1, dQ2, dq2};
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(P / 128, sms()));
     cudaStream_t s = (cudaStream_t)stream;
     if (d->width == 32) {
         const size_t sb = std::max(ProjSmem<32>::bytes, SMEM_1_PER_SM);
@@ -1129,16 +1138,16 @@ int fno_net_proj(const fno_net_dims* d, const void* hL, const void* q1w, const v
 
 int fno_net_bwd(int mode, const fno_net_dims* d, const void* dpre_in, const void* dZ, const void* wn_img,
                 const void* fz_img, const void* pre, const void* h, const float* x, const void* gzt_img, void* dpre_out,
-                void* dV, float* p_dW, float* p_db, void* stream) {
+                void* dV, float* dW, float* db, void* stream) {
     std::string why;
     if (!dims_ok(d, &why)) return fail(FNO_NET_ERR_INVALID, "fno_net_bwd: %s", why.c_str());
-    if (mode < 0 || mode > 2 || !dpre_in || !p_dW || !p_db || (mode != 0 && (!dZ || !wn_img || !fz_img)) ||
+    if (mode < 0 || mode > 2 || !dpre_in || !dW || !db || (mode != 0 && (!dZ || !wn_img || !fz_img)) ||
         (mode == 1 && (!pre || !dpre_out)) || (mode != 2 && (!h || !gzt_img || !dV)) || (mode == 2 && !x))
         return fail(FNO_NET_ERR_INVALID, "fno_net_bwd: missing argument for mode %d", mode);
     BwdP p{d->batch * d->nr, d->nr, d->nz, d->in_ch, (float)((double)d->nr * d->nz), (const bf16*)dpre_in,
            (const bf16*)dZ, (const bf16*)wn_img, (const bf16*)fz_img, (const bf16*)pre, (const bf16*)h, x,
-           (const bf16*)gzt_img, (bf16*)dpre_out, (bf16*)dV, p_dW, p_db};
-    const unsigned grid = (unsigned)fno_net_parts(d);   // every partial slot is written
+           (const bf16*)gzt_img, (bf16*)dpre_out, (bf16*)dV, dW, db};
+    const unsigned grid = (unsigned)std::max(1, std::min(p.nrows / (128 / d->width), sms()));
     cudaStream_t s = (cudaStream_t)stream;
     bool launched = false;
     BWD_CASE(32, 32, 0) BWD_CASE(32, 32, 1) BWD_CASE(32, 32, 2)
@@ -1211,16 +1220,6 @@ int fno_net_mix_bwd(const fno_net_dims* d, const float* W, const float* R, const
     if (int rc = set_smem(k_mixb, sb)) return rc;
     k_mixb<<<(unsigned)(2 * d->modes * d->modes), 256, sb, (cudaStream_t)stream>>>(W, R, dY, dW, dR, B, C, d->modes,
                                                                                      accumulate);
-    NCK(cudaGetLastError());
-    return FNO_NET_OK;
-}
-
-int fno_net_reduce(const float* part, int parts, int64_t n, int rows, float* out, int accumulate, void* stream) {
-    if (!part || !out || parts < 1 || n < 0 || rows < 0 || (rows > 0 && n % rows))
-        return fail(FNO_NET_ERR_INVALID, "fno_net_reduce: bad arguments");
-    if (n == 0) return FNO_NET_OK;
-    k_reduce<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, (cudaStream_t)stream>>>(part, parts, n,
-                                                                                                   rows, out, accumulate);
     NCK(cudaGetLastError());
     return FNO_NET_OK;
 }

@@ -396,8 +396,8 @@ FNO_NET_LIB_PATH = os.path.join(HERE, "libfnonet.so")
 _net_lib = None
 _NET_SIGS = {
     "fno_net_supported": [_vp],
-    "fno_net_parts": [_vp],
     "fno_net_pack": [_vp, _i64, _i64, C.c_int, C.c_int, _vp, C.c_int, C.c_int, _vp],
+    "fno_net_pack_many": [_vp, C.c_int, _vp],
     "fno_net_fwd": [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fno_net_proj": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fno_net_bwd": [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -405,13 +405,17 @@ _NET_SIGS = {
     "fno_net_k2r": [_vp, _vp, _vp, _vp, _vp],
     "fno_net_mix_fwd": [_vp, _vp, _vp, _vp, _vp],
     "fno_net_mix_bwd": [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp],
-    "fno_net_reduce": [_vp, C.c_int, _i64, C.c_int, _vp, C.c_int, _vp],
     "fno_net_status": [C.c_int],
 }
 
 
 class fno_net_dims(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("batch", "nr", "nz", "width", "modes", "hidden", "in_ch", "out_ch")]
+
+
+class fno_net_pack_job(C.Structure):
+    _fields_ = [("src", _vp), ("so", _i64), ("si", _i64), ("O", C.c_int32), ("I", C.c_int32),
+                ("Opad", C.c_int32), ("Ipad", C.c_int32), ("dst", _vp)]
 
 
 def load_net():
@@ -448,8 +452,9 @@ def fno_net_status(clear: bool = True) -> int:
 
 class FusedFNO2d:
     """The operator of FNO2d on the fused tcgen05 kernels of libfnonet.so: BF16
-    activations, FP32 master weights and Adam state (same layouts as FNO2d), BF16 operand
-    images of the weights refreshed after every update.  Torch provides device buffers
+    activations, FP32 master weights and Adam state (same layouts as FNO2d, views into one
+    flat buffer each, so that one Adam launch updates them all), BF16 operand images of the
+    weights refreshed by one launch after every update.  Torch provides device buffers
     only; every step runs in libfnonet.so (and Adam in libfno.so)."""
 
     def __init__(self, nr, nz, width=32, modes=16, layers=4, in_ch=8, out_ch=3, hidden=128, seed=0, params=None):
@@ -462,10 +467,16 @@ class FusedFNO2d:
             raise ValueError("sizes outside the fused kernels' range (include/fno_net.h)")
         P = params if params is not None else init_params(nr, nz, width, modes, layers, in_ch, out_ch, hidden, seed)
         dev = "cuda"
-        self.w = {k: torch.tensor(np.ascontiguousarray(v, dtype=np.float32), device=dev) for k, v in P.items()}
-        self.g = {k: torch.zeros_like(v) for k, v in self.w.items()}
-        self.adam_m = {k: torch.zeros_like(v) for k, v in self.w.items()}
-        self.adam_v = {k: torch.zeros_like(v) for k, v in self.w.items()}
+        total = sum(int(np.prod(v.shape)) for v in P.values())
+        self._flat = {n: torch.zeros(total, dtype=torch.float32, device=dev) for n in ("w", "g", "m", "v")}
+        self.w, self.g, self.adam_m, self.adam_v = {}, {}, {}, {}
+        off = 0
+        for k, v in P.items():
+            n = int(np.prod(v.shape))
+            for name, d in (("w", self.w), ("g", self.g), ("m", self.adam_m), ("v", self.adam_v)):
+                d[k] = self._flat[name][off:off + n].view(v.shape)
+            self.w[k].copy_(torch.tensor(np.ascontiguousarray(v, dtype=np.float32), device=dev))
+            off += n
         self.step_count = 0
         load()
         load_net()
@@ -492,21 +503,31 @@ class FusedFNO2d:
         _ncheck(load_net().fno_net_pack(src.data_ptr(), so, si, O, I, out.data_ptr(), Opad, Ipad, _stream()))
         return out
 
+    def _pack_jobs(self):
+        """The weight images as one table of pack jobs (built once: the weights are views
+        into the flat buffer and the images never move)."""
+        import torch
+
+        C, H, CI, CO, w, im = self.width, self.hidden, self.in_ch, self.out_ch, self.w, self.img
+        spec = [("P", w["P"], 1, C, C, CI, C, 16)]                                   # P^T: (c, ci)
+        for l in range(self.L):
+            spec.append((f"Wf{l}", w[f"W{l}"], 1, C, C, C, C, C))                   # W^T: (c_out, c_in)
+            spec.append((f"Wn{l}", w[f"W{l}"], C, 1, C, C, C, C))                   # W: (c_in, c_out)
+        spec += [("q1w", w["Q1"], 1, H, H, C, H, C), ("q1n", w["Q1"], H, 1, C, H, C, H),   # Q1^T, Q1
+                 ("q2w", w["Q2"], 1, CO, CO, H, 16, H), ("q2n", w["Q2"], CO, 1, H, CO, H, 16)]   # Q2^T, Q2
+        jobs = (fno_net_pack_job * len(spec))()
+        for j, (name, src, so, si, O, I, Op, Ip) in enumerate(spec):
+            im[name] = torch.empty(Op * Ip, dtype=torch.bfloat16, device="cuda")
+            jobs[j] = fno_net_pack_job(src.data_ptr(), so, si, O, I, Op, Ip, im[name].data_ptr())
+        return jobs
+
     def _refresh_images(self):
         """BF16 operand images of the current FP32 weights (after every update)."""
         if not self._dirty:
             return
-        C, H, CI, CO, w = self.width, self.hidden, self.in_ch, self.out_ch, self.w
-        im = self.img
-        im["P"] = self._pack(w["P"], 1, C, C, CI, C, 16, im.get("P"))                  # P^T: (c, ci)
-        for l in range(self.L):
-            W = w[f"W{l}"]
-            im[f"Wf{l}"] = self._pack(W, 1, C, C, C, C, C, im.get(f"Wf{l}"))          # W^T: (c_out, c_in)
-            im[f"Wn{l}"] = self._pack(W, C, 1, C, C, C, C, im.get(f"Wn{l}"))          # W: (c_in, c_out)
-        im["q1w"] = self._pack(w["Q1"], 1, H, H, C, H, C, im.get("q1w"))              # Q1^T: (j, c)
-        im["q1n"] = self._pack(w["Q1"], H, 1, C, H, C, H, im.get("q1n"))              # Q1: (c, j)
-        im["q2w"] = self._pack(w["Q2"], 1, CO, CO, H, 16, H, im.get("q2w"))           # Q2^T: (o, j)
-        im["q2n"] = self._pack(w["Q2"], CO, 1, H, CO, H, 16, im.get("q2n"))           # Q2: (j, o)
+        if getattr(self, "_jobs", None) is None:
+            self._jobs = self._pack_jobs()
+        _ncheck(load_net().fno_net_pack_many(self._jobs, len(self._jobs), _stream()))
         self._dirty = False
 
     def _dims(self, B):
@@ -568,29 +589,18 @@ class FusedFNO2d:
                                      im["q2w"].data_ptr(), None, w["q2"].data_ptr(), None, y.data_ptr(), None, None,
                                      None, None, None, None, s))
             return y
-        parts = lib.fno_net_parts(dp)
-        H, CO = self.hidden, self.out_ch
-        pQ1 = self._b("pQ1", (parts, H, Cw), torch.float32)
-        pq1 = self._b("pq1", (parts, H), torch.float32)
-        pQ2 = self._b("pQ2", (parts, H, CO), torch.float32)
-        pq2 = self._b("pq2", (parts, CO), torch.float32)
         dhL = self._b("dhL", act)
         lbuf = self._b("lossd", (1,), torch.float64)
         lbuf.zero_()
+        g = self.g
         _ncheck(lib.fno_net_proj(dp, h[L].data_ptr(), im["q1w"].data_ptr(), im["q1n"].data_ptr(), w["q1"].data_ptr(),
                                  im["q2w"].data_ptr(), im["q2n"].data_ptr(), w["q2"].data_ptr(), t.data_ptr(),
-                                 y.data_ptr(), dhL.data_ptr(), lbuf.data_ptr(), pQ1.data_ptr(), pq1.data_ptr(),
-                                 pQ2.data_ptr(), pq2.data_ptr(), s))
-        g = self.g
-        _ncheck(lib.fno_net_reduce(pQ1.data_ptr(), parts, H * Cw, H, g["Q1"].data_ptr(), 1, s))
-        _ncheck(lib.fno_net_reduce(pq1.data_ptr(), parts, H, 0, g["q1"].data_ptr(), 1, s))
-        _ncheck(lib.fno_net_reduce(pQ2.data_ptr(), parts, H * CO, 0, g["Q2"].data_ptr(), 1, s))
-        _ncheck(lib.fno_net_reduce(pq2.data_ptr(), parts, CO, 0, g["q2"].data_ptr(), 1, s))
+                                 y.data_ptr(), dhL.data_ptr(), lbuf.data_ptr(), g["Q1"].data_ptr(), g["q1"].data_ptr(),
+                                 g["Q2"].data_ptr(), g["q2"].data_ptr(), s))
         return y
 
     def zero_grad(self):
-        for g in self.g.values():
-            g.zero_()
+        self._flat["g"].zero_()
 
     def _backward_layers(self, x, B):
         import torch
@@ -604,24 +614,16 @@ class FusedFNO2d:
         act = (B, nr, nz, Cw)
         zs = (B, M, 2, nr, Cw)
         ks = (M, 2 * M, 2, B, Cw)
-        parts = lib.fno_net_parts(dp)
-        pdW = self._b("pdW", (parts, Cw, Cw), torch.float32)
-        pdb = self._b("pdb", (parts, Cw), torch.float32)
         dV = self._b("dV", zs)
         dZ = self._b("dZ", zs)
         dYk = self._b("dYk", ks, torch.float32)
         dWk = self._b("dWk", ks, torch.float32)
         dpre = [self._b("dpre_a", act), self._b("dpre_b", act)]
         h = [self._buf[f"h{l}"] for l in range(L + 1)]
-
-        def red(name_w, name_b, rows):
-            _ncheck(lib.fno_net_reduce(pdW.data_ptr(), parts, rows * Cw, 0, g[name_w].data_ptr(), 1, s))
-            _ncheck(lib.fno_net_reduce(pdb.data_ptr(), parts, Cw, 0, g[name_b].data_ptr(), 1, s))
-
         cur = self._buf["dhL"]   # dL/dpre_{L-1} (h_L = pre_{L-1})
         _ncheck(lib.fno_net_bwd(0, dp, cur.data_ptr(), None, None, None, None, h[L - 1].data_ptr(), None,
-                                im["gzt"].data_ptr(), None, dV.data_ptr(), pdW.data_ptr(), pdb.data_ptr(), s))
-        red(f"W{L - 1}", f"b{L - 1}", Cw)
+                                im["gzt"].data_ptr(), None, dV.data_ptr(), g[f"W{L - 1}"].data_ptr(),
+                                g[f"b{L - 1}"].data_ptr(), s))
         for l in range(L - 1, -1, -1):
             _ncheck(lib.fno_net_r2k(dp, dV.data_ptr(), im["f2"].data_ptr(), dYk.data_ptr(), s))
             _ncheck(lib.fno_net_mix_bwd(dp, self._buf[f"Wk{l}"].data_ptr(), w[f"R{l}"].data_ptr(), dYk.data_ptr(),
@@ -631,15 +633,13 @@ class FusedFNO2d:
                 nxt = dpre[l % 2]
                 _ncheck(lib.fno_net_bwd(1, dp, cur.data_ptr(), dZ.data_ptr(), im[f"Wn{l}"].data_ptr(),
                                         im["fz"].data_ptr(), self._buf[f"pre{l - 1}"].data_ptr(), h[l - 1].data_ptr(),
-                                        None, im["gzt"].data_ptr(), nxt.data_ptr(), dV.data_ptr(), pdW.data_ptr(),
-                                        pdb.data_ptr(), s))
-                red(f"W{l - 1}", f"b{l - 1}", Cw)
+                                        None, im["gzt"].data_ptr(), nxt.data_ptr(), dV.data_ptr(),
+                                        g[f"W{l - 1}"].data_ptr(), g[f"b{l - 1}"].data_ptr(), s))
                 cur = nxt
             else:
                 _ncheck(lib.fno_net_bwd(2, dp, cur.data_ptr(), dZ.data_ptr(), im["Wn0"].data_ptr(),
                                         im["fz"].data_ptr(), None, None, x.data_ptr(), None, None, None,
-                                        pdW.data_ptr(), pdb.data_ptr(), s))
-                red("P", "p", self.in_ch)
+                                        g["P"].data_ptr(), g["p"].data_ptr(), s))
 
     def loss_and_grad(self, x, t):
         """MSE loss (device double) and parameter gradients (accumulated into self.g) of
@@ -652,8 +652,8 @@ class FusedFNO2d:
 
     def adam_step(self, lr, b1=0.9, b2=0.999, eps=1e-8):
         self.step_count += 1
-        for k in self.w:
-            fno_adam(self.w[k], self.g[k], self.adam_m[k], self.adam_v[k], lr, b1, b2, eps, self.step_count)
+        f = self._flat
+        fno_adam(f["w"], f["g"], f["m"], f["v"], lr, b1, b2, eps, self.step_count)
         self._dirty = True
 
 

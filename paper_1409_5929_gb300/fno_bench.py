@@ -81,6 +81,7 @@ def main():
     ap.add_argument("--nz", type=int, default=256)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--fused-only", action="store_true", help="time only the fused path (profiling)")
     a = ap.parse_args()
     hbm, tc, src = _peaks()
     rng = np.random.default_rng(0)
@@ -88,7 +89,7 @@ def main():
     t = torch.tensor(rng.normal(size=(a.batch, a.nr, a.nz, 3)).astype(np.float32), device="cuda")
     out = {"workload": f"FNO training step, batch {a.batch} x {a.nr} x {a.nz}, width 32, 16 modes, 4 layers",
            "peaks": {"hbm_gbs": hbm, "bf16_tflops": tc, "source": src}, "paths": {}}
-    for path, name in ((0, "mma.sync"), (1, "tcgen05")):
+    for path, name in ((0, "mma.sync"), (1, "tcgen05")) if not a.fused_only else ():
         F.fno_set_tensor_path(path)
         net = F.FNO2d(a.nr, a.nz, seed=1)
         for _ in range(3):
