@@ -355,8 +355,16 @@ struct ProjSmem {
                                     128 * 16 * 2 + (H + 16) * 4 + 16 * 4 + 1024;
 };
 
+// Tensor-memory columns of k_proj: q_pre, then (same columns) the raw dq; y; dQ2; dh;
+// [dQ1^T | dq1].  Width 32 fits 256 columns (two CTAs per SM), width 64 takes 512.
+template <int C>
+struct ProjCols {
+    static constexpr int TCOLS = C == 32 ? 256 : 512;
+    static constexpr int D1 = 0, D3 = 0, D2 = 128, D6 = 144, D4 = 160, D5 = C == 32 ? 192 : 256;
+};
+
 template <int C, bool TRAIN>
-__global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
+__global__ void __launch_bounds__(256, C == 32 ? 2 : 1) k_proj(const ProjP a) {
     constexpr int H = 128, HI = ProjSmem<C>::HI;
     extern __shared__ uint8_t dsm[];
     uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -376,10 +384,10 @@ __global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
     __shared__ double sloss;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hh = warp >> 2;
-    // tensor-memory columns: q_pre, y, dh, [dQ1^T | dq1], dQ2, dq
-    constexpr int D1 = 0, D2 = 128, D4 = 160, D5 = 256, D6 = 352, D3 = 384;
+    using TC = ProjCols<C>;
+    constexpr int D1 = TC::D1, D2 = TC::D2, D3 = TC::D3, D4 = TC::D4, D5 = TC::D5, D6 = TC::D6;
 
-    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (warp == 0) tc::tmem_alloc(&tslot, TC::TCOLS);
     if (tid == 0) {
         tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -445,14 +453,22 @@ __global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
             break;
         const int p = 32 * q + lane;
 #pragma unroll 1
-        for (int jc = 0; jc < 2; ++jc) {   // q = GELU(q_pre)
+        for (int jc = 0; jc < 2; ++jc) {   // q = GELU(q_pre) into sQI; GELU'(q_pre) into sDQ
             const int col0 = 64 * hh + 32 * jc;
             float v[32];
             tc::ld32(tc::taddr(tmem, q, D1 + col0), v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = gelu(v[i] + sq1[col0 + i]);
+            for (int k = 0; k < 4; ++k) {
+                float gq[8], gd[8];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) st16(sQI + tc::img_off(col0 + 8 * k, p, H), pack8(v + 8 * k));
+                for (int i = 0; i < 8; ++i) {
+                    const float x = v[8 * k + i] + sq1[col0 + 8 * k + i];
+                    gq[i] = gelu(x);
+                    gd[i] = gelu_d(x);
+                }
+                st16(sQI + tc::img_off(col0 + 8 * k, p, H), pack8(gq));
+                if (TRAIN) st16(sDQ + tc::img_off(col0 + 8 * k, p, H), pack8(gd));
+            }
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -497,15 +513,19 @@ __global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
               })))
             break;
 #pragma unroll 1
-        for (int jc = 0; jc < 2; ++jc) {   // dq = (dy Q2^T) GELU'(q_pre)
+        for (int jc = 0; jc < 2; ++jc) {   // dq = (dy Q2^T) GELU'(q_pre), in place of GELU'
             const int col0 = 64 * hh + 32 * jc;
-            float g[32], v[32];
+            float g[32];
             tc::ld32(tc::taddr(tmem, q, D3 + col0), g);
-            tc::ld32(tc::taddr(tmem, q, D1 + col0), v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) g[i] *= gelu_d(v[i] + sq1[col0 + i]);
+            for (int k = 0; k < 4; ++k) {
+                uint8_t* at = sDQ + tc::img_off(col0 + 8 * k, p, H);
+                float gd[8];
+                unpack8(*reinterpret_cast<const uint4*>(at), gd);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) st16(sDQ + tc::img_off(col0 + 8 * k, p, H), pack8(g + 8 * k));
+                for (int i = 0; i < 8; ++i) gd[i] *= g[8 * k + i];
+                st16(at, pack8(gd));
+            }
         }
         tc::fence_async_smem();
         tc::fence_before();
@@ -544,7 +564,9 @@ __global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
         if (hh == 0) {
             float v[16];
             tc::ld16(tc::taddr(tmem, q, D6), v);
-            for (int o = 0; o < a.CO; ++o) atomicAdd(&a.gQ2[(int64_t)j * a.CO + o], v[o]);
+#pragma unroll
+            for (int o = 0; o < 16; ++o)
+                if (o < a.CO) atomicAdd(&a.gQ2[(int64_t)j * a.CO + o], v[o]);
         }
 #pragma unroll
         for (int o = 0; o < 16; ++o) {
@@ -561,12 +583,13 @@ __global__ void __launch_bounds__(256, 1) k_proj(const ProjP a) {
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(tmem, 512);
+    if (warp == 0) tc::tmem_free(tmem, TC::TCOLS);
 }
 
 // -------------------------------------------------------------- backward --
 struct BwdP {
     int nrows, nr, nz, ci;
+    int nbuf;         // 2: the next tile's inputs load while the current one computes
     float db_scale;   // nr nz: the kz = 0 coefficient of Gz is 1 / (nr nz)
     const bf16* dpre_in;
     const bf16* dZ;
@@ -586,9 +609,12 @@ template <int C, int KZ2, int MODE>
 struct BwdSmem {
     static constexpr int G = 128 / C;
     static constexpr bool HB = MODE != 0, HA = MODE != 2;
-    static size_t bytes(int nz) {
-        return (HB ? (size_t)128 * 128 * 2 + C * C * 2 + (size_t)nz * KZ2 * 2 + (size_t)G * KZ2 * C * 2 : 0) +
-               (size_t)128 * 128 * 2 * 2 + (HA ? (size_t)nz * KZ2 * 2 : 0) + (size_t)C * C * 4 + C * 4 + 1024;
+    static constexpr size_t TILE = 128 * 128 * 2;
+    // input tiles (dpre_in, or in mode 0 the gradient itself, and h or x) times nbuf
+    static size_t bytes(int nz, int nbuf) {
+        return (HB ? TILE * nbuf + C * C * 2 + (size_t)nz * KZ2 * 2 + (size_t)G * KZ2 * C * 2 : 0) +
+               TILE * (HB ? 1 : nbuf) + TILE * nbuf + (HA ? (size_t)nz * KZ2 * 2 : 0) + (size_t)C * C * 4 + C * 4 +
+               1024;
     }
 };
 
@@ -600,13 +626,15 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
     constexpr int M = KZ2 / 2;
     extern __shared__ uint8_t dsm[];
     uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
-    uint8_t* sDP = sm;                                        // dpre_l tile (B part)
-    uint8_t* sWN = sDP + (HB ? 128 * 128 * 2 : 0);
+    constexpr int TILE = (int)S::TILE;
+    const int nbuf = a.nbuf;
+    uint8_t* sDP = sm;                                        // dpre_l tiles (B part), nbuf of them
+    uint8_t* sWN = sDP + (HB ? TILE * nbuf : 0);
     uint8_t* sF = sWN + (HB ? C * C * 2 : 0);
     uint8_t* sdZ = sF + (HB ? a.nz * KZ2 * 2 : 0);
-    uint8_t* sD2 = sdZ + (HB ? G * KZ2 * C * 2 : 0);          // the gradient the A part uses
-    uint8_t* sH = sD2 + 128 * 128 * 2;                        // h_{l-1} tile, or x with ones
-    uint8_t* sG = sH + 128 * 128 * 2;
+    uint8_t* sD2 = sdZ + (HB ? G * KZ2 * C * 2 : 0);          // the gradient the A part uses (nbuf in mode 0)
+    uint8_t* sH = sD2 + TILE * (HB ? 1 : nbuf);               // h_{l-1} tiles, or x with ones, nbuf of them
+    uint8_t* sG = sH + TILE * nbuf;
     float* sacc = reinterpret_cast<float*>(sG + (HA ? a.nz * KZ2 * 2 : 0));   // C x C
     float* sdb = sacc + C * C;
     __shared__ __align__(8) uint64_t mbar[2];
@@ -628,17 +656,17 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
     if (HA) cp_flat(sG, a.gzt, a.nz * KZ2 * 2, tid, 256);
     for (int i = tid; i < C * C; i += 256) sacc[i] = 0.f;
     for (int i = tid; i < C; i += 256) sdb[i] = 0.f;
-    if (MODE == 2) {   // per row block of the x image: x (16) | ones (8) | zeros
-        for (int i = tid; i < 128 * G; i += 256) {
-            const int z = i % 128, rl = i / 128;
+    if (MODE == 2) {   // per row block of each x image: x (16) | ones (8) | zeros
+        for (int i = tid; i < 128 * G * nbuf; i += 256) {
+            const int z = i % 128, rl = (i / 128) % G, bf = i / (128 * G);
             float one[8], zero[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 one[k] = 1.f;
                 zero[k] = 0.f;
             }
-            st16(sH + tc::img_off(rl * C + 16, z, 128), pack8(one));
-            for (int c = 24; c < C; c += 8) st16(sH + tc::img_off(rl * C + c, z, 128), pack8(zero));
+            st16(sH + bf * TILE + tc::img_off(rl * C + 16, z, 128), pack8(one));
+            for (int c = 24; c < C; c += 8) st16(sH + bf * TILE + tc::img_off(rl * C + c, z, 128), pack8(zero));
         }
     }
     tc::fence_before();
@@ -652,9 +680,37 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
     float dbacc = 0.f;
     const int ngroups = a.nrows / G, ntz = a.nz / 128;
 
-    for (int g = blockIdx.x; g < ngroups && ok; g += gridDim.x) {
-        const int R0 = g * G, b = R0 / a.nr, r0 = R0 % a.nr;
-        if (HB) {
+    // this CTA's work: its row groups g = blockIdx.x + j gridDim.x, each in ntz z tiles
+    const int my_groups = (int)blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nwork = my_groups * ntz;
+    auto load_tile = [&](int w, int bf) {   // input tiles of work item w into buffer bf
+        const int R0 = (blockIdx.x + (w / ntz) * gridDim.x) * G, z0 = (w % ntz) * 128;
+        for (int i = tid; i < 128 * G * (C / 8); i += 256) {
+            const int c8 = i % (C / 8), t2 = i / (C / 8), z = t2 % 128, rl = t2 / 128;
+            const int64_t off = ((int64_t)(R0 + rl) * a.nz + z0 + z) * C + c8 * 8;
+            const uint32_t so = bf * TILE + tc::img_off(rl * C + c8 * 8, z, 128);
+            if (HB) tc::cp16(tc::smem_u32(sDP + so), a.dpre_in + off);
+            else tc::cp16(tc::smem_u32(sD2 + so), a.dpre_in + off);
+            if (HA) tc::cp16(tc::smem_u32(sH + so), a.h + off);
+        }
+        if (MODE == 2) {
+            for (int i = tid; i < 128 * G; i += 256) {
+                const int z = i % 128, rl = i / 128;
+                const float* src = a.x + ((int64_t)(R0 + rl) * a.nz + z0 + z) * a.ci;
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = j < a.ci ? src[j] : 0.f;
+                st16(sH + bf * TILE + tc::img_off(rl * C, z, 128), pack8(v));
+                st16(sH + bf * TILE + tc::img_off(rl * C + 8, z, 128), pack8(v + 8));
+            }
+        }
+    };
+    if (nwork > 0) load_tile(0, 0);
+    for (int w = 0; w < nwork && ok; ++w) {
+        const int bf = nbuf == 2 ? (w & 1) : 0;
+        const int g = blockIdx.x + (w / ntz) * gridDim.x, t = w % ntz;
+        const int R0 = g * G, b = R0 / a.nr, r0 = R0 % a.nr, z0 = t * 128;
+        if (HB && t == 0) {   // the group's dZ rows (the previous tile's MMAs have completed)
             for (int i = tid; i < G * KZ2 * (C / 8); i += 256) {
                 const int c8 = i % (C / 8), t2 = i / (C / 8), kz2 = t2 % KZ2, rl = t2 / KZ2;
                 const int part = kz2 / M, kz = kz2 % M;
@@ -662,88 +718,82 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
                 tc::cp16(tc::smem_u32(sdZ + rl * (KZ2 * C * 2) + tc::img_off(c8 * 8, kz2, C)), src);
             }
         }
-        for (int t = 0; t < ntz && ok; ++t) {
-            const int z0 = t * 128;
-            for (int i = tid; i < 128 * G * (C / 8); i += 256) {
-                const int c8 = i % (C / 8), t2 = i / (C / 8), z = t2 % 128, rl = t2 / 128;
-                const int64_t off = ((int64_t)(R0 + rl) * a.nz + z0 + z) * C + c8 * 8;
-                const uint32_t so = tc::img_off(rl * C + c8 * 8, z, 128);
-                if (HB) tc::cp16(tc::smem_u32(sDP + so), a.dpre_in + off);
-                else tc::cp16(tc::smem_u32(sD2 + so), a.dpre_in + off);
-                if (HA) tc::cp16(tc::smem_u32(sH + so), a.h + off);
-            }
-            if (MODE == 2) {
-                for (int i = tid; i < 128 * G; i += 256) {
-                    const int z = i % 128, rl = i / 128;
-                    const float* src = a.x + ((int64_t)(R0 + rl) * a.nz + z0 + z) * a.ci;
-                    float v[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = j < a.ci ? src[j] : 0.f;
-                    st16(sH + tc::img_off(rl * C, z, 128), pack8(v));
-                    st16(sH + tc::img_off(rl * C + 8, z, 128), pack8(v + 8));
-                }
-            }
-            tc::cp_wait_all();
-            tc::fence_async_smem();
-            __syncthreads();
-            if (HB) {
-                if (tid == 0) {
-                    tc::fence_after();
-                    for (int rl = 0; rl < G; ++rl) {
-                        const uint32_t d = tmem + DB + rl * C;
-                        tc::mma(d, opnd(sDP, 128, 0, rl * C, false), opnd(sWN, C, 0, 0, false), C, C, false);
-                        tc::mma(d, opnd(sF, KZ2, z0, 0, false), opnd(sdZ + rl * (KZ2 * C * 2), C, 0, 0, true), C,
-                                KZ2, true);
-                    }
-                    tc::commit(mb0);
-                }
-                pend[0] = true;
-                if (!(ok = block_wait(mb0, phase[0]))) break;
-                phase[0] ^= 1;
-                pend[0] = false;
-                tc::fence_after();
-#pragma unroll 1
-                for (int jc = 0; jc < 2; ++jc) {
-                    const int col0 = 64 * hh + 32 * jc, rl = col0 / C, c0 = col0 % C;
-                    const int z = 32 * q + lane;
-                    float v[32];
-                    tc::ld32(tc::taddr(tmem, q, DB + col0), v);
-                    const int64_t pix = (int64_t)(R0 + rl) * a.nz + z0 + z;
-                    if (MODE == 1) {   // dpre_{l-1} = dh_l GELU'(pre_{l-1})
-                        const uint4* pp = reinterpret_cast<const uint4*>(a.pre + pix * C + c0);
-                        uint4* po = reinterpret_cast<uint4*>(a.dpre_out + pix * C + c0);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            float pv[8];
-                            unpack8(pp[k], pv);
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) v[8 * k + i] *= gelu_d(pv[i]);
-                            po[k] = pack8(v + 8 * k);
-                        }
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) st16(sD2 + tc::img_off(rl * C + c0 + 8 * k, z, 128), pack8(v + 8 * k));
-                }
-                tc::fence_async_smem();
-                tc::fence_before();
-                __syncthreads();
-            }
-            const bool accw = !first;
+        tc::cp_wait_all();
+        tc::fence_async_smem();
+        __syncthreads();
+        // the next item's inputs into the other buffer (read by the item before this one,
+        // whose MMAs have completed), overlapping this item's MMAs and epilogue
+        if (nbuf == 2 && w + 1 < nwork) load_tile(w + 1, bf ^ 1);
+        uint8_t* dp = sDP + bf * TILE;
+        uint8_t* d2 = HB ? sD2 : sD2 + bf * TILE;
+        uint8_t* hx = sH + bf * TILE;
+        if (HB) {
             if (tid == 0) {
                 tc::fence_after();
-                if (HA) tc::mma(tmem + DV, opnd(sD2, 128, 0, 0, true), opnd(sG, KZ2, 0, z0, true), KZ2, 128, t > 0);
-                tc::mma(tmem + DW, opnd(sH, 128, 0, 0, true), opnd(sD2, 128, 0, 0, true), 128, 128, accw);
-                tc::commit(mb1);
+                for (int rl = 0; rl < G; ++rl) {
+                    const uint32_t d = tmem + DB + rl * C;
+                    tc::mma(d, opnd(dp, 128, 0, rl * C, false), opnd(sWN, C, 0, 0, false), C, C, false);
+                    tc::mma(d, opnd(sF, KZ2, z0, 0, false), opnd(sdZ + rl * (KZ2 * C * 2), C, 0, 0, true), C,
+                            KZ2, true);
+                }
+                tc::commit(mb0);
             }
-            pend[1] = true;
-            if (!(ok = block_wait(mb1, phase[1]))) break;
-            phase[1] ^= 1;
-            pend[1] = false;
-            first = false;
+            pend[0] = true;
+            const int z = 32 * q + lane;
+            uint4 pre_r[2][4];   // pre_{l-1} of this thread's columns, loaded while the MMAs run
+            if (MODE == 1) {
+#pragma unroll
+                for (int jc = 0; jc < 2; ++jc) {
+                    const int col0 = 64 * hh + 32 * jc, rl = col0 / C, c0 = col0 % C;
+                    const uint4* pp =
+                        reinterpret_cast<const uint4*>(a.pre + ((int64_t)(R0 + rl) * a.nz + z0 + z) * C + c0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) pre_r[jc][k] = pp[k];
+                }
+            }
+            if (!(ok = block_wait(mb0, phase[0]))) break;
+            phase[0] ^= 1;
+            pend[0] = false;
             tc::fence_after();
+#pragma unroll
+            for (int jc = 0; jc < 2; ++jc) {
+                const int col0 = 64 * hh + 32 * jc, rl = col0 / C, c0 = col0 % C;
+                float v[32];
+                tc::ld32(tc::taddr(tmem, q, DB + col0), v);
+                const int64_t pix = (int64_t)(R0 + rl) * a.nz + z0 + z;
+                if (MODE == 1) {   // dpre_{l-1} = dh_l GELU'(pre_{l-1})
+                    uint4* po = reinterpret_cast<uint4*>(a.dpre_out + pix * C + c0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float pv[8];
+                        unpack8(pre_r[jc][k], pv);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v[8 * k + i] *= gelu_d(pv[i]);
+                        po[k] = pack8(v + 8 * k);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) st16(d2 + tc::img_off(rl * C + c0 + 8 * k, z, 128), pack8(v + 8 * k));
+            }
+            tc::fence_async_smem();
+            tc::fence_before();
+            __syncthreads();
         }
-        if (!ok) break;
-        if (HA) {   // dV of the group; db from its kz = 0 cosine coefficient
+        const bool accw = !first;
+        if (tid == 0) {
+            tc::fence_after();
+            if (HA) tc::mma(tmem + DV, opnd(d2, 128, 0, 0, true), opnd(sG, KZ2, 0, z0, true), KZ2, 128, t > 0);
+            tc::mma(tmem + DW, opnd(hx, 128, 0, 0, true), opnd(d2, 128, 0, 0, true), 128, 128, accw);
+            tc::commit(mb1);
+        }
+        pend[1] = true;
+        if (!(ok = block_wait(mb1, phase[1]))) break;
+        phase[1] ^= 1;
+        pend[1] = false;
+        first = false;
+        tc::fence_after();
+        if (nbuf == 1 && w + 1 < nwork) load_tile(w + 1, 0);
+        if (HA && t == ntz - 1) {   // dV of the group; db from its kz = 0 cosine coefficient
             const int m = 32 * q + lane, rl = m / C, c = m % C;
             if (hh * 16 < KZ2) {
                 float v[16];
@@ -755,9 +805,9 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
                 }
                 if (hh == 0) dbacc += v[0];
             }
+            tc::fence_before();
+            __syncthreads();
         }
-        tc::fence_before();
-        __syncthreads();
     }
     if (!ok) {
         recover(mbar, phase, pend, 2);
@@ -1040,8 +1090,10 @@ int fno_net_pack(const float* src, int64_t so, int64_t si, int O, int I, void* d
 // Dynamic shared memory is padded so that no more CTAs share an SM than its 512
 // tensor-memory columns serve: a CTA whose allocation cannot be met would wait in
 // tcgen05.alloc until another one on the SM finishes.  k_fwd: 256 columns, at most two CTAs
-// per SM; k_proj, k_bwd: 512 columns, one; k_k2r: up to 64 columns, at most seven.
+// per SM; k_proj: 256 columns at width 32 (two per SM), else 512 (one); k_bwd: 512
+// columns, one; k_k2r: up to 64 columns, at most seven.
 constexpr size_t SMEM_2_PER_SM = 80 * 1024, SMEM_1_PER_SM = 120 * 1024, SMEM_7_PER_SM = 32 * 1024;
+constexpr size_t SMEM_MAX = 227 * 1024;   // dynamic shared memory of one CTA
 
 int fno_net_pack_many(const fno_net_pack_job* jobs, int n, void* stream) {
     if (!jobs || n < 1 || n > FNO_NET_PACK_MAX) return fail(FNO_NET_ERR_INVALID, "fno_net_pack_many: 1 <= n <= %d", FNO_NET_PACK_MAX);
@@ -1103,10 +1155,11 @@ int fno_net_proj(const fno_net_dims* d, const void* hL, const void* q1w, const v
     ProjP p{(int)P, d->out_ch, (float)(2.0 / ((double)P * d->out_ch)), (const bf16*)hL, (const bf16*)q1w,
             (const bf16*)q1n, q1, (const bf16*)q2w, (const bf16*)q2n, q2, t, y, (bf16*)dhL, loss,
             dQ1, dq1, dQ2, dq2};
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(P / 128, sms()));
+    const int per_sm = d->width == 32 ? 2 : 1;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(P / 128, (int64_t)per_sm * sms()));
     cudaStream_t s = (cudaStream_t)stream;
     if (d->width == 32) {
-        const size_t sb = std::max(ProjSmem<32>::bytes, SMEM_1_PER_SM);
+        const size_t sb = std::max(ProjSmem<32>::bytes, SMEM_2_PER_SM);
         if (t) {
             if (int rc = set_smem(k_proj<32, true>, sb)) return rc;
             k_proj<32, true><<<grid, 256, sb, s>>>(p);
@@ -1130,7 +1183,8 @@ int fno_net_proj(const fno_net_dims* d, const void* hL, const void* q1w, const v
 
 #define BWD_CASE(C_, K_, MODE_)                                                                         \
     if (d->width == C_ && 2 * d->modes == K_ && mode == MODE_) {                                       \
-        const size_t sb = std::max(BwdSmem<C_, K_, MODE_>::bytes(d->nz), SMEM_1_PER_SM);               \
+        p.nbuf = BwdSmem<C_, K_, MODE_>::bytes(d->nz, 2) <= SMEM_MAX ? 2 : 1;                          \
+        const size_t sb = std::max(BwdSmem<C_, K_, MODE_>::bytes(d->nz, p.nbuf), SMEM_1_PER_SM);       \
         if (int rc = set_smem(k_bwd<C_, K_, MODE_>, sb)) return rc;                                    \
         k_bwd<C_, K_, MODE_><<<grid, 256, sb, s>>>(p);                                                  \
         launched = true;                                                                              \
@@ -1144,7 +1198,7 @@ int fno_net_bwd(int mode, const fno_net_dims* d, const void* dpre_in, const void
     if (mode < 0 || mode > 2 || !dpre_in || !dW || !db || (mode != 0 && (!dZ || !wn_img || !fz_img)) ||
         (mode == 1 && (!pre || !dpre_out)) || (mode != 2 && (!h || !gzt_img || !dV)) || (mode == 2 && !x))
         return fail(FNO_NET_ERR_INVALID, "fno_net_bwd: missing argument for mode %d", mode);
-    BwdP p{d->batch * d->nr, d->nr, d->nz, d->in_ch, (float)((double)d->nr * d->nz), (const bf16*)dpre_in,
+    BwdP p{d->batch * d->nr, d->nr, d->nz, d->in_ch, 2, (float)((double)d->nr * d->nz), (const bf16*)dpre_in,
            (const bf16*)dZ, (const bf16*)wn_img, (const bf16*)fz_img, (const bf16*)pre, (const bf16*)h, x,
            (const bf16*)gzt_img, (bf16*)dpre_out, (bf16*)dV, dW, db};
     const unsigned grid = (unsigned)std::max(1, std::min(p.nrows / (128 / d->width), sms()));
