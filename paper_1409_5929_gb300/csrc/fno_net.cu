@@ -83,10 +83,33 @@ __device__ __forceinline__ void unpack8(uint4 u, float* v) {
 
 __device__ __forceinline__ void st16(uint8_t* p, uint4 u) { *reinterpret_cast<uint4*>(p) = u; }
 
+// The standard normal's distribution function Phi(x) and density phi(x) from one
+// exponential: erf(z) for z = |x| / sqrt 2 by Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26 (|error| <= 1.5e-7):
+//     erf(z) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-z^2),  t = 1 / (1 + p z),
+// whose exp(-z^2) = exp(-x^2 / 2) is also phi's.  The error is far below the BF16 rounding
+// every activation of the network carries.
+__device__ __forceinline__ void normal_cdf_pdf(float x, float& cdf, float& pdf) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float e = __expf(-z * z);
+    const float t = __fdividef(1.f, fmaf(0.3275911f, z, 1.f));
+    const float poly =
+        t * (0.254829592f + t * (-0.284496736f + t * (1.421413741f + t * (-1.453152027f + t * 1.061405429f))));
+    const float erfz = 1.f - poly * e;
+    cdf = 0.5f + 0.5f * copysignf(erfz, x);
+    pdf = 0.39894228040143268f * e;
+}
+
 // GELU in its exact form x Phi(x) and its derivative Phi(x) + x phi(x)
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu(float x) {
+    float c, d;
+    normal_cdf_pdf(x, c, d);
+    return x * c;
+}
 __device__ __forceinline__ float gelu_d(float x) {
-    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+    float c, d;
+    normal_cdf_pdf(x, c, d);
+    return fmaf(x, d, c);
 }
 
 // A bounded wait that the whole block agrees on (every thread calls it).
@@ -463,8 +486,10 @@ __global__ void __launch_bounds__(256, C == 32 ? 2 : 1) k_proj(const ProjP a) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const float x = v[8 * k + i] + sq1[col0 + 8 * k + i];
-                    gq[i] = gelu(x);
-                    gd[i] = gelu_d(x);
+                    float c, d;
+                    normal_cdf_pdf(x, c, d);
+                    gq[i] = x * c;
+                    gd[i] = fmaf(x, d, c);
                 }
                 st16(sQI + tc::img_off(col0 + 8 * k, p, H), pack8(gq));
                 if (TRAIN) st16(sDQ + tc::img_off(col0 + 8 * k, p, H), pack8(gd));
@@ -589,7 +614,6 @@ __global__ void __launch_bounds__(256, C == 32 ? 2 : 1) k_proj(const ProjP a) {
 // -------------------------------------------------------------- backward --
 struct BwdP {
     int nrows, nr, nz, ci;
-    int nbuf;         // 2: the next tile's inputs load while the current one computes
     float db_scale;   // nr nz: the kz = 0 coefficient of Gz is 1 / (nr nz)
     const bf16* dpre_in;
     const bf16* dZ;
@@ -610,40 +634,41 @@ struct BwdSmem {
     static constexpr int G = 128 / C;
     static constexpr bool HB = MODE != 0, HA = MODE != 2;
     static constexpr size_t TILE = 128 * 128 * 2;
-    // input tiles (dpre_in, or in mode 0 the gradient itself, and h or x) times nbuf
-    static size_t bytes(int nz, int nbuf) {
-        return (HB ? TILE * nbuf + C * C * 2 + (size_t)nz * KZ2 * 2 + (size_t)G * KZ2 * C * 2 : 0) +
-               TILE * (HB ? 1 : nbuf) + TILE * nbuf + (HA ? (size_t)nz * KZ2 * 2 : 0) + (size_t)C * C * 4 + C * 4 +
-               1024;
+    // the gradient tile (dpre_in, overwritten by the next dpre), W, Fz, dZ rows, the h (x)
+    // tile, Gz^T, the CTA's sums
+    static size_t bytes(int nz) {
+        return TILE + (HB ? C * C * 2 + (size_t)nz * KZ2 * 2 + (size_t)G * KZ2 * C * 2 : 0) + TILE +
+               (HA ? (size_t)nz * KZ2 * 2 : 0) + (size_t)C * C * 4 + C * 4 + 1024;
     }
 };
 
+// Two CTAs per SM (256 tensor-memory columns each): columns 0..127 hold the layer's input
+// gradient dh (B part) and then, per tile, the weight-gradient product whose diagonal
+// blocks each thread adds to 32 registers; columns 128.. the dV accumulator of the group.
 template <int C, int KZ2, int MODE>
-__global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
+__global__ void __launch_bounds__(256, 2) k_bwd(const BwdP a) {
     using S = BwdSmem<C, KZ2, MODE>;
     constexpr int G = S::G;
     constexpr bool HB = S::HB, HA = S::HA;
     constexpr int M = KZ2 / 2;
+    constexpr int TILE = (int)S::TILE;
     extern __shared__ uint8_t dsm[];
     uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
-    constexpr int TILE = (int)S::TILE;
-    const int nbuf = a.nbuf;
-    uint8_t* sDP = sm;                                        // dpre_l tiles (B part), nbuf of them
-    uint8_t* sWN = sDP + (HB ? TILE * nbuf : 0);
+    uint8_t* sD2 = sm;                                        // dpre_l (B part), then the gradient the A part uses
+    uint8_t* sWN = sD2 + TILE;
     uint8_t* sF = sWN + (HB ? C * C * 2 : 0);
     uint8_t* sdZ = sF + (HB ? a.nz * KZ2 * 2 : 0);
-    uint8_t* sD2 = sdZ + (HB ? G * KZ2 * C * 2 : 0);          // the gradient the A part uses (nbuf in mode 0)
-    uint8_t* sH = sD2 + TILE * (HB ? 1 : nbuf);               // h_{l-1} tiles, or x with ones, nbuf of them
-    uint8_t* sG = sH + TILE * nbuf;
+    uint8_t* sH = sdZ + (HB ? G * KZ2 * C * 2 : 0);           // h_{l-1} tile, or x with ones
+    uint8_t* sG = sH + TILE;
     float* sacc = reinterpret_cast<float*>(sG + (HA ? a.nz * KZ2 * 2 : 0));   // C x C
     float* sdb = sacc + C * C;
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hh = warp >> 2;
-    constexpr int DB = 0, DV = 128, DW = 256;
+    constexpr int DB = 0, DW = 0, DV = 128;
 
-    if (warp == 0) tc::tmem_alloc(&tslot, 512);
+    if (warp == 0) tc::tmem_alloc(&tslot, 256);
     if (tid == 0) {
         tc::mbar_init(tc::smem_u32(&mbar[0]), 1);
         tc::mbar_init(tc::smem_u32(&mbar[1]), 1);
@@ -656,17 +681,17 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
     if (HA) cp_flat(sG, a.gzt, a.nz * KZ2 * 2, tid, 256);
     for (int i = tid; i < C * C; i += 256) sacc[i] = 0.f;
     for (int i = tid; i < C; i += 256) sdb[i] = 0.f;
-    if (MODE == 2) {   // per row block of each x image: x (16) | ones (8) | zeros
-        for (int i = tid; i < 128 * G * nbuf; i += 256) {
-            const int z = i % 128, rl = (i / 128) % G, bf = i / (128 * G);
+    if (MODE == 2) {   // per row block of the x image: x (16) | ones (8) | zeros
+        for (int i = tid; i < 128 * G; i += 256) {
+            const int z = i % 128, rl = i / 128;
             float one[8], zero[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 one[k] = 1.f;
                 zero[k] = 0.f;
             }
-            st16(sH + bf * TILE + tc::img_off(rl * C + 16, z, 128), pack8(one));
-            for (int c = 24; c < C; c += 8) st16(sH + bf * TILE + tc::img_off(rl * C + c, z, 128), pack8(zero));
+            st16(sH + tc::img_off(rl * C + 16, z, 128), pack8(one));
+            for (int c = 24; c < C; c += 8) st16(sH + tc::img_off(rl * C + c, z, 128), pack8(zero));
         }
     }
     tc::fence_before();
@@ -676,41 +701,18 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
     const uint32_t mb0 = tc::smem_u32(&mbar[0]), mb1 = tc::smem_u32(&mbar[1]);
     uint32_t phase[2] = {0, 0};
     bool pend[2] = {false, false};
-    bool ok = true, first = true;
-    float dbacc = 0.f;
-    const int ngroups = a.nrows / G, ntz = a.nz / 128;
-
-    // this CTA's work: its row groups g = blockIdx.x + j gridDim.x, each in ntz z tiles
-    const int my_groups = (int)blockIdx.x < ngroups ? (ngroups - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int nwork = my_groups * ntz;
-    auto load_tile = [&](int w, int bf) {   // input tiles of work item w into buffer bf
-        const int R0 = (blockIdx.x + (w / ntz) * gridDim.x) * G, z0 = (w % ntz) * 128;
-        for (int i = tid; i < 128 * G * (C / 8); i += 256) {
-            const int c8 = i % (C / 8), t2 = i / (C / 8), z = t2 % 128, rl = t2 / 128;
-            const int64_t off = ((int64_t)(R0 + rl) * a.nz + z0 + z) * C + c8 * 8;
-            const uint32_t so = bf * TILE + tc::img_off(rl * C + c8 * 8, z, 128);
-            if (HB) tc::cp16(tc::smem_u32(sDP + so), a.dpre_in + off);
-            else tc::cp16(tc::smem_u32(sD2 + so), a.dpre_in + off);
-            if (HA) tc::cp16(tc::smem_u32(sH + so), a.h + off);
-        }
-        if (MODE == 2) {
-            for (int i = tid; i < 128 * G; i += 256) {
-                const int z = i % 128, rl = i / 128;
-                const float* src = a.x + ((int64_t)(R0 + rl) * a.nz + z0 + z) * a.ci;
-                float v[16];
+    bool ok = true, any = false;
+    float dbacc = 0.f, wacc[32];   // this thread's diagonal row: (rl, c_in) x 32 columns c
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = j < a.ci ? src[j] : 0.f;
-                st16(sH + bf * TILE + tc::img_off(rl * C, z, 128), pack8(v));
-                st16(sH + bf * TILE + tc::img_off(rl * C + 8, z, 128), pack8(v + 8));
-            }
-        }
-    };
-    if (nwork > 0) load_tile(0, 0);
-    for (int w = 0; w < nwork && ok; ++w) {
-        const int bf = nbuf == 2 ? (w & 1) : 0;
-        const int g = blockIdx.x + (w / ntz) * gridDim.x, t = w % ntz;
-        const int R0 = g * G, b = R0 / a.nr, r0 = R0 % a.nr, z0 = t * 128;
-        if (HB && t == 0) {   // the group's dZ rows (the previous tile's MMAs have completed)
+    for (int i = 0; i < 32; ++i) wacc[i] = 0.f;
+    const int ngroups = a.nrows / G, ntz = a.nz / 128;
+    const int m = 32 * q + lane, mrl = m / C, mci = m % C;
+    const int wc0 = 32 * hh;                // this warp's 32 diagonal columns (C = 32: warps 0..3 only)
+    const bool wdiag = wc0 < C;
+
+    for (int g = blockIdx.x; g < ngroups && ok; g += gridDim.x) {
+        const int R0 = g * G, b = R0 / a.nr, r0 = R0 % a.nr;
+        if (HB) {
             for (int i = tid; i < G * KZ2 * (C / 8); i += 256) {
                 const int c8 = i % (C / 8), t2 = i / (C / 8), kz2 = t2 % KZ2, rl = t2 / KZ2;
                 const int part = kz2 / M, kz = kz2 % M;
@@ -718,130 +720,138 @@ __global__ void __launch_bounds__(256, 1) k_bwd(const BwdP a) {
                 tc::cp16(tc::smem_u32(sdZ + rl * (KZ2 * C * 2) + tc::img_off(c8 * 8, kz2, C)), src);
             }
         }
-        tc::cp_wait_all();
-        tc::fence_async_smem();
-        __syncthreads();
-        // the next item's inputs into the other buffer (read by the item before this one,
-        // whose MMAs have completed), overlapping this item's MMAs and epilogue
-        if (nbuf == 2 && w + 1 < nwork) load_tile(w + 1, bf ^ 1);
-        uint8_t* dp = sDP + bf * TILE;
-        uint8_t* d2 = HB ? sD2 : sD2 + bf * TILE;
-        uint8_t* hx = sH + bf * TILE;
-        if (HB) {
+        for (int t = 0; t < ntz && ok; ++t) {
+            const int z0 = t * 128;
+            for (int i = tid; i < 128 * G * (C / 8); i += 256) {
+                const int c8 = i % (C / 8), t2 = i / (C / 8), z = t2 % 128, rl = t2 / 128;
+                const int64_t off = ((int64_t)(R0 + rl) * a.nz + z0 + z) * C + c8 * 8;
+                const uint32_t so = tc::img_off(rl * C + c8 * 8, z, 128);
+                tc::cp16(tc::smem_u32(sD2 + so), a.dpre_in + off);
+                if (HA) tc::cp16(tc::smem_u32(sH + so), a.h + off);
+            }
+            if (MODE == 2) {
+                for (int i = tid; i < 128 * G; i += 256) {
+                    const int z = i % 128, rl = i / 128;
+                    const float* src = a.x + ((int64_t)(R0 + rl) * a.nz + z0 + z) * a.ci;
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = j < a.ci ? src[j] : 0.f;
+                    st16(sH + tc::img_off(rl * C, z, 128), pack8(v));
+                    st16(sH + tc::img_off(rl * C + 8, z, 128), pack8(v + 8));
+                }
+            }
+            tc::cp_wait_all();
+            tc::fence_async_smem();
+            __syncthreads();
+            if (HB) {
+                if (tid == 0) {
+                    tc::fence_after();
+                    for (int rl = 0; rl < G; ++rl) {
+                        const uint32_t d = tmem + DB + rl * C;
+                        tc::mma(d, opnd(sD2, 128, 0, rl * C, false), opnd(sWN, C, 0, 0, false), C, C, false);
+                        tc::mma(d, opnd(sF, KZ2, z0, 0, false), opnd(sdZ + rl * (KZ2 * C * 2), C, 0, 0, true), C,
+                                KZ2, true);
+                    }
+                    tc::commit(mb0);
+                }
+                pend[0] = true;
+                if (!(ok = block_wait(mb0, phase[0]))) break;
+                phase[0] ^= 1;
+                pend[0] = false;
+                tc::fence_after();
+                // dh -> (MODE 1) dpre_{l-1} = dh GELU'(pre_{l-1}); written over dpre_l in sD2,
+                // which the MMAs above have finished reading
+                const int z = 32 * q + lane;
+#pragma unroll 1
+                for (int jc = 0; jc < 4; ++jc) {   // 16 columns at a time (the 32 wacc registers stay live)
+                    const int col0 = 64 * hh + 16 * jc, rl = col0 / C, c0 = col0 % C;
+                    const int64_t pix = (int64_t)(R0 + rl) * a.nz + z0 + z;
+                    uint4 pr[2];
+                    if (MODE == 1) {
+                        const uint4* pp = reinterpret_cast<const uint4*>(a.pre + pix * C + c0);
+                        pr[0] = pp[0];
+                        pr[1] = pp[1];
+                    }
+                    float v[16];
+                    tc::ld16(tc::taddr(tmem, q, DB + col0), v);
+                    if (MODE == 1) {
+                        uint4* po = reinterpret_cast<uint4*>(a.dpre_out + pix * C + c0);
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            float pv[8];
+                            unpack8(pr[k], pv);
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) v[8 * k + i] *= gelu_d(pv[i]);
+                            po[k] = pack8(v + 8 * k);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) st16(sD2 + tc::img_off(rl * C + c0 + 8 * k, z, 128), pack8(v + 8 * k));
+                }
+                tc::fence_async_smem();
+                tc::fence_before();
+                __syncthreads();
+            }
             if (tid == 0) {
                 tc::fence_after();
-                for (int rl = 0; rl < G; ++rl) {
-                    const uint32_t d = tmem + DB + rl * C;
-                    tc::mma(d, opnd(dp, 128, 0, rl * C, false), opnd(sWN, C, 0, 0, false), C, C, false);
-                    tc::mma(d, opnd(sF, KZ2, z0, 0, false), opnd(sdZ + rl * (KZ2 * C * 2), C, 0, 0, true), C,
-                            KZ2, true);
-                }
-                tc::commit(mb0);
+                if (HA) tc::mma(tmem + DV, opnd(sD2, 128, 0, 0, true), opnd(sG, KZ2, 0, z0, true), KZ2, 128, t > 0);
+                tc::mma(tmem + DW, opnd(sH, 128, 0, 0, true), opnd(sD2, 128, 0, 0, true), 128, 128, false);
+                tc::commit(mb1);
             }
-            pend[0] = true;
-            const int z = 32 * q + lane;
-            uint4 pre_r[2][4];   // pre_{l-1} of this thread's columns, loaded while the MMAs run
-            if (MODE == 1) {
-#pragma unroll
-                for (int jc = 0; jc < 2; ++jc) {
-                    const int col0 = 64 * hh + 32 * jc, rl = col0 / C, c0 = col0 % C;
-                    const uint4* pp =
-                        reinterpret_cast<const uint4*>(a.pre + ((int64_t)(R0 + rl) * a.nz + z0 + z) * C + c0);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) pre_r[jc][k] = pp[k];
-                }
-            }
-            if (!(ok = block_wait(mb0, phase[0]))) break;
-            phase[0] ^= 1;
-            pend[0] = false;
+            pend[1] = true;
+            if (!(ok = block_wait(mb1, phase[1]))) break;
+            phase[1] ^= 1;
+            pend[1] = false;
             tc::fence_after();
-#pragma unroll
-            for (int jc = 0; jc < 2; ++jc) {
-                const int col0 = 64 * hh + 32 * jc, rl = col0 / C, c0 = col0 % C;
+            if (wdiag) {   // the diagonal block of this tile's (rows, c_in) x (rows, c) product
                 float v[32];
-                tc::ld32(tc::taddr(tmem, q, DB + col0), v);
-                const int64_t pix = (int64_t)(R0 + rl) * a.nz + z0 + z;
-                if (MODE == 1) {   // dpre_{l-1} = dh_l GELU'(pre_{l-1})
-                    uint4* po = reinterpret_cast<uint4*>(a.dpre_out + pix * C + c0);
+                tc::ld32(tc::taddr(tmem, q, DW + mrl * C + wc0), v);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        float pv[8];
-                        unpack8(pre_r[jc][k], pv);
+                for (int i = 0; i < 32; ++i) wacc[i] += v[i];
+            }
+            any = true;
+            if (HA && t == ntz - 1) {   // dV of the group; db from its kz = 0 cosine coefficient
+                const int rl = mrl, c = mci;
+                if (hh * 16 < KZ2) {
+                    float v[16];
+                    tc::ld16(tc::taddr(tmem, q, DV + 16 * hh), v);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) v[8 * k + i] *= gelu_d(pv[i]);
-                        po[k] = pack8(v + 8 * k);
+                    for (int i = 0; i < 16; ++i) {
+                        const int kz2 = 16 * hh + i, part = kz2 / M, kz = kz2 % M;
+                        a.dV[((((int64_t)b * M + kz) * 2 + part) * a.nr + r0 + rl) * C + c] =
+                            __float2bfloat16_rn(v[i]);
                     }
+                    if (hh == 0) dbacc += v[0];
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) st16(d2 + tc::img_off(rl * C + c0 + 8 * k, z, 128), pack8(v + 8 * k));
-            }
-            tc::fence_async_smem();
-            tc::fence_before();
-            __syncthreads();
-        }
-        const bool accw = !first;
-        if (tid == 0) {
-            tc::fence_after();
-            if (HA) tc::mma(tmem + DV, opnd(d2, 128, 0, 0, true), opnd(sG, KZ2, 0, z0, true), KZ2, 128, t > 0);
-            tc::mma(tmem + DW, opnd(hx, 128, 0, 0, true), opnd(d2, 128, 0, 0, true), 128, 128, accw);
-            tc::commit(mb1);
-        }
-        pend[1] = true;
-        if (!(ok = block_wait(mb1, phase[1]))) break;
-        phase[1] ^= 1;
-        pend[1] = false;
-        first = false;
-        tc::fence_after();
-        if (nbuf == 1 && w + 1 < nwork) load_tile(w + 1, 0);
-        if (HA && t == ntz - 1) {   // dV of the group; db from its kz = 0 cosine coefficient
-            const int m = 32 * q + lane, rl = m / C, c = m % C;
-            if (hh * 16 < KZ2) {
-                float v[16];
-                tc::ld16(tc::taddr(tmem, q, DV + 16 * hh), v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int kz2 = 16 * hh + i, part = kz2 / M, kz = kz2 % M;
-                    a.dV[((((int64_t)b * M + kz) * 2 + part) * a.nr + r0 + rl) * C + c] = __float2bfloat16_rn(v[i]);
-                }
-                if (hh == 0) dbacc += v[0];
             }
             tc::fence_before();
-            __syncthreads();
+            __syncthreads();   // tensor memory read before the next tile's MMAs overwrite it
         }
     }
     if (!ok) {
         recover(mbar, phase, pend, 2);
-    } else {
-        // diagonal blocks of the (rows, c_in) x (rows, c) accumulator: this CTA's partial
-        // weight gradient (or, for the lift, rows x (16), ones (16) of the x image)
-        const int m = 32 * q + lane, rl = m / C, ci = m % C;
-        for (int c0 = 32 * hh; c0 < C; c0 += 64) {
-            float v[32];
-            if (first) {
+    } else if (any) {
+        // this CTA's sums, added to the gradients (FP32 atomics): dL/dW[c_in][c] from every
+        // diagonal row, or for the lift dL/dP[ci][c] (rows ci < in_ch of each x block) and
+        // dL/dp (its first ones row)
+        if (wdiag) {
+            if (MODE == 2 && mci == 16) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = 0.f;
-            } else {
-                tc::ld32(tc::taddr(tmem, q, DW + rl * C + c0), v);
-            }
-            if (MODE == 2 && ci == 16) {          // a ones row: dL/dp
+                for (int i = 0; i < 32; ++i) atomicAdd(&sdb[wc0 + i], wacc[i]);
+            } else if (MODE != 2 || mci < a.ci) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) atomicAdd(&sdb[c0 + i], v[i]);
-            } else if (MODE != 2 || ci < a.ci) {  // dL/dW[c_in][c], or dL/dP[ci][c]
-#pragma unroll
-                for (int i = 0; i < 32; ++i) atomicAdd(&sacc[ci * C + c0 + i], v[i]);
+                for (int i = 0; i < 32; ++i) atomicAdd(&sacc[mci * C + wc0 + i], wacc[i]);
             }
         }
-        if (HA && hh == 0) atomicAdd(&sdb[m % C], dbacc * a.db_scale);
+        if (HA && hh == 0) atomicAdd(&sdb[mci], dbacc * a.db_scale);
         __syncthreads();
-        if (!first) {   // this CTA's sums, added to the gradients (FP32 atomics)
-            const int rows = MODE == 2 ? a.ci : C;
-            for (int i = tid; i < rows * C; i += 256) atomicAdd(&a.gW[i], sacc[i]);
-            for (int i = tid; i < C; i += 256) atomicAdd(&a.gb[i], sdb[i]);
-        }
+        const int rows = MODE == 2 ? a.ci : C;
+        for (int i = tid; i < rows * C; i += 256) atomicAdd(&a.gW[i], sacc[i]);
+        for (int i = tid; i < C; i += 256) atomicAdd(&a.gb[i], sdb[i]);
     }
     tc::fence_before();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(tmem, 512);
+    if (warp == 0) tc::tmem_free(tmem, 256);
 }
 
 // ------------------------------------------------------- r transforms --
@@ -1090,10 +1100,9 @@ int fno_net_pack(const float* src, int64_t so, int64_t si, int O, int I, void* d
 // Dynamic shared memory is padded so that no more CTAs share an SM than its 512
 // tensor-memory columns serve: a CTA whose allocation cannot be met would wait in
 // tcgen05.alloc until another one on the SM finishes.  k_fwd: 256 columns, at most two CTAs
-// per SM; k_proj: 256 columns at width 32 (two per SM), else 512 (one); k_bwd: 512
-// columns, one; k_k2r: up to 64 columns, at most seven.
+// per SM; k_proj: 256 columns at width 32 (two per SM), else 512 (one); k_bwd: 256
+// columns, two; k_k2r: up to 64 columns, at most seven.
 constexpr size_t SMEM_2_PER_SM = 80 * 1024, SMEM_1_PER_SM = 120 * 1024, SMEM_7_PER_SM = 32 * 1024;
-constexpr size_t SMEM_MAX = 227 * 1024;   // dynamic shared memory of one CTA
 
 int fno_net_pack_many(const fno_net_pack_job* jobs, int n, void* stream) {
     if (!jobs || n < 1 || n > FNO_NET_PACK_MAX) return fail(FNO_NET_ERR_INVALID, "fno_net_pack_many: 1 <= n <= %d", FNO_NET_PACK_MAX);
@@ -1183,8 +1192,7 @@ int fno_net_proj(const fno_net_dims* d, const void* hL, const void* q1w, const v
 
 #define BWD_CASE(C_, K_, MODE_)                                                                         \
     if (d->width == C_ && 2 * d->modes == K_ && mode == MODE_) {                                       \
-        p.nbuf = BwdSmem<C_, K_, MODE_>::bytes(d->nz, 2) <= SMEM_MAX ? 2 : 1;                          \
-        const size_t sb = std::max(BwdSmem<C_, K_, MODE_>::bytes(d->nz, p.nbuf), SMEM_1_PER_SM);       \
+        const size_t sb = std::max(BwdSmem<C_, K_, MODE_>::bytes(d->nz), SMEM_2_PER_SM);               \
         if (int rc = set_smem(k_bwd<C_, K_, MODE_>, sb)) return rc;                                    \
         k_bwd<C_, K_, MODE_><<<grid, 256, sb, s>>>(p);                                                  \
         launched = true;                                                                              \
@@ -1198,10 +1206,10 @@ int fno_net_bwd(int mode, const fno_net_dims* d, const void* dpre_in, const void
     if (mode < 0 || mode > 2 || !dpre_in || !dW || !db || (mode != 0 && (!dZ || !wn_img || !fz_img)) ||
         (mode == 1 && (!pre || !dpre_out)) || (mode != 2 && (!h || !gzt_img || !dV)) || (mode == 2 && !x))
         return fail(FNO_NET_ERR_INVALID, "fno_net_bwd: missing argument for mode %d", mode);
-    BwdP p{d->batch * d->nr, d->nr, d->nz, d->in_ch, 2, (float)((double)d->nr * d->nz), (const bf16*)dpre_in,
+    BwdP p{d->batch * d->nr, d->nr, d->nz, d->in_ch, (float)((double)d->nr * d->nz), (const bf16*)dpre_in,
            (const bf16*)dZ, (const bf16*)wn_img, (const bf16*)fz_img, (const bf16*)pre, (const bf16*)h, x,
            (const bf16*)gzt_img, (bf16*)dpre_out, (bf16*)dV, dW, db};
-    const unsigned grid = (unsigned)std::max(1, std::min(p.nrows / (128 / d->width), sms()));
+    const unsigned grid = (unsigned)std::max(1, std::min(p.nrows / (128 / d->width), 2 * sms()));
     cudaStream_t s = (cudaStream_t)stream;
     bool launched = false;
     BWD_CASE(32, 32, 0) BWD_CASE(32, 32, 1) BWD_CASE(32, 32, 2)
