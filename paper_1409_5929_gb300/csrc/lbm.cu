@@ -436,7 +436,7 @@ __device__ __forceinline__ void update_pair(const Consts<float>& c, const Buf<ST
     // a lane past the last column, or on the end column of a closed geometry (a boundary
     // node), computes on clamped indices and is not stored
     const bool in1 = kz0 + 1 < nz;
-    const bool st0 = pz || kz0 > 0;
+    const bool st0 = pz || (kz0 > 0 && kz0 < nz - 1);   // (kz0 = nz - 1 when nz is odd)
     const bool st1 = in1 && (pz || kz0 + 1 < nz - 1);
     if (!st0 && !st1) return;
     const int zc1 = in1 ? kz0 + 1 : kz0;
@@ -1135,6 +1135,10 @@ struct lbm_handle {
     int device = 0;
     int sms = 0;             // multiprocessors of the device
     cudaStream_t stream = nullptr;
+    // the wall kernel of a two-buffer step runs beside the bulk kernel on its own stream
+    // (forked from and joined back into `stream` every step)
+    cudaStream_t wstream = nullptr;
+    cudaEvent_t wfork = nullptr, wjoin = nullptr;
     int64_t plane = 0;       // elements per plane (padded)
     int64_t N = 0;           // nr * nz
     void* buf[2] = {nullptr, nullptr};
@@ -1405,6 +1409,12 @@ int lbm_destroy(lbm_handle* h) {
     cudaFree(h->phi);
     cudaFree(h->fstage);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->wstream) {
+        cudaStreamSynchronize(h->wstream);
+        cudaStreamDestroy(h->wstream);
+    }
+    if (h->wfork) cudaEventDestroy(h->wfork);
+    if (h->wjoin) cudaEventDestroy(h->wjoin);
     for (int i = 0; i < 2; ++i) {
         cudaFree(h->astage[i]);
         if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
@@ -1478,6 +1488,13 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     ALLOC(h->result, 8 * sizeof(double));
     ALLOC(h->bad, sizeof(unsigned int));
 #undef ALLOC
+    e = cudaStreamCreateWithFlags(&h->wstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->wfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->wjoin, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lbm_destroy(h);
+        return fail(LBM_ERR_CUDA, "wall stream: %s", cudaGetErrorString(e));
+    }
     // uniform porosity eps_mean, then the cold start
     const int thr = 256;
     const unsigned blocks = (unsigned)((h->N + thr - 1) / thr);
@@ -1687,6 +1704,17 @@ static int launch_step(lbm_handle* h) {
     const int64_t zblocks = (h->p.nz + cols - 1) / cols;
     const int rpt = (i32 && zblocks * ((h->p.nr + BULK_RPT - 1) / BULK_RPT) >= (int64_t)BULK_RPT_MIN_BLOCKS * h->sms) ? BULK_RPT : 1;
     const dim3 gb((unsigned)zblocks, (unsigned)((h->p.nr + rpt - 1) / rpt));
+    // the wall kernel reads only the pre-step state A and writes only boundary nodes of B,
+    // which the bulk kernel does not touch: it runs beside it on the wall stream
+    CK(cudaEventRecord(h->wfork, h->stream));
+    CK(cudaStreamWaitEvent(h->wstream, h->wfork, 0));
+    if (h->timing) CK(cudaEventRecord(e1b, h->wstream));
+    DISPATCH_STO(h->p.storage,
+                 k_wall<S_><<<(nw + 127) / 128, 128, 0, h->wstream>>>(h->cf, bufp<S_>(h, h->cur),
+                                                                      bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi,
+                                                                      h->plane, nw));
+    CK(cudaGetLastError());
+    if (h->timing) CK(cudaEventRecord(e2, h->wstream));
     if (pair) {
         const bool vec = (h->p.nz & 1) == 0;
         DISPATCH_STO16(h->p.storage, {
@@ -1712,17 +1740,11 @@ static int launch_step(lbm_handle* h) {
                          h->cf, bufp<S_>(h, h->cur), bufp<S_>(h, h->cur ^ 1), (const PP<S_>*)h->phi, h->plane));
     }
     CK(cudaGetLastError());
+    if (h->timing) CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventRecord(h->wjoin, h->wstream));
+    CK(cudaStreamWaitEvent(h->stream, h->wjoin, 0));
     if (h->timing) {
-        CK(cudaEventRecord(e1, h->stream));
-        CK(cudaEventRecord(e1b, h->stream));
-    }
-    DISPATCH_STO(h->p.storage,
-                 k_wall<S_><<<(nw + 127) / 128, 128, 0, h->stream>>>(h->cf, bufp<S_>(h, h->cur), bufp<S_>(h, h->cur ^ 1),
-                                                                     (const PP<S_>*)h->phi, h->plane, nw));
-    CK(cudaGetLastError());
-    if (h->timing) {
-        CK(cudaEventRecord(e2, h->stream));
-        // (bulk start, bulk end, wall start, wall end): the wall kernel starts where the bulk ends
+        // (bulk start, bulk end, wall start, wall end), the wall pair on the wall stream
         h->ev.push_back(e0);
         h->ev.push_back(e1);
         h->ev.push_back(e1b);
@@ -2412,6 +2434,9 @@ struct lbm_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the wall kernel runs beside the bulk kernels on its own stream (fork / join per step)
+    cudaStream_t wstream = nullptr;
+    cudaEvent_t wfork = nullptr, wjoin = nullptr;
     std::vector<lbm_params> p;
     std::vector<lbm_info> info;
     std::vector<Consts<double>> cd;
@@ -2512,6 +2537,13 @@ static int batch_launch_step(lbm_batch* b) {
     // 16-bit storage: the refresh of lbm_step, every LBM_FREF_EVERY steps since the last
     if (b->storage != LBM_F32 && b->since_rebase >= LBM_FREF_EVERY)
         if (int rc = batch_launch_rebase_flow(b)) return rc;
+    // the wall kernel reads only the pre-step states and writes only boundary nodes, which
+    // the bulk kernels do not touch: it runs beside them on the wall stream
+    CK(cudaEventRecord(b->wfork, b->stream));
+    CK(cudaStreamWaitEvent(b->wstream, b->wfork, 0));
+    DISPATCH_STO(b->storage, k_batch_wall<S_><<<(b->nwall + 127) / 128, 128, 0, b->wstream>>>(
+                                 b->d_desc, b->pool, b->parity, b->d_active, b->d_prefix, b->nactive));
+    CK(cudaGetLastError());
     const dim3 blk(b->bz, b->rows);
     if (b->storage == LBM_F32) {
         DISPATCH_RPT(b->rpt, k_batch_bulk<LBM_F32, R_, false><<<b->ntiles, blk, 0, b->stream>>>(
@@ -2526,9 +2558,8 @@ static int batch_launch_step(lbm_batch* b) {
                                                                 b->d_desc, b->pool, b->parity, b->d_tiles + ne)));
     }
     CK(cudaGetLastError());
-    DISPATCH_STO(b->storage, k_batch_wall<S_><<<(b->nwall + 127) / 128, 128, 0, b->stream>>>(
-                                 b->d_desc, b->pool, b->parity, b->d_active, b->d_prefix, b->nactive));
-    CK(cudaGetLastError());
+    CK(cudaEventRecord(b->wjoin, b->wstream));
+    CK(cudaStreamWaitEvent(b->stream, b->wjoin, 0));
     b->parity ^= 1;
     b->since_rebase += 1;
     return LBM_OK;
@@ -2540,6 +2571,12 @@ int lbm_batch_destroy(lbm_batch* b) {
     if (!b) return LBM_OK;
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->wstream) {
+        cudaStreamSynchronize(b->wstream);
+        cudaStreamDestroy(b->wstream);
+    }
+    if (b->wfork) cudaEventDestroy(b->wfork);
+    if (b->wjoin) cudaEventDestroy(b->wjoin);
     batch_free_graph(b);
     cudaFree(b->d_desc);
     cudaFree(b->pool);
@@ -2596,6 +2633,9 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
     b->iparity.assign(n, 0);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->wstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->wfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->wjoin, cudaEventDisableTiming);
     b->own_stream = e == cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->pool, state_off);
     if (e == cudaSuccess)
