@@ -288,6 +288,23 @@ def test_deterministic(lbm):
     assert all(np.array_equal(a, b) for a, b in zip(out[0], out[1]))
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("nz", [3, 129, 301])
+def test_boundary_nodes_written_once_odd_nz(lbm, storage, nz):
+    """The wall kernel runs beside the bulk kernel, so a boundary node written by both would
+    race.  With odd nz the two-column bulk kernel's last pair starts on the closed end
+    column; it must leave that node to the wall kernel: three runs of the same problem are
+    bit-identical.  (test_gpu_batch's 3 x 3 instance, stepped by other kernels, compares
+    the result itself.)"""
+    out = []
+    for _ in range(3):
+        s = lbm.Solver(lbm.lbm_params_default(nr=21, nz=nz, Ra=1e4, storage=storage))
+        s.step(200)
+        out.append(s.export_populations())
+    for o in out[1:]:
+        assert all(np.array_equal(a, b, equal_nan=True) for a, b in zip(out[0], o))
+
+
 def test_largest_domain_runs(lbm):
     """8192 x 8192 (the stress case's size), FP16 storage, tau_nu = 0.51."""
     phi = _config5_phi()
