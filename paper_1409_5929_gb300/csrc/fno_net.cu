@@ -56,6 +56,17 @@ constexpr int SPIN = 1 << 22;   // try_wait rounds of one bounded wait
 __device__ int g_net_error;
 
 // ------------------------------------------------------------------ helpers --
+// Programmatic dependent launch: every kernel here is launched with the attribute that
+// lets it start while the kernel before it in the stream finishes (launch_pdl); each one
+// first lets its own successor be scheduled and then waits until its predecessor has
+// completed and its writes are visible, before touching global or tensor memory.  The
+// successor is scheduled only once every CTA of this grid has started, so a kernel of
+// several waves is never short of SMs for its own CTAs.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ uint4 pack8(const float* v) {
     uint4 u;
     __nv_bfloat162 t;
@@ -141,6 +152,7 @@ __device__ __forceinline__ void recover(const uint64_t* mbar, const uint32_t* ph
 // ------------------------------------------------------------------- pack --
 __global__ void k_pack(const float* __restrict__ src, int64_t so, int64_t si, int O, int I, bf16* __restrict__ dst,
                        int Opad, int Ipad) {
+    pdl_enter();
     const int64_t n = (int64_t)Opad * Ipad;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
         const int o = (int)(idx / Ipad), i = (int)(idx % Ipad);
@@ -155,6 +167,7 @@ struct PackJobs {
 };
 
 __global__ void k_pack_many(const PackJobs jobs) {
+    pdl_enter();
     const fno_net_pack_job& jb = jobs.j[blockIdx.y];
     const int64_t n = (int64_t)jb.Opad * jb.Ipad;
     const float* src = jb.src;
@@ -196,6 +209,7 @@ struct FwdSmem {
 
 template <int C, int KZ2, int MODE>
 __global__ void __launch_bounds__(256) k_fwd(const FwdP a) {
+    pdl_enter();
     using S = FwdSmem<C, KZ2, MODE>;
     constexpr int G = S::G, KIN = S::KIN, HIN = S::HIN;
     constexpr bool IZ = S::IZ, ZF = S::ZF;
@@ -388,6 +402,7 @@ struct ProjCols {
 
 template <int C, bool TRAIN>
 __global__ void __launch_bounds__(256, C == 32 ? 2 : 1) k_proj(const ProjP a) {
+    pdl_enter();
     constexpr int H = 128, HI = ProjSmem<C>::HI;
     extern __shared__ uint8_t dsm[];
     uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -647,6 +662,7 @@ struct BwdSmem {
 // blocks each thread adds to 32 registers; columns 128.. the dV accumulator of the group.
 template <int C, int KZ2, int MODE>
 __global__ void __launch_bounds__(256, 2) k_bwd(const BwdP a) {
+    pdl_enter();
     using S = BwdSmem<C, KZ2, MODE>;
     constexpr int G = S::G;
     constexpr bool HB = S::HB, HA = S::HA;
@@ -860,6 +876,7 @@ __global__ void __launch_bounds__(256, 2) k_bwd(const BwdP a) {
 template <int C>
 __global__ void __launch_bounds__(128) k_r2k(const bf16* __restrict__ in, const bf16* __restrict__ f2,
                                              float* __restrict__ out, int B, int nr, int M) {
+    pdl_enter();
     const int K = 2 * nr, kz = blockIdx.x % M, b = blockIdx.x / M;
     extern __shared__ uint8_t dsm[];
     uint8_t* sA = reinterpret_cast<uint8_t*>(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
@@ -917,6 +934,7 @@ __global__ void __launch_bounds__(128) k_r2k(const bf16* __restrict__ in, const 
 template <int C>
 __global__ void __launch_bounds__(128) k_k2r(const float* __restrict__ in, const bf16* __restrict__ f2i,
                                              bf16* __restrict__ out, int B, int nr, int M) {
+    pdl_enter();
     const int K = 4 * M, ntm = 2 * nr / 128;
     const int mt = blockIdx.x % ntm, kz = (blockIdx.x / ntm) % M, b = blockIdx.x / (ntm * M);
     extern __shared__ uint8_t dsm[];
@@ -975,6 +993,7 @@ __global__ void __launch_bounds__(128) k_k2r(const float* __restrict__ in, const
 // CTA (kz, kr): the mode's weights R[kr][kz] (C x C complex) and the batch's coefficients.
 __global__ void k_mixf(const float* __restrict__ W, const float* __restrict__ R, float* __restrict__ Y, int B, int C,
                        int M) {
+    pdl_enter();
     extern __shared__ float s[];
     float* sR = s;                 // C x C x 2
     float* sW = sR + 2 * C * C;    // [part][b][c]
@@ -1001,6 +1020,7 @@ __global__ void k_mixf(const float* __restrict__ W, const float* __restrict__ R,
 
 __global__ void k_mixb(const float* __restrict__ W, const float* __restrict__ R, const float* __restrict__ dY,
                        float* __restrict__ dW, float* __restrict__ dR, int B, int C, int M, int accumulate) {
+    pdl_enter();
     extern __shared__ float s[];
     float* sR = s;
     float* sW = sR + 2 * C * C;
@@ -1057,6 +1077,23 @@ static int sms() {
     return g_sms;
 }
 
+// Launch with programmatic stream serialization allowed (see pdl_enter).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 static bool dims_ok(const fno_net_dims* d, std::string* why) {
     auto no = [&](const char* m) {
         if (why) *why = m;
@@ -1091,8 +1128,8 @@ int fno_net_pack(const float* src, int64_t so, int64_t si, int O, int I, void* d
         return fail(FNO_NET_ERR_INVALID, "fno_net_pack: bad arguments");
     const int64_t n = (int64_t)Opad * Ipad;
     if (n == 0) return FNO_NET_OK;
-    k_pack<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(
-        src, so, si, O, I, (bf16*)dst, Opad, Ipad);
+    NCK(launch_pdl(k_pack, dim3((unsigned)std::min<int64_t>((n + 255) / 256, 4096)), dim3(256), 0, (cudaStream_t)stream, 
+        src, so, si, O, I, (bf16*)dst, Opad, Ipad));
     NCK(cudaGetLastError());
     return FNO_NET_OK;
 }
@@ -1117,7 +1154,7 @@ int fno_net_pack_many(const fno_net_pack_job* jobs, int n, void* stream) {
     }
     if (most == 0) return FNO_NET_OK;
     const dim3 grid((unsigned)std::min<int64_t>((most + 255) / 256, 256), (unsigned)n);
-    k_pack_many<<<grid, 256, 0, (cudaStream_t)stream>>>(pj);
+    NCK(launch_pdl(k_pack_many, dim3(grid), dim3(256), 0, (cudaStream_t)stream, pj));
     NCK(cudaGetLastError());
     return FNO_NET_OK;
 }
@@ -1126,7 +1163,7 @@ int fno_net_pack_many(const fno_net_pack_job* jobs, int n, void* stream) {
     if (d->width == C_ && 2 * d->modes == K_ && mode == MODE_) {                                       \
         const size_t sb = std::max(FwdSmem<C_, K_, MODE_>::bytes(d->nz), SMEM_2_PER_SM);               \
         if (int rc = set_smem(k_fwd<C_, K_, MODE_>, sb)) return rc;                                    \
-        k_fwd<C_, K_, MODE_><<<grid, 256, sb, s>>>(p);                                                  \
+        NCK(launch_pdl(k_fwd<C_, K_, MODE_>, dim3(grid), dim3(256), sb, s, p));                                                  \
         launched = true;                                                                              \
     }
 
@@ -1171,19 +1208,19 @@ int fno_net_proj(const fno_net_dims* d, const void* hL, const void* q1w, const v
         const size_t sb = std::max(ProjSmem<32>::bytes, SMEM_2_PER_SM);
         if (t) {
             if (int rc = set_smem(k_proj<32, true>, sb)) return rc;
-            k_proj<32, true><<<grid, 256, sb, s>>>(p);
+            NCK(launch_pdl(k_proj<32, true>, dim3(grid), dim3(256), sb, s, p));
         } else {
             if (int rc = set_smem(k_proj<32, false>, sb)) return rc;
-            k_proj<32, false><<<grid, 256, sb, s>>>(p);
+            NCK(launch_pdl(k_proj<32, false>, dim3(grid), dim3(256), sb, s, p));
         }
     } else {
         const size_t sb = std::max(ProjSmem<64>::bytes, SMEM_1_PER_SM);
         if (t) {
             if (int rc = set_smem(k_proj<64, true>, sb)) return rc;
-            k_proj<64, true><<<grid, 256, sb, s>>>(p);
+            NCK(launch_pdl(k_proj<64, true>, dim3(grid), dim3(256), sb, s, p));
         } else {
             if (int rc = set_smem(k_proj<64, false>, sb)) return rc;
-            k_proj<64, false><<<grid, 256, sb, s>>>(p);
+            NCK(launch_pdl(k_proj<64, false>, dim3(grid), dim3(256), sb, s, p));
         }
     }
     NCK(cudaGetLastError());
@@ -1194,7 +1231,7 @@ int fno_net_proj(const fno_net_dims* d, const void* hL, const void* q1w, const v
     if (d->width == C_ && 2 * d->modes == K_ && mode == MODE_) {                                       \
         const size_t sb = std::max(BwdSmem<C_, K_, MODE_>::bytes(d->nz), SMEM_2_PER_SM);               \
         if (int rc = set_smem(k_bwd<C_, K_, MODE_>, sb)) return rc;                                    \
-        k_bwd<C_, K_, MODE_><<<grid, 256, sb, s>>>(p);                                                  \
+        NCK(launch_pdl(k_bwd<C_, K_, MODE_>, dim3(grid), dim3(256), sb, s, p));                                                  \
         launched = true;                                                                              \
     }
 
@@ -1230,10 +1267,10 @@ int fno_net_r2k(const fno_net_dims* d, const void* in, const void* f2_img, float
     const unsigned grid = (unsigned)(d->batch * d->modes);
     if (d->width == 32) {
         if (int rc = set_smem(k_r2k<32>, sb)) return rc;
-        k_r2k<32><<<grid, 128, sb, s>>>((const bf16*)in, (const bf16*)f2_img, out, d->batch, d->nr, d->modes);
+        NCK(launch_pdl(k_r2k<32>, dim3(grid), dim3(128), sb, s, (const bf16*)in, (const bf16*)f2_img, out, d->batch, d->nr, d->modes));
     } else {
         if (int rc = set_smem(k_r2k<64>, sb)) return rc;
-        k_r2k<64><<<grid, 128, sb, s>>>((const bf16*)in, (const bf16*)f2_img, out, d->batch, d->nr, d->modes);
+        NCK(launch_pdl(k_r2k<64>, dim3(grid), dim3(128), sb, s, (const bf16*)in, (const bf16*)f2_img, out, d->batch, d->nr, d->modes));
     }
     NCK(cudaGetLastError());
     return FNO_NET_OK;
@@ -1249,10 +1286,10 @@ int fno_net_k2r(const fno_net_dims* d, const float* in, const void* f2i_img, voi
     const unsigned grid = (unsigned)(d->batch * d->modes * (2 * d->nr / 128));
     if (d->width == 32) {
         if (int rc = set_smem(k_k2r<32>, sb)) return rc;
-        k_k2r<32><<<grid, 128, sb, s>>>(in, (const bf16*)f2i_img, (bf16*)out, d->batch, d->nr, d->modes);
+        NCK(launch_pdl(k_k2r<32>, dim3(grid), dim3(128), sb, s, in, (const bf16*)f2i_img, (bf16*)out, d->batch, d->nr, d->modes));
     } else {
         if (int rc = set_smem(k_k2r<64>, sb)) return rc;
-        k_k2r<64><<<grid, 128, sb, s>>>(in, (const bf16*)f2i_img, (bf16*)out, d->batch, d->nr, d->modes);
+        NCK(launch_pdl(k_k2r<64>, dim3(grid), dim3(128), sb, s, in, (const bf16*)f2i_img, (bf16*)out, d->batch, d->nr, d->modes));
     }
     NCK(cudaGetLastError());
     return FNO_NET_OK;
@@ -1266,7 +1303,7 @@ int fno_net_mix_fwd(const fno_net_dims* d, const float* W, const float* R, float
     const size_t sb = (size_t)(2 * C * C + 2 * B * C) * 4;
     if (sb > 200 * 1024) return fail(FNO_NET_ERR_INVALID, "fno_net_mix_fwd: batch too large");
     if (int rc = set_smem(k_mixf, sb)) return rc;
-    k_mixf<<<(unsigned)(2 * d->modes * d->modes), 256, sb, (cudaStream_t)stream>>>(W, R, Y, B, C, d->modes);
+    NCK(launch_pdl(k_mixf, dim3((unsigned)(2 * d->modes * d->modes)), dim3(256), sb, (cudaStream_t)stream, W, R, Y, B, C, d->modes));
     NCK(cudaGetLastError());
     return FNO_NET_OK;
 }
@@ -1280,8 +1317,8 @@ int fno_net_mix_bwd(const fno_net_dims* d, const float* W, const float* R, const
     const size_t sb = (size_t)(2 * C * C + 4 * B * C) * 4;
     if (sb > 200 * 1024) return fail(FNO_NET_ERR_INVALID, "fno_net_mix_bwd: batch too large");
     if (int rc = set_smem(k_mixb, sb)) return rc;
-    k_mixb<<<(unsigned)(2 * d->modes * d->modes), 256, sb, (cudaStream_t)stream>>>(W, R, dY, dW, dR, B, C, d->modes,
-                                                                                     accumulate);
+    NCK(launch_pdl(k_mixb, dim3((unsigned)(2 * d->modes * d->modes)), dim3(256), sb, (cudaStream_t)stream, W, R, dY, dW, dR, B, C, d->modes,
+                                                                                     accumulate));
     NCK(cudaGetLastError());
     return FNO_NET_OK;
 }
