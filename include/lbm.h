@@ -287,6 +287,19 @@ int lbm_export_populations(lbm_handle *h, int32_t row0, int32_t nrows, double *f
 /* Derived constants and step count of h. */
 int lbm_get_info(lbm_handle *h, lbm_info *out);
 
+/* Bounded waits of the staged 16-bit bulk kernel (not an operation of the paper).  With
+ * 16-bit storage, nz a multiple of 8 and grids of at least 16 blocks per SM, the bulk
+ * step copies each row's source segments into shared memory with bulk copies whose
+ * completion every thread awaits for at most `rounds` polls (default a few seconds).
+ * A wait that runs out marks the handle: the block drains its copies in flight and
+ * stops, so that step's results are invalid.  lbm_wait_status synchronises the handle's
+ * stream and returns LBM_ERR_TIMEOUT if any wait ran out since the last clear (clear = 1
+ * resets the mark), else LBM_OK; lbm_run checks it at every residual check.
+ * lbm_set_wait_limit sets `rounds` (< 0: the default; 0 makes every wait run out at
+ * once, for tests of the error path). */
+int lbm_set_wait_limit(lbm_handle *h, int rounds);
+int lbm_wait_status(lbm_handle *h, int clear);
+
 /* Per-launch timing of the step kernels with CUDA events on the handle's stream.
  * enable = 1 starts recording (and clears the totals), 0 stops.  lbm_kernel_times
  * synchronises and returns the summed milliseconds and launch counts of the bulk

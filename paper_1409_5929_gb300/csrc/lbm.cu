@@ -424,6 +424,60 @@ __device__ __forceinline__ void st2(float* p, int a, V2 v, bool s0, bool s1, boo
     }
 }
 
+// The rest of one row of a column pair once its sources are loaded: the flow reference
+// added back (D_pop of each source's word; g_1 .. g_4 re-expressed against the node's own
+// temperature reference), the recovery and collision, and the store with the own word's
+// D_i removed.  qw(rs, cs): the two reference words of the sources in row kr - 1 + rs and
+// columns (kz0 - 1, kz0), (kz0, kz0 + 1) or (kz0 + 1, kz0 + 2) for cs = 0, 1, 2.
+template <int STO, bool VEC, class QW>
+__device__ __forceinline__ void pair_finish(const Consts<float>& c, const Buf<STO>& B, int plane, int kr, int row,
+                                            int kz0, int p1, int p5, int p8, V2 (&fh)[9], V2 (&gh)[5], V2 ph,
+                                            const QW& qw, bool st0, bool st1) {
+    // the reference words of the sources: the flow part D_pop of the pulled values and,
+    // in their fourth slot, the temperature references R that re-express g_1 .. g_4
+    // against the node's own R(x)
+    const Q2 q0o = qw(1, 1);
+    const V2 rref = q0o.R;
+    {
+        const Q2 qmo = qw(0, 1), qml = qw(0, 0), qmr = qw(0, 2);
+        fh[1] += fref_delta2(p1, qmo);
+        fh[5] += fref_delta2(p5, qml);
+        fh[8] += fref_delta2(p8, qmr);
+        gh[1] += 0.1f * (qmo.R - rref);
+        const Q2 q0l = qw(1, 0), q0r = qw(1, 2);
+        fh[0] += fref_delta2(0, q0o);
+        fh[2] += fref_delta2(2, q0l);
+        fh[4] += fref_delta2(4, q0r);
+        gh[2] += 0.1f * (q0l.R - rref);
+        gh[4] += 0.1f * (q0r.R - rref);
+        const Q2 qpo = qw(2, 1), qpl = qw(2, 0), qpr = qw(2, 2);
+        fh[3] += fref_delta2(3, qpo);
+        fh[6] += fref_delta2(6, qpl);
+        fh[7] += fref_delta2(7, qpr);
+        gh[3] += 0.1f * (qpo.R - rref);
+    }
+    const RowC q = row_consts(c, kr);
+    V2 lin, nl, iph, m0, rho, ur, uz, dT;
+    porous2(c, ph, lin, nl, iph);
+    recover2(c, q, ph, lin, nl, fh, gh, rref, m0, rho, ur, uz, dT);
+    collide2(c, q, ph, lin, nl, iph, fh, gh, rref, m0, rho, ur, uz, dT);
+    auto* __restrict__ Fo = B.f;
+    float* __restrict__ Go = B.g;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fh[i] = fh[i] - fref_delta2(i, q0o);
+    if (VEC && st0 && st1) {   // both lanes stored, aligned: one vector store per population
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i], true, true, true);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], true, true, true);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i], st0, st1, false);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], st0, st1, false);
+    }
+}
+
 // Update rows kr0 .. kr0 + rows - 1 (non-wall rows below nr) of the column pair starting
 // at the even column kz0.  VEC: nz is even, so every row's first element index is even
 // and the own-column pairs are aligned for vector loads and stores.
@@ -472,51 +526,13 @@ __device__ __forceinline__ void update_pair(const Consts<float>& c, const Buf<ST
         gh[3] = ld2(G + 3 * plane, rowp + kz0, rowp + zc1, VEC);
         gh[4] = ld2(G + 4 * plane, row + zp0, row + zp1, false);
         const V2 ph = ld2(phi, row + kz0, row + zc1, VEC);
-        // the reference words of the sources: the flow part D_pop of the pulled values and,
-        // in their fourth slot, the temperature references R that re-express g_1 .. g_4
-        // against the node's own R(x)
-        const Q2 q0o = ldq2(Qp, row + kz0, row + zc1, VEC);
-        const V2 rref = q0o.R;
-        {
-            const Q2 qmo = ldq2(Qp, rowm + kz0, rowm + zc1, VEC), qml = ldq2(Qp, rowm + zm0, rowm + kz0, false);
-            const Q2 qmr = ldq2(Qp, rowm + zp0, rowm + zp1, false);
-            fh[1] += fref_delta2(p1, qmo);
-            fh[5] += fref_delta2(p5, qml);
-            fh[8] += fref_delta2(p8, qmr);
-            gh[1] += 0.1f * (qmo.R - rref);
-            const Q2 q0l = ldq2(Qp, row + zm0, row + kz0, false), q0r = ldq2(Qp, row + zp0, row + zp1, false);
-            fh[0] += fref_delta2(0, q0o);
-            fh[2] += fref_delta2(2, q0l);
-            fh[4] += fref_delta2(4, q0r);
-            gh[2] += 0.1f * (q0l.R - rref);
-            gh[4] += 0.1f * (q0r.R - rref);
-            const Q2 qpo = ldq2(Qp, rowp + kz0, rowp + zc1, VEC), qpl = ldq2(Qp, rowp + zm0, rowp + kz0, false);
-            const Q2 qpr = ldq2(Qp, rowp + zp0, rowp + zp1, false);
-            fh[3] += fref_delta2(3, qpo);
-            fh[6] += fref_delta2(6, qpl);
-            fh[7] += fref_delta2(7, qpr);
-            gh[3] += 0.1f * (qpo.R - rref);
-        }
-        const RowC q = row_consts(c, kr);
-        V2 lin, nl, iph, m0, rho, ur, uz, dT;
-        porous2(c, ph, lin, nl, iph);
-        recover2(c, q, ph, lin, nl, fh, gh, rref, m0, rho, ur, uz, dT);
-        collide2(c, q, ph, lin, nl, iph, fh, gh, rref, m0, rho, ur, uz, dT);
-        auto* __restrict__ Fo = B.f;
-        float* __restrict__ Go = B.g;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fh[i] = fh[i] - fref_delta2(i, q0o);
-        if (VEC && st0 && st1) {   // both lanes stored, aligned: one vector store per population
-#pragma unroll
-            for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i], true, true, true);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], true, true, true);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) st2(Fo + i * plane, row + kz0, fh[i], st0, st1, false);
-#pragma unroll
-            for (int i = 0; i < 5; ++i) st2(Go + i * plane, row + kz0, gh[i], st0, st1, false);
-        }
+        const auto qw = [&](int rs, int cs) {   // words of row kr - 1 + rs, columns left / own / right
+            const int r = rs == 0 ? rowm : (rs == 1 ? row : rowp);
+            if (cs == 1) return ldq2(Qp, r + kz0, r + zc1, VEC);
+            if (cs == 0) return ldq2(Qp, r + zm0, r + kz0, false);
+            return ldq2(Qp, r + zp0, r + zp1, false);
+        };
+        pair_finish<STO, VEC>(c, B, plane, kr, row, kz0, p1, p5, p8, fh, gh, ph, qw, st0, st1);
     }
 }
 
@@ -558,6 +574,189 @@ __global__ void __launch_bounds__(BULK_THREADS, LBM_PAIR_MIN_BLOCKS) k_bulk_pair
     const int kz0 = 2 * (blockIdx.x * BULK_THREADS + threadIdx.x);
     if (kz0 >= c.nz) return;
     update_pair<STO, VEC>(c, A, B, phi, plane, blockIdx.y * RPT, RPT, kz0);
+}
+
+// 16-bit storage, staged: when nz is a multiple of 8, a block whose columns [z0, z0 + 2
+// BULK_THREADS) lie at least 8 columns inside both ends copies the row segments its next
+// row needs (nine flow planes, five thermal planes, the porosity, one new row of reference
+// words) into shared memory with 1-D bulk copies (cp.async.bulk, issued by one thread,
+// completion counted on an mbarrier per buffer), while the current row computes from the
+// other buffer; the e_z = +-1 columns come from there.  Segments start 16-byte aligned:
+// flow planes cover columns z0 - 8 .. z0 + 263, thermal planes z0 - 4 .. z0 + 259,
+// reference words z0 - 2 .. z0 + 257.  Reference words live in a ring of four rows (row
+// mod 4; the pipe axis row's mirror row -1 holds row 0's words).  Other blocks run
+// update_pair on global loads.  Every wait is bounded: a wait that runs out sets *status
+// to LBM_ERR_TIMEOUT, and the block then waits (with the drain bound) for the copies it
+// has in flight and stops.
+#ifndef LBM_PAIR_STAGE
+#define LBM_PAIR_STAGE 1
+#endif
+constexpr int STG_F = 2 * BULK_THREADS + 16;   // columns of a flow segment
+constexpr int STG_G = 2 * BULK_THREADS + 8;    // thermal segment
+constexpr int STG_Q = 2 * BULK_THREADS + 4;    // reference-word segment
+constexpr uint32_t STG_BYTES = 9 * STG_F * 2 + 5 * STG_G * 4 + 2 * BULK_THREADS * 4;   // one row, without words
+constexpr uint32_t STG_QBYTES = STG_Q * 8;
+constexpr int STAGE_SPIN = 1 << 22;            // try_wait rounds of one bounded wait (a few seconds)
+struct __align__(16) PairStage {
+    unsigned short f[2][9][STG_F];
+    float g[2][5][STG_G];
+    float ph[2][2 * BULK_THREADS];
+    uint2 q[4][STG_Q];
+    unsigned long long bar[2];
+};
+static_assert(STG_F * 2 % 16 == 0 && STG_G * 4 % 16 == 0 && STG_Q * 8 % 16 == 0, "16-byte bulk copies");
+
+__device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sm_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Bounded wait for the completion of phase `phase` of an mbarrier.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t phase, int spin) {
+    for (int i = 0; i < spin; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ V2 h16x2(uint32_t w, const __half*) {
+    return {__half22float2(*reinterpret_cast<const __half2*>(&w))};
+}
+__device__ __forceinline__ V2 h16x2(uint32_t w, const __nv_bfloat16*) {
+    return {__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w))};
+}
+__device__ __forceinline__ float h16(unsigned short u, const __half*) { return __half2float(__ushort_as_half(u)); }
+__device__ __forceinline__ float h16(unsigned short u, const __nv_bfloat16*) {
+    return __bfloat162float(__ushort_as_bfloat16(u));
+}
+__device__ __forceinline__ Q2 q2_of(uint2 ua, uint2 ub) {
+    const Qf x = fref_unpack(ua), y = fref_unpack(ub);
+    return {v2(x.A, y.A), v2(x.Jr, y.Jr), v2(x.Jz, y.Jz), v2(x.R, y.R)};
+}
+
+#ifndef LBM_STAGE_MIN_BLOCKS
+#define LBM_STAGE_MIN_BLOCKS 6
+#endif
+// spin: try_wait rounds of the per-row waits (the final drain always uses STAGE_SPIN).
+template <int STO, int RPT>
+__global__ void __launch_bounds__(BULK_THREADS, LBM_STAGE_MIN_BLOCKS) k_bulk_stage(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
+                                                             const float* __restrict__ phi, int plane, int spin,
+                                                             int* __restrict__ status) {
+    using TF = typename St<STO>::TF;
+    __shared__ PairStage sb;
+    const int nz = c.nz, t = threadIdx.x;
+    const int z0 = blockIdx.x * 2 * BULK_THREADS, r0 = blockIdx.y * RPT, kz0 = z0 + 2 * t;
+    if (z0 < 8 || z0 + 2 * BULK_THREADS + 8 > nz) {   // a block near a z end: global loads
+        if (kz0 < nz) update_pair<STO, true>(c, A, B, phi, plane, r0, RPT, kz0);
+        return;
+    }
+    const bool row0_wall = c.geometry == ANNULUS || c.geometry == ANNULUS_PERIODIC_Z;
+    const auto computes = [&](int kr) { return kr < c.nr - 1 && (kr > 0 || !row0_wall); };
+    const TF* __restrict__ F = A.f;
+    const float* __restrict__ G = A.g;
+    const uint2* __restrict__ Qp = c.fref;
+    const int rows = min(RPT, c.nr - r0);
+    const uint32_t bar0 = sm_addr(&sb.bar[0]), bar1 = sm_addr(&sb.bar[1]);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // thread 0: copy the sources of row r0 + j into buffer j & 1, and the reference words
+    // it needs first (rows kr - 1 .. kr + 1 for the first row, then row kr + 1)
+    const auto issue = [&](int j) {
+        const int kr = r0 + j, b = j & 1;
+        const uint32_t bar = b ? bar1 : bar0;
+        const int q_lo = j == 0 ? kr - 1 : kr + 1, q_hi = min(kr + 1, c.nr - 1);
+        const bool axis = kr == 0 && !row0_wall;   // pipe axis: row -1 mirrors row 0
+        int nq = 0;
+        for (int qr = q_lo; qr <= q_hi; ++qr) nq += qr >= 0 || axis;
+        const bool comp = computes(kr);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // after the reads of the buffer's last use
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((comp ? STG_BYTES : 0u) + nq * STG_QBYTES)
+                     : "memory");
+        if (comp) {
+            const int row = kr * nz, rowp = row + nz, rowm = axis ? row : row - nz;
+            const int p1 = axis ? 3 : 1, p5 = axis ? 6 : 5, p8 = axis ? 7 : 8;
+            const int fsrc[9] = {row, rowm + p1 * plane, row + 2 * plane, rowp + 3 * plane, row + 4 * plane,
+                                 rowm + p5 * plane, rowp + 6 * plane, rowp + 7 * plane, rowm + p8 * plane};
+#pragma unroll
+            for (int i = 0; i < 9; ++i) bulk_copy(sb.f[b][i], F + fsrc[i] + z0 - 8, STG_F * 2, bar);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) bulk_copy(sb.g[b][i], G + (i == 1 || i == 3 ? fsrc[i] : row + i * plane) + z0 - 4,
+                                                  STG_G * 4, bar);
+            bulk_copy(sb.ph[b], phi + row + z0, 2 * BULK_THREADS * 4, bar);
+        }
+        for (int qr = q_lo; qr <= q_hi; ++qr)
+            if (qr >= 0 || axis) bulk_copy(sb.q[qr & 3], Qp + (qr < 0 ? 0 : qr) * nz + z0 - 2, STG_QBYTES, bar);
+    };
+    if (t == 0) issue(0);
+    bool ok = true;
+#pragma unroll 1
+    for (int j = 0; j < rows; ++j) {
+        if (t == 0 && j + 1 < rows) issue(j + 1);
+        const int kr = r0 + j, b = j & 1;
+        ok = bar_wait(b ? bar1 : bar0, (j >> 1) & 1, spin);
+        if (computes(kr)) {
+            const bool axis = kr == 0;
+            const int p1 = axis ? 3 : 1, p5 = axis ? 6 : 5, p8 = axis ? 7 : 8;
+            // segment index of column z: z - z0 + 8 (flow), + 4 (thermal), + 2 (words)
+            const auto own = [&](int i) { return h16x2(reinterpret_cast<const uint32_t*>(sb.f[b][i])[t + 4], F); };
+            const auto sh = [&](int i, int k) { return v2(h16(sb.f[b][i][2 * t + k], F), h16(sb.f[b][i][2 * t + k + 1], F)); };
+            const auto gown = [&](int i) { return V2{*reinterpret_cast<const float2*>(&sb.g[b][i][2 * t + 4])}; };
+            const auto gsh = [&](int i, int k) { return v2(sb.g[b][i][2 * t + k], sb.g[b][i][2 * t + k + 1]); };
+            V2 fh[9], gh[5];
+            fh[0] = own(0);
+            fh[1] = own(1);
+            fh[2] = sh(2, 7);
+            fh[3] = own(3);
+            fh[4] = sh(4, 9);
+            fh[5] = sh(5, 7);
+            fh[6] = sh(6, 7);
+            fh[7] = sh(7, 9);
+            fh[8] = sh(8, 9);
+            gh[0] = gown(0);
+            gh[1] = gown(1);
+            gh[2] = gsh(2, 3);
+            gh[3] = gown(3);
+            gh[4] = gsh(4, 5);
+            const V2 ph{*reinterpret_cast<const float2*>(&sb.ph[b][2 * t])};
+            const auto qw = [&](int rs, int cs) {   // words 2t + 2, 2t + 3: the own pair
+                const uint2* q = sb.q[(kr - 1 + rs) & 3];
+                const uint4 o = *reinterpret_cast<const uint4*>(q + 2 * t + 2);
+                if (cs == 1) return q2_of(make_uint2(o.x, o.y), make_uint2(o.z, o.w));
+                if (cs == 0) return q2_of(q[2 * t + 1], make_uint2(o.x, o.y));
+                return q2_of(make_uint2(o.z, o.w), q[2 * t + 4]);
+            };
+            pair_finish<STO, true>(c, B, plane, kr, kr * nz, kz0, p1, p5, p8, fh, gh, ph, qw, true, true);
+        }
+        if (__syncthreads_or(!ok)) {   // a wait ran out: drain what is in flight and stop
+            if (t == 0) {
+                atomicExch(status, LBM_ERR_TIMEOUT);
+                bar_wait(b ? bar1 : bar0, (j >> 1) & 1, STAGE_SPIN);
+                if (j + 1 < rows) bar_wait(b ? bar0 : bar1, ((j + 1) >> 1) & 1, STAGE_SPIN);
+            }
+            return;
+        }
+    }
+}
+
+// The staged kernel keeps sizeof(PairStage) (30 KB) of shared memory per block; at
+// LBM_PAIR_MIN_BLOCKS blocks per SM that needs the largest shared-memory carveout.
+template <int STO>
+static cudaError_t stage_carveout() {
+    return cudaFuncSetAttribute(k_bulk_stage<STO, BULK_RPT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // Wall nodes; LIN / LOUT: layouts read and written (in-place storage alternates S and L).
@@ -1163,6 +1362,8 @@ struct lbm_handle {
     uint8_t* cls = nullptr;
     bool timing = false;
     std::vector<cudaEvent_t> ev;   // (bulk start, bulk end, wall start, wall end) per timed step
+    int* wait_status = nullptr;    // 16-bit storage: LBM_ERR_TIMEOUT once a bounded wait of the staged kernel ran out
+    int spin = STAGE_SPIN;         // try_wait rounds of its per-row waits
 };
 
 static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
@@ -1416,6 +1617,7 @@ int lbm_destroy(lbm_handle* h) {
     cudaFree(h->result);
     cudaFree(h->bad);
     cudaFree(h->cls);
+    cudaFree(h->wait_status);
     for (auto e : h->ev) cudaEventDestroy(e);
     delete h;
     return LBM_OK;
@@ -1447,6 +1649,10 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
     if (e != cudaSuccess) { delete h; return fail(LBM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); }
     e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) { delete h; return fail(LBM_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e)); }
+    if (p->storage != LBM_F32) {
+        e = p->storage == LBM_F16 ? stage_carveout<LBM_F16>() : stage_carveout<LBM_BF16>();
+        if (e != cudaSuccess) { delete h; return fail(LBM_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)); }
+    }
     h->N = (int64_t)p->nr * p->nz;
     h->plane = (h->N + 63) / 64 * 64;
     h->mstride = h->plane;
@@ -1472,6 +1678,9 @@ int lbm_create(const lbm_params* p, lbm_handle** out) {
         ALLOC(h->fref, h->plane * sizeof(uint2));
         h->cd.fref = h->fref;
         h->cf.fref = h->fref;
+        ALLOC(h->wait_status, sizeof(int));
+        e = cudaMemset(h->wait_status, 0, sizeof(int));
+        if (e != cudaSuccess) { lbm_destroy(h); return fail(LBM_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e)); }
     }
     ALLOC(h->phi, h->plane * phi_size(p->storage));
     ALLOC(h->partials, (size_t)h->pblocks * RES_NV * sizeof(double));
@@ -1693,7 +1902,8 @@ static int launch_step(lbm_handle* h) {
             auto A = bufp<S_>(h, h->cur);
             auto B = bufp<S_>(h, h->cur ^ 1);
             const float* ph = (const float*)h->phi;
-            if (vec && rpt > 1) k_bulk_pair<S_, true, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
+            if (rpt > 1 && h->p.nz % 8 == 0 && LBM_PAIR_STAGE) k_bulk_stage<S_, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane, h->spin, h->wait_status);
+            else if (vec && rpt > 1) k_bulk_pair<S_, true, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
             else if (vec) k_bulk_pair<S_, true, 1><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
             else if (rpt > 1) k_bulk_pair<S_, false, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
             else k_bulk_pair<S_, false, 1><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
@@ -1899,6 +2109,7 @@ int lbm_run(lbm_handle* h, int64_t max_steps, int64_t check_every, double tol, i
         if ((rc = lbm_rebase(h))) break;
         if ((rc = lbm_step(h, k))) break;
         done += k;
+        if ((rc = lbm_wait_status(h, 0))) break;   // before the residual reads a state the timeout left invalid
         if ((rc = snapshot(h, h->cur, a))) break;
         double m;
         rc = residual_between(h, a, b, &r, &m);
@@ -2039,6 +2250,24 @@ int lbm_export_populations(lbm_handle* h, int32_t row0, int32_t nrows, double* f
 int lbm_get_info(lbm_handle* h, lbm_info* out) {
     if (!h || !out) return fail(LBM_ERR_INVALID, "NULL argument");
     *out = h->info;
+    return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_handle* h, int rounds) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    h->spin = rounds < 0 ? STAGE_SPIN : rounds;
+    return LBM_OK;
+}
+
+int lbm_wait_status(lbm_handle* h, int clear) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    if (!h->wait_status) return LBM_OK;
+    CK(cudaSetDevice(h->device));
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, h->wait_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (clear && v) CK(cudaMemsetAsync(h->wait_status, 0, sizeof(int), h->stream));
+    if (v) return fail(LBM_ERR_TIMEOUT, "a bounded wait of the staged bulk kernel ran out (step results are invalid)");
     return LBM_OK;
 }
 

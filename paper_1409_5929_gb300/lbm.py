@@ -80,6 +80,8 @@ _SIGS = {
     "lbm_export_populations": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp]),
     "lbm_get_info": (C.c_int, [_vp, C.POINTER(lbm_info)]),
     "lbm_set_timing": (C.c_int, [_vp, C.c_int]),
+    "lbm_set_wait_limit": (C.c_int, [_vp, C.c_int]),
+    "lbm_wait_status": (C.c_int, [_vp, C.c_int]),
     "lbm_kernel_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]),
     "lbm_field_residual_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, _vp, _vp, C.c_int64,
@@ -268,6 +270,18 @@ def lbm_get_info(h) -> lbm_info:
 
 def lbm_set_timing(h, enable: bool):
     _check(load().lbm_set_timing(h, int(enable)))
+
+
+def lbm_set_wait_limit(h, rounds: int):
+    _check(load().lbm_set_wait_limit(h, int(rounds)))
+
+
+def lbm_wait_status(h, clear: bool = False) -> int:
+    """LBM_OK, or LBM_ERR_TIMEOUT if a bounded wait of the staged bulk kernel ran out."""
+    rc = load().lbm_wait_status(h, int(clear))
+    if rc not in (LBM_OK, LBM_ERR_TIMEOUT):
+        _check(rc)
+    return rc
 
 
 def lbm_kernel_times(h):
