@@ -41,8 +41,9 @@ E2E_STEPS = 50                    # minimum length of the end-to-end window (ste
 # DRAM traffic of one k_bulk launch on the 4096 x 8192 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of the bulk kernel in one single-pass ncu capture of this
 # benchmark), valid only for the bulk kernel's source it was taken on (_kernel_hash).
-TRAFFIC = {("f32", 4096, 8192): ("00835f3f7241bf06", 2089972224 + 1827687424),
-           ("f16", 4096, 8192): ("00835f3f7241bf06", 1692685568 + 1230361856)}
+TRAFFIC = {("f32", 4096, 8192): ("e6fefb4c32bbea41", 2090093568 + 1827627520),
+           ("f16", 4096, 8192): ("e6fefb4c32bbea41", 1691415552 + 1227592704),
+           ("bf16", 4096, 8192): ("e6fefb4c32bbea41", 1691169536 + 1227447552)}
 
 
 def _kernel_hash() -> str:
