@@ -288,9 +288,9 @@ int lbm_export_populations(lbm_handle *h, int32_t row0, int32_t nrows, double *f
 int lbm_get_info(lbm_handle *h, lbm_info *out);
 
 /* Bounded waits of the staged 16-bit bulk kernel (not an operation of the paper).  With
- * 16-bit storage, nz a multiple of 8 and grids of at least 16 blocks per SM, the bulk
- * step copies each row's source segments into shared memory with bulk copies whose
- * completion every thread awaits for at most `rounds` polls (default a few seconds).
+ * 16-bit storage, even nz and grids of at least 16 blocks per SM, the bulk step copies
+ * each row's source segments into shared memory with bulk copies whose completion every
+ * thread awaits for at most `rounds` polls (default a few seconds).
  * A wait that runs out marks the handle: the block drains its copies in flight and
  * stops, so that step's results are invalid.  lbm_wait_status synchronises the handle's
  * stream and returns LBM_ERR_TIMEOUT if any wait ran out since the last clear (clear = 1
@@ -299,6 +299,10 @@ int lbm_get_info(lbm_handle *h, lbm_info *out);
  * once, for tests of the error path). */
 int lbm_set_wait_limit(lbm_handle *h, int rounds);
 int lbm_wait_status(lbm_handle *h, int clear);
+/* enable = 0 runs the 16-bit bulk step on global loads everywhere (the update and its
+ * arithmetic are the same; the staged kernel only moves the loads); 1 (default) stages
+ * where it applies. */
+int lbm_set_staging(lbm_handle *h, int enable);
 
 /* Per-launch timing of the step kernels with CUDA events on the handle's stream.
  * enable = 1 starts recording (and clears the totals), 0 stops.  lbm_kernel_times
@@ -381,6 +385,12 @@ int lbm_batch_pipe_nusselt(lbm_batch *b, int32_t i, double *nu, int32_t nz);
  * advances by the steps the tuning ran (2 warm-up steps + `steps` per shape; the batch's
  * step count in lbm_batch_get_info includes them). */
 int lbm_batch_tune(lbm_batch *b, int32_t steps, int32_t *cols, int32_t *rows, float *ms_per_step);
+/* lbm_set_wait_limit and lbm_wait_status for the batch's staged 16-bit bulk kernel
+ * (instances with even nz; the tuned tile shape then serves the odd-nz instances and the
+ * reference refresh).  lbm_batch_run checks the status after every check interval. */
+int lbm_batch_set_wait_limit(lbm_batch *b, int rounds);
+int lbm_batch_wait_status(lbm_batch *b, int clear);
+int lbm_batch_set_staging(lbm_batch *b, int enable);
 /* Derived constants of instance i; steps = steps taken by the batch. */
 int lbm_batch_get_info(lbm_batch *b, int32_t i, lbm_info *out);
 int lbm_batch_destroy(lbm_batch *b);

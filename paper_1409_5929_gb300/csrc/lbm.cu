@@ -576,35 +576,46 @@ __global__ void __launch_bounds__(BULK_THREADS, LBM_PAIR_MIN_BLOCKS) k_bulk_pair
     update_pair<STO, VEC>(c, A, B, phi, plane, blockIdx.y * RPT, RPT, kz0);
 }
 
-// 16-bit storage, staged: when nz is a multiple of 8, a block whose columns [z0, z0 + 2
-// BULK_THREADS) lie at least 8 columns inside both ends copies the row segments its next
-// row needs (nine flow planes, five thermal planes, the porosity, one new row of reference
-// words) into shared memory with 1-D bulk copies (cp.async.bulk, issued by one thread,
-// completion counted on an mbarrier per buffer), while the current row computes from the
-// other buffer; the e_z = +-1 columns come from there.  Segments start 16-byte aligned:
-// flow planes cover columns z0 - 8 .. z0 + 263, thermal planes z0 - 4 .. z0 + 259,
-// reference words z0 - 2 .. z0 + 257.  Reference words live in a ring of four rows (row
-// mod 4; the pipe axis row's mirror row -1 holds row 0's words).  Other blocks run
-// update_pair on global loads.  Every wait is bounded: a wait that runs out sets *status
-// to LBM_ERR_TIMEOUT, and the block then waits (with the drain bound) for the copies it
-// has in flight and stops.
-#ifndef LBM_PAIR_STAGE
-#define LBM_PAIR_STAGE 1
-#endif
-constexpr int STG_F = 2 * BULK_THREADS + 16;   // columns of a flow segment
-constexpr int STG_G = 2 * BULK_THREADS + 8;    // thermal segment
-constexpr int STG_Q = 2 * BULK_THREADS + 4;    // reference-word segment
-constexpr uint32_t STG_BYTES = 9 * STG_F * 2 + 5 * STG_G * 4 + 2 * BULK_THREADS * 4;   // one row, without words
-constexpr uint32_t STG_QBYTES = STG_Q * 8;
-constexpr int STAGE_SPIN = 1 << 22;            // try_wait rounds of one bounded wait (a few seconds)
+// 16-bit storage, staged (even nz): a block of NT threads covers the columns [z0, z0 + 2 NT)
+// of RPT rows.  For each row it needs one run of columns [a, b) = [z0 - 1, z0 + 2 NT + 1)
+// (clipped to the row) of the source row of every population plane, the porosity of its
+// own columns and the reference words of three rows.  Thread 0 copies each run into shared
+// memory with a 1-D bulk copy (cp.async.bulk) of the 16-byte-aligned window around it
+// (the window may take a few elements of the neighbouring row, never of another plane:
+// planes are multiples of 64 elements), completion counted in bytes on an mbarrier per
+// buffer; the next row's copies are in flight while the current row computes from the
+// other buffer.  Reference words live in a ring of four rows (row mod 4; the pipe axis
+// row's mirror row -1 holds row 0's words), so each row after the first copies one new
+// row of them.  At a closed z end the clipped runs serve every stored lane (a lane on an
+// end column is not stored, as in update_pair; it reads one column past the run, inside
+// the shared block, and computes on whatever it finds there);
+// blocks at a periodic z end run update_pair.  Every wait is bounded: a wait that runs
+// out sets *status to LBM_ERR_TIMEOUT, and the block then waits (with the drain bound)
+// for the copies it has in flight and stops.
+constexpr int STAGE_SPIN = 1 << 22;   // try_wait rounds of one bounded wait (a few seconds)
+template <int NT>
 struct __align__(16) PairStage {
-    unsigned short f[2][9][STG_F];
-    float g[2][5][STG_G];
-    float ph[2][2 * BULK_THREADS];
-    uint2 q[4][STG_Q];
-    unsigned long long bar[2];
+    static constexpr int F = 2 * NT + 16, G = 2 * NT + 8, Q = 2 * NT + 4, P = 2 * NT + 4;   // window capacities
+    uint4 pad;                   // column -1 of the first window (read by an unstored lane) lands here
+    unsigned short f[2][9][F];   // 16-bit flow sources, two rows in flight
+    float g[2][5][G];            // thermal sources
+    float ph[2][P];              // porosity of the own columns
+    uint2 q[4][Q];               // reference words, ring over row mod 4
+    unsigned long long bar[2];   // one mbarrier per buffer
 };
-static_assert(STG_F * 2 % 16 == 0 && STG_G * 4 % 16 == 0 && STG_Q * 8 % 16 == 0, "16-byte bulk copies");
+
+// The 16-byte-aligned window of elements (U per 16 bytes, ES bytes each) around columns
+// [a, b) of row R of a plane with row stride nz: its first element, the window index of
+// column a, and its length in bytes.
+struct Win {
+    int start, off;
+    uint32_t bytes;
+};
+template <int U, int ES>
+__device__ __forceinline__ Win win(int R, int nz, int a, int b) {
+    const int e0 = R * nz + a, s = e0 & -U, e1 = (R * nz + b + U - 1) & -U;
+    return {s, e0 - s, (uint32_t)((e1 - s) * ES)};
+}
 
 __device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
@@ -642,19 +653,23 @@ __device__ __forceinline__ Q2 q2_of(uint2 ua, uint2 ub) {
     return {v2(x.A, y.A), v2(x.Jr, y.Jr), v2(x.Jz, y.Jz), v2(x.R, y.R)};
 }
 
-#ifndef LBM_STAGE_MIN_BLOCKS
-#define LBM_STAGE_MIN_BLOCKS 6
-#endif
+// One staged block: rows r0 .. r0 + RPT - 1, columns z0 .. z0 + 2 NT - 1 (see above).
 // spin: try_wait rounds of the per-row waits (the final drain always uses STAGE_SPIN).
-template <int STO, int RPT>
-__global__ void __launch_bounds__(BULK_THREADS, LBM_STAGE_MIN_BLOCKS) k_bulk_stage(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
-                                                             const float* __restrict__ phi, int plane, int spin,
-                                                             int* __restrict__ status) {
+// ALN: nz is a multiple of 8 and the blocks at both z ends run update_pair, so every staged
+// block starts its runs at column z0 - 1 = 7 mod 8 of a row that starts 16-byte aligned
+// (the window index of each column is a constant offset from it) and stores both lanes of
+// every thread.
+template <int STO, int RPT, int NT, bool ALN>
+__device__ __forceinline__ void stage_block(const Consts<float>& c, const Buf<STO>& A, const Buf<STO>& B,
+                                            const float* __restrict__ phi, int plane, int r0, int z0, int spin,
+                                            int* __restrict__ status, PairStage<NT>& sb) {
     using TF = typename St<STO>::TF;
-    __shared__ PairStage sb;
-    const int nz = c.nz, t = threadIdx.x;
-    const int z0 = blockIdx.x * 2 * BULK_THREADS, r0 = blockIdx.y * RPT, kz0 = z0 + 2 * t;
-    if (z0 < 8 || z0 + 2 * BULK_THREADS + 8 > nz) {   // a block near a z end: global loads
+    const int nz = c.nz, t = threadIdx.x, kz0 = z0 + 2 * t;
+    if (nz & 1) {   // launched for even nz only: the pair reads below assume it
+        if (t == 0) atomicExch(status, LBM_ERR_INVALID);
+        return;
+    }
+    if ((ALN && (z0 == 0 || z0 + 2 * NT + 8 > nz)) || (c.periodic && (z0 == 0 || z0 + 2 * NT >= nz))) {   // global loads
         if (kz0 < nz) update_pair<STO, true>(c, A, B, phi, plane, r0, RPT, kz0);
         return;
     }
@@ -664,6 +679,7 @@ __global__ void __launch_bounds__(BULK_THREADS, LBM_STAGE_MIN_BLOCKS) k_bulk_sta
     const float* __restrict__ G = A.g;
     const uint2* __restrict__ Qp = c.fref;
     const int rows = min(RPT, c.nr - r0);
+    const int a = ALN ? z0 - 1 : max(z0 - 1, 0);   // first column of the runs; they end at min(z0 + 2 NT + 1, nz)
     const uint32_t bar0 = sm_addr(&sb.bar[0]), bar1 = sm_addr(&sb.bar[1]);
     if (t == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
@@ -674,89 +690,134 @@ __global__ void __launch_bounds__(BULK_THREADS, LBM_STAGE_MIN_BLOCKS) k_bulk_sta
     // thread 0: copy the sources of row r0 + j into buffer j & 1, and the reference words
     // it needs first (rows kr - 1 .. kr + 1 for the first row, then row kr + 1)
     const auto issue = [&](int j) {
-        const int kr = r0 + j, b = j & 1;
-        const uint32_t bar = b ? bar1 : bar0;
+        const int kr = r0 + j, bf = j & 1;
+        const uint32_t bar = bf ? bar1 : bar0;
         const int q_lo = j == 0 ? kr - 1 : kr + 1, q_hi = min(kr + 1, c.nr - 1);
         const bool axis = kr == 0 && !row0_wall;   // pipe axis: row -1 mirrors row 0
-        int nq = 0;
-        for (int qr = q_lo; qr <= q_hi; ++qr) nq += qr >= 0 || axis;
         const bool comp = computes(kr);
+        const int Rm = axis ? kr : kr - 1, b = min(z0 + 2 * NT + 1, nz), pb = min(z0 + 2 * NT, nz);
+        const Win wf[3] = {win<8, 2>(Rm, nz, a, b), win<8, 2>(kr, nz, a, b), win<8, 2>(kr + 1, nz, a, b)};
+        const Win wg[3] = {win<4, 4>(Rm, nz, a, b), win<4, 4>(kr, nz, a, b), win<4, 4>(kr + 1, nz, a, b)};
+        const Win wp = win<4, 4>(kr, nz, z0, pb);
+        uint32_t bytes = 0;
+        if (comp)   // three flow slots per row group; thermal slots 0, 2, 4 in row kr, 1 and 3 in the others
+            bytes = 3 * (wf[0].bytes + wf[1].bytes + wf[2].bytes) + 3 * wg[1].bytes + wg[0].bytes + wg[2].bytes +
+                    wp.bytes;
+        for (int qr = q_lo; qr <= q_hi; ++qr)
+            if (qr >= 0 || axis) bytes += win<2, 8>(max(qr, 0), nz, a, b).bytes;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // after the reads of the buffer's last use
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((comp ? STG_BYTES : 0u) + nq * STG_QBYTES)
-                     : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
         if (comp) {
-            const int row = kr * nz, rowp = row + nz, rowm = axis ? row : row - nz;
             const int p1 = axis ? 3 : 1, p5 = axis ? 6 : 5, p8 = axis ? 7 : 8;
-            const int fsrc[9] = {row, rowm + p1 * plane, row + 2 * plane, rowp + 3 * plane, row + 4 * plane,
-                                 rowm + p5 * plane, rowp + 6 * plane, rowp + 7 * plane, rowm + p8 * plane};
+            // flow slot i: plane and row group (0: row kr - 1 or its mirror, 1: kr, 2: kr + 1)
+            const int fpl[9] = {0, p1, 2, 3, 4, p5, 6, 7, p8};
+            const int frg[9] = {1, 0, 1, 2, 1, 0, 2, 2, 0};
 #pragma unroll
-            for (int i = 0; i < 9; ++i) bulk_copy(sb.f[b][i], F + fsrc[i] + z0 - 8, STG_F * 2, bar);
+            for (int i = 0; i < 9; ++i) {
+                const Win& w = wf[frg[i]];
+                bulk_copy(sb.f[bf][i], F + fpl[i] * plane + w.start, w.bytes, bar);
+            }
 #pragma unroll
-            for (int i = 0; i < 5; ++i) bulk_copy(sb.g[b][i], G + (i == 1 || i == 3 ? fsrc[i] : row + i * plane) + z0 - 4,
-                                                  STG_G * 4, bar);
-            bulk_copy(sb.ph[b], phi + row + z0, 2 * BULK_THREADS * 4, bar);
+            for (int i = 0; i < 5; ++i) {
+                const Win& w = wg[frg[i]];
+                bulk_copy(sb.g[bf][i], G + fpl[i] * plane + w.start, w.bytes, bar);
+            }
+            bulk_copy(sb.ph[bf], phi + wp.start, wp.bytes, bar);
         }
         for (int qr = q_lo; qr <= q_hi; ++qr)
-            if (qr >= 0 || axis) bulk_copy(sb.q[qr & 3], Qp + (qr < 0 ? 0 : qr) * nz + z0 - 2, STG_QBYTES, bar);
+            if (qr >= 0 || axis) {
+                const Win w = win<2, 8>(max(qr, 0), nz, a, b);
+                bulk_copy(sb.q[qr & 3], Qp + w.start, w.bytes, bar);
+            }
     };
     if (t == 0) issue(0);
+    const bool active = ALN || kz0 < nz;
     bool ok = true;
 #pragma unroll 1
     for (int j = 0; j < rows; ++j) {
         if (t == 0 && j + 1 < rows) issue(j + 1);
-        const int kr = r0 + j, b = j & 1;
-        ok = bar_wait(b ? bar1 : bar0, (j >> 1) & 1, spin);
-        if (computes(kr)) {
+        const int kr = r0 + j, bf = j & 1;
+        ok = bar_wait(bf ? bar1 : bar0, (j >> 1) & 1, spin);
+        if (active && computes(kr)) {
             const bool axis = kr == 0;
             const int p1 = axis ? 3 : 1, p5 = axis ? 6 : 5, p8 = axis ? 7 : 8;
-            // segment index of column z: z - z0 + 8 (flow), + 4 (thermal), + 2 (words)
-            const auto own = [&](int i) { return h16x2(reinterpret_cast<const uint32_t*>(sb.f[b][i])[t + 4], F); };
-            const auto sh = [&](int i, int k) { return v2(h16(sb.f[b][i][2 * t + k], F), h16(sb.f[b][i][2 * t + k + 1], F)); };
-            const auto gown = [&](int i) { return V2{*reinterpret_cast<const float2*>(&sb.g[b][i][2 * t + 4])}; };
-            const auto gsh = [&](int i, int k) { return v2(sb.g[b][i][2 * t + k], sb.g[b][i][2 * t + k + 1]); };
-            V2 fh[9], gh[5];
-            fh[0] = own(0);
-            fh[1] = own(1);
-            fh[2] = sh(2, 7);
-            fh[3] = own(3);
-            fh[4] = sh(4, 9);
-            fh[5] = sh(5, 7);
-            fh[6] = sh(6, 7);
-            fh[7] = sh(7, 9);
-            fh[8] = sh(8, 9);
-            gh[0] = gown(0);
-            gh[1] = gown(1);
-            gh[2] = gsh(2, 3);
-            gh[3] = gown(3);
-            gh[4] = gsh(4, 5);
-            const V2 ph{*reinterpret_cast<const float2*>(&sb.ph[b][2 * t])};
-            const auto qw = [&](int rs, int cs) {   // words 2t + 2, 2t + 3: the own pair
-                const uint2* q = sb.q[(kr - 1 + rs) & 3];
-                const uint4 o = *reinterpret_cast<const uint4*>(q + 2 * t + 2);
-                if (cs == 1) return q2_of(make_uint2(o.x, o.y), make_uint2(o.z, o.w));
-                if (cs == 0) return q2_of(q[2 * t + 1], make_uint2(o.x, o.y));
-                return q2_of(make_uint2(o.z, o.w), q[2 * t + 4]);
+            const int Rm = axis ? kr : kr - 1;
+            // window index of the own column kz0 in row group rg (the left column is one
+            // below, the right columns one and two above)
+            const auto wo = [&](int R, int U) { return kz0 - a + (ALN ? U - 1 : ((R * nz + a) & (U - 1))); };
+            const int of[3] = {wo(Rm, 8), wo(kr, 8), wo(kr + 1, 8)};
+            const int og[3] = {wo(Rm, 4), wo(kr, 4), wo(kr + 1, 4)};
+            const auto own = [&](int i, int rg) {
+                return h16x2(*reinterpret_cast<const uint32_t*>(&sb.f[bf][i][of[rg]]), F);
             };
-            pair_finish<STO, true>(c, B, plane, kr, kr * nz, kz0, p1, p5, p8, fh, gh, ph, qw, true, true);
+            const auto fat = [&](int i, int rg, int d) {   // columns kz0 + d, kz0 + d + 1
+                return v2(h16(sb.f[bf][i][of[rg] + d], F), h16(sb.f[bf][i][of[rg] + d + 1], F));
+            };
+            const auto gown = [&](int i, int rg) { return V2{*reinterpret_cast<const float2*>(&sb.g[bf][i][og[rg]])}; };
+            const auto gat = [&](int i, int rg, int d) {
+                return v2(sb.g[bf][i][og[rg] + d], sb.g[bf][i][og[rg] + d + 1]);
+            };
+            V2 fh[9], gh[5];
+            fh[0] = own(0, 1);
+            fh[1] = own(1, 0);
+            fh[2] = fat(2, 1, -1);
+            fh[3] = own(3, 2);
+            fh[4] = fat(4, 1, 1);
+            fh[5] = fat(5, 0, -1);
+            fh[6] = fat(6, 2, -1);
+            fh[7] = fat(7, 2, 1);
+            fh[8] = fat(8, 0, 1);
+            gh[0] = gown(0, 1);
+            gh[1] = gown(1, 0);
+            gh[2] = gat(2, 1, -1);
+            gh[3] = gown(3, 2);
+            gh[4] = gat(4, 1, 1);
+            const V2 ph{*reinterpret_cast<const float2*>(&sb.ph[bf][kz0 - z0 + (ALN ? 0 : (kr * nz + z0) & 3)])};
+            const auto qw = [&](int rs, int cs) {
+                const int qr = kr - 1 + rs;
+                const uint2* q = sb.q[qr & 3];
+                const int o = kz0 - a + (ALN ? 1 : ((max(qr, 0) * nz + a) & 1));
+                const uint4 u = *reinterpret_cast<const uint4*>(q + o);   // the own pair's two words
+                if (cs == 1) return q2_of(make_uint2(u.x, u.y), make_uint2(u.z, u.w));
+                if (cs == 0) return q2_of(q[o - 1], make_uint2(u.x, u.y));
+                return q2_of(make_uint2(u.z, u.w), q[o + 2]);
+            };
+            const bool st0 = ALN || kz0 > 0 || c.periodic, st1 = ALN || kz0 + 1 < nz - 1 || c.periodic;
+            pair_finish<STO, true>(c, B, plane, kr, kr * nz, kz0, p1, p5, p8, fh, gh, ph, qw, st0, st1);
         }
         if (__syncthreads_or(!ok)) {   // a wait ran out: drain what is in flight and stop
             if (t == 0) {
                 atomicExch(status, LBM_ERR_TIMEOUT);
-                bar_wait(b ? bar1 : bar0, (j >> 1) & 1, STAGE_SPIN);
-                if (j + 1 < rows) bar_wait(b ? bar0 : bar1, ((j + 1) >> 1) & 1, STAGE_SPIN);
+                bar_wait(bf ? bar1 : bar0, (j >> 1) & 1, STAGE_SPIN);
+                if (j + 1 < rows) bar_wait(bf ? bar0 : bar1, ((j + 1) >> 1) & 1, STAGE_SPIN);
             }
             return;
         }
     }
 }
 
-// The staged kernel keeps sizeof(PairStage) (30 KB) of shared memory per block; at
-// LBM_PAIR_MIN_BLOCKS blocks per SM that needs the largest shared-memory carveout.
+#ifndef LBM_STAGE_MIN_BLOCKS
+#define LBM_STAGE_MIN_BLOCKS 6
+#endif
+template <int STO, int RPT, bool ALN>
+__global__ void __launch_bounds__(BULK_THREADS, LBM_STAGE_MIN_BLOCKS) k_bulk_stage(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
+                                                             const float* __restrict__ phi, int plane, int spin,
+                                                             int* __restrict__ status) {
+    __shared__ PairStage<BULK_THREADS> sb;
+    stage_block<STO, RPT, BULK_THREADS, ALN>(c, A, B, phi, plane, blockIdx.y * RPT, blockIdx.x * 2 * BULK_THREADS,
+                                             spin, status, sb);
+}
+
+// The staged kernel keeps sizeof(PairStage<BULK_THREADS>) (30.7 KB) of shared memory per
+// block; at LBM_STAGE_MIN_BLOCKS blocks per SM that needs the largest shared-memory carveout.
 template <int STO>
 static cudaError_t stage_carveout() {
-    return cudaFuncSetAttribute(k_bulk_stage<STO, BULK_RPT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared);
+    cudaError_t e = cudaFuncSetAttribute(k_bulk_stage<STO, BULK_RPT, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bulk_stage<STO, BULK_RPT, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 // Wall nodes; LIN / LOUT: layouts read and written (in-place storage alternates S and L).
@@ -1364,6 +1425,7 @@ struct lbm_handle {
     std::vector<cudaEvent_t> ev;   // (bulk start, bulk end, wall start, wall end) per timed step
     int* wait_status = nullptr;    // 16-bit storage: LBM_ERR_TIMEOUT once a bounded wait of the staged kernel ran out
     int spin = STAGE_SPIN;         // try_wait rounds of its per-row waits
+    int stage = 1;                 // 16-bit: the staged bulk kernel where it applies (lbm_set_staging)
 };
 
 static int derive(const lbm_params* p, lbm_info* o, Consts<double>* cd) {
@@ -1902,7 +1964,8 @@ static int launch_step(lbm_handle* h) {
             auto A = bufp<S_>(h, h->cur);
             auto B = bufp<S_>(h, h->cur ^ 1);
             const float* ph = (const float*)h->phi;
-            if (rpt > 1 && h->p.nz % 8 == 0 && LBM_PAIR_STAGE) k_bulk_stage<S_, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane, h->spin, h->wait_status);
+            if (vec && rpt > 1 && h->stage && h->p.nz % 8 == 0) k_bulk_stage<S_, BULK_RPT, true><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane, h->spin, h->wait_status);
+            else if (vec && rpt > 1 && h->stage) k_bulk_stage<S_, BULK_RPT, false><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane, h->spin, h->wait_status);
             else if (vec && rpt > 1) k_bulk_pair<S_, true, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
             else if (vec) k_bulk_pair<S_, true, 1><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
             else if (rpt > 1) k_bulk_pair<S_, false, BULK_RPT><<<gb, BULK_THREADS, 0, h->stream>>>(h->cf, A, B, ph, (int)h->plane);
@@ -2253,6 +2316,12 @@ int lbm_get_info(lbm_handle* h, lbm_info* out) {
     return LBM_OK;
 }
 
+int lbm_set_staging(lbm_handle* h, int enable) {
+    if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
+    h->stage = enable != 0;
+    return LBM_OK;
+}
+
 int lbm_set_wait_limit(lbm_handle* h, int rounds) {
     if (!h) return fail(LBM_ERR_INVALID, "handle is NULL");
     h->spin = rounds < 0 ? STAGE_SPIN : rounds;
@@ -2267,7 +2336,9 @@ int lbm_wait_status(lbm_handle* h, int clear) {
     CK(cudaMemcpyAsync(&v, h->wait_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (clear && v) CK(cudaMemsetAsync(h->wait_status, 0, sizeof(int), h->stream));
-    if (v) return fail(LBM_ERR_TIMEOUT, "a bounded wait of the staged bulk kernel ran out (step results are invalid)");
+    if (v == LBM_ERR_TIMEOUT)
+        return fail(LBM_ERR_TIMEOUT, "a bounded wait of the staged bulk kernel ran out (step results are invalid)");
+    if (v) return fail(v, "the staged bulk kernel was launched for an odd nz (step results are invalid)");
     return LBM_OK;
 }
 
@@ -2476,6 +2547,35 @@ __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__
     }
 }
 
+// 16-bit batches: the staged block (stage_block) over tiles (instance, first row, first
+// column) of BATCH_STAGE_NT column pairs and BATCH_STAGE_RPT rows of every active instance
+// with even nz.  On the sweep of 256 instances with Nr 64..512, 128-thread blocks at five
+// per SM (the instance's pointers stay live: 102 registers allowed) measured 0.874 ms per
+// step, 64-thread blocks 0.927 (ten per SM) and 0.969 (twelve, with spills), although
+// 128-column tiles leave fewer thread slots idle on short rows (9 % against 17 %).
+#ifndef LBM_BATCH_STAGE_NT
+#define LBM_BATCH_STAGE_NT 128
+#endif
+#ifndef LBM_BATCH_STAGE_MIN_BLOCKS
+#define LBM_BATCH_STAGE_MIN_BLOCKS 5
+#endif
+constexpr int BATCH_STAGE_NT = LBM_BATCH_STAGE_NT;
+constexpr int BATCH_STAGE_RPT = 4;
+template <int STO>
+__global__ void __launch_bounds__(BATCH_STAGE_NT, LBM_BATCH_STAGE_MIN_BLOCKS) k_batch_stage(
+    const InstDesc* __restrict__ desc, char* __restrict__ pool, int parity, const int4* __restrict__ tiles, int spin,
+    int* __restrict__ status) {
+    __shared__ PairStage<BATCH_STAGE_NT> sb;
+    __shared__ InstDesc sd;   // the tile's instance: constants read from shared memory
+    const int4 t = tiles[blockIdx.x];
+    for (int w = threadIdx.x; w < (int)(sizeof(InstDesc) / sizeof(int)); w += BATCH_STAGE_NT)
+        reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(desc + t.x)[w];
+    __syncthreads();
+    const Buf<STO> A = inst_buf<STO>(sd, pool, parity), B = inst_buf<STO>(sd, pool, parity ^ 1);
+    stage_block<STO, BATCH_STAGE_RPT, BATCH_STAGE_NT, false>(sd.c, A, B, (const float*)(pool + sd.off_phi), (int)sd.plane,
+                                                      t.y, t.z, spin, status, sb);
+}
+
 // Flow reference refresh of every node the tiles cover (all nodes of the active instances),
 // with the bulk kernels' tiles and block shape.
 template <int STO, int RPT>
@@ -2672,6 +2772,12 @@ struct lbm_batch {
     double* partials = nullptr;
     double* result = nullptr;
     std::vector<int> iparity;         // buffer holding the state of an instance that stopped
+    int4* d_stiles = nullptr;         // 16-bit: staged tiles of the active instances with even nz
+    int nstiles = 0;
+    size_t cap_stiles = 0;
+    int* wait_status = nullptr;       // 16-bit: LBM_ERR_TIMEOUT once a bounded wait of k_batch_stage ran out
+    int spin = STAGE_SPIN;            // try_wait rounds of its per-row waits
+    int stage = 1;                    // 16-bit: staged tiles for the even-nz instances (lbm_batch_set_staging)
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;
     int graph_parity = 0;             // batch parity the graph was captured at
@@ -2701,6 +2807,21 @@ static int batch_rebuild(lbm_batch* b) {
     }
     b->ntiles_even = (int)tiles.size();
     tiles.insert(tiles.end(), odd.begin(), odd.end());
+    std::vector<int4> st;
+    if (b->storage != LBM_F32 && b->stage)
+        for (int i : act)
+            if (!(b->p[i].nz & 1))
+                for (int kr = 0; kr < b->p[i].nr; kr += BATCH_STAGE_RPT)
+                    for (int z0 = 0; z0 < b->p[i].nz; z0 += 2 * BATCH_STAGE_NT) st.push_back(make_int4(i, kr, z0, 0));
+    b->nstiles = (int)st.size();
+    if (st.size() > b->cap_stiles) {
+        cudaFree(b->d_stiles);
+        b->d_stiles = nullptr;
+        CK(cudaMalloc((void**)&b->d_stiles, st.size() * sizeof(int4)));
+        b->cap_stiles = st.size();
+    }
+    if (!st.empty())
+        CK(cudaMemcpyAsync(b->d_stiles, st.data(), st.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
     b->ntiles = (int)tiles.size();
     b->nactive = (int)act.size();
     b->nwall = prefix.back();
@@ -2759,9 +2880,14 @@ static int batch_launch_step(lbm_batch* b) {
                                  b->d_desc, b->pool, b->parity, b->d_tiles));
     } else {
         const int ne = b->ntiles_even, no = b->ntiles - b->ntiles_even;
-        if (ne)
+        if (b->stage) {   // even nz: staged tiles
+            if (b->nstiles)
+                DISPATCH_STO16(b->storage, k_batch_stage<S_><<<b->nstiles, BATCH_STAGE_NT, 0, b->stream>>>(
+                                               b->d_desc, b->pool, b->parity, b->d_stiles, b->spin, b->wait_status));
+        } else if (ne) {
             DISPATCH_STO16(b->storage, DISPATCH_RPT(b->rpt, k_batch_bulk<S_, R_, true><<<ne, blk, 0, b->stream>>>(
                                                                 b->d_desc, b->pool, b->parity, b->d_tiles)));
+        }
         if (no)
             DISPATCH_STO16(b->storage, DISPATCH_RPT(b->rpt, k_batch_bulk<S_, R_, false><<<no, blk, 0, b->stream>>>(
                                                                 b->d_desc, b->pool, b->parity, b->d_tiles + ne)));
@@ -2792,6 +2918,8 @@ int lbm_batch_destroy(lbm_batch* b) {
     cudaFree(b->macpool);
     cudaFree(b->fstage);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_stiles);
+    cudaFree(b->wait_status);
     cudaFree(b->d_active);
     cudaFree(b->d_prefix);
     cudaFree(b->partials);
@@ -2862,6 +2990,13 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_prefix, (n + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->partials, (size_t)n * BATCH_RB * RES_NV * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->result, (size_t)n * RES_NV * sizeof(double));
+    if (e == cudaSuccess && b->storage != LBM_F32) {
+        e = cudaMalloc((void**)&b->wait_status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->wait_status, 0, sizeof(int), b->stream);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(b->storage == LBM_F16 ? k_batch_stage<LBM_F16> : k_batch_stage<LBM_BF16>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_desc, b->desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice,
                                               b->stream);
     if (e != cudaSuccess) {
@@ -3064,6 +3199,7 @@ int lbm_batch_run(lbm_batch* b, int64_t max_steps, int64_t check_every, double t
         b->steps += k;
         for (int i = 0; i < b->n; ++i)
             if (b->active[i]) done[i] += k;
+        if ((rc = lbm_batch_wait_status(b, 0))) return rc;   // before the residual reads an invalid state
         if ((rc = batch_snapshot(b, slot))) return rc;
         const dim3 grid(BATCH_RB, b->nactive);
         k_batch_resid<<<grid, 256, 0, b->stream>>>(b->d_desc, b->macpool, slot, b->d_active, b->partials);
@@ -3181,6 +3317,33 @@ int lbm_batch_moments(lbm_batch* b, int32_t i, float* rho, float* ur, float* uz,
 // advanced by the steps it ran (2 warm-up + `steps` per shape).
 static const int kTuneShapes[][3] = {{64, 1, 1}, {128, 1, 1}, {256, 1, 1}, {64, 2, 1}, {128, 2, 1}, {64, 4, 1},
                                      {32, 8, 1}, {64, 1, 2}, {64, 1, 4}, {128, 1, 2}, {128, 1, 4}, {32, 4, 4}};
+
+int lbm_batch_set_staging(lbm_batch* b, int enable) {
+    if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+    b->stage = enable != 0;
+    return batch_rebuild(b);   // the tile lists (and the captured graph) follow the choice
+}
+
+int lbm_batch_set_wait_limit(lbm_batch* b, int rounds) {
+    if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+    b->spin = rounds < 0 ? STAGE_SPIN : rounds;
+    b->graph_dirty = true;   // captured launches hold the old limit
+    return LBM_OK;
+}
+
+int lbm_batch_wait_status(lbm_batch* b, int clear) {
+    if (!b) return fail(LBM_ERR_INVALID, "batch is NULL");
+    if (!b->wait_status) return LBM_OK;
+    CK(cudaSetDevice(b->device));
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, b->wait_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (clear && v) CK(cudaMemsetAsync(b->wait_status, 0, sizeof(int), b->stream));
+    if (v == LBM_ERR_TIMEOUT)
+        return fail(LBM_ERR_TIMEOUT, "a bounded wait of the staged batch kernel ran out (step results are invalid)");
+    if (v) return fail(v, "the staged batch kernel was launched for an odd nz (step results are invalid)");
+    return LBM_OK;
+}
 
 int lbm_batch_tune(lbm_batch* b, int32_t steps, int32_t* bz_out, int32_t* rows_out, float* ms_out) {
     if (!b || steps < 1) return fail(LBM_ERR_INVALID, "bad batch or steps");

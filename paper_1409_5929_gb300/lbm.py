@@ -82,6 +82,10 @@ _SIGS = {
     "lbm_set_timing": (C.c_int, [_vp, C.c_int]),
     "lbm_set_wait_limit": (C.c_int, [_vp, C.c_int]),
     "lbm_wait_status": (C.c_int, [_vp, C.c_int]),
+    "lbm_batch_set_wait_limit": (C.c_int, [_vp, C.c_int]),
+    "lbm_set_staging": (C.c_int, [_vp, C.c_int]),
+    "lbm_batch_set_staging": (C.c_int, [_vp, C.c_int]),
+    "lbm_batch_wait_status": (C.c_int, [_vp, C.c_int]),
     "lbm_kernel_times": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]),
     "lbm_field_residual_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, _vp, _vp, C.c_int64,
@@ -279,6 +283,26 @@ def lbm_set_wait_limit(h, rounds: int):
 def lbm_wait_status(h, clear: bool = False) -> int:
     """LBM_OK, or LBM_ERR_TIMEOUT if a bounded wait of the staged bulk kernel ran out."""
     rc = load().lbm_wait_status(h, int(clear))
+    if rc not in (LBM_OK, LBM_ERR_TIMEOUT):
+        _check(rc)
+    return rc
+
+
+def lbm_set_staging(h, enable: bool):
+    _check(load().lbm_set_staging(h, int(enable)))
+
+
+def lbm_batch_set_staging(b, enable: bool):
+    _check(load().lbm_batch_set_staging(b, int(enable)))
+
+
+def lbm_batch_set_wait_limit(b, rounds: int):
+    _check(load().lbm_batch_set_wait_limit(b, int(rounds)))
+
+
+def lbm_batch_wait_status(b, clear: bool = False) -> int:
+    """LBM_OK, or LBM_ERR_TIMEOUT if a bounded wait of the staged batch kernel ran out."""
+    rc = load().lbm_batch_wait_status(b, int(clear))
     if rc not in (LBM_OK, LBM_ERR_TIMEOUT):
         _check(rc)
     return rc
