@@ -653,16 +653,16 @@ __device__ __forceinline__ Q2 q2_of(uint2 ua, uint2 ub) {
     return {v2(x.A, y.A), v2(x.Jr, y.Jr), v2(x.Jz, y.Jz), v2(x.R, y.R)};
 }
 
-// One staged block: rows r0 .. r0 + RPT - 1, columns z0 .. z0 + 2 NT - 1 (see above).
+// One staged block: rows r0 .. r0 + RPT - 1 (at most), columns z0 .. z0 + 2 NT - 1 (see above).
 // spin: try_wait rounds of the per-row waits (the final drain always uses STAGE_SPIN).
 // ALN: nz is a multiple of 8 and the blocks at both z ends run update_pair, so every staged
 // block starts its runs at column z0 - 1 = 7 mod 8 of a row that starts 16-byte aligned
 // (the window index of each column is a constant offset from it) and stores both lanes of
 // every thread.
-template <int STO, int RPT, int NT, bool ALN>
+template <int STO, int NT, bool ALN>
 __device__ __forceinline__ void stage_block(const Consts<float>& c, const Buf<STO>& A, const Buf<STO>& B,
-                                            const float* __restrict__ phi, int plane, int r0, int z0, int spin,
-                                            int* __restrict__ status, PairStage<NT>& sb) {
+                                            const float* __restrict__ phi, int plane, int r0, int RPT, int z0,
+                                            int spin, int* __restrict__ status, PairStage<NT>& sb) {
     using TF = typename St<STO>::TF;
     const int nz = c.nz, t = threadIdx.x, kz0 = z0 + 2 * t;
     if (nz & 1) {   // launched for even nz only: the pair reads below assume it
@@ -804,8 +804,8 @@ __global__ void __launch_bounds__(BULK_THREADS, LBM_STAGE_MIN_BLOCKS) k_bulk_sta
                                                              const float* __restrict__ phi, int plane, int spin,
                                                              int* __restrict__ status) {
     __shared__ PairStage<BULK_THREADS> sb;
-    stage_block<STO, RPT, BULK_THREADS, ALN>(c, A, B, phi, plane, blockIdx.y * RPT, blockIdx.x * 2 * BULK_THREADS,
-                                             spin, status, sb);
+    stage_block<STO, BULK_THREADS, ALN>(c, A, B, phi, plane, blockIdx.y * RPT, RPT, blockIdx.x * 2 * BULK_THREADS, spin,
+                                        status, sb);
 }
 
 // The staged kernel keeps sizeof(PairStage<BULK_THREADS>) (30.7 KB) of shared memory per
@@ -2548,8 +2548,8 @@ __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__
 }
 
 // 16-bit batches: the staged block (stage_block) over tiles (instance, first row, first
-// column) of BATCH_STAGE_NT column pairs and BATCH_STAGE_RPT rows of every active instance
-// with even nz.  On the sweep of 256 instances with Nr 64..512, 128-thread blocks at five
+// column, rows) of BATCH_STAGE_NT column pairs of every active instance with even nz; the
+// rows per tile (batch_stage_rows) are the same for all tiles of a batch.  On the sweep of 256 instances with Nr 64..512, 128-thread blocks at five
 // per SM (the instance's pointers stay live: 102 registers allowed) measured 0.874 ms per
 // step, 64-thread blocks 0.927 (ten per SM) and 0.969 (twelve, with spills), although
 // 128-column tiles leave fewer thread slots idle on short rows (9 % against 17 %).
@@ -2559,8 +2559,10 @@ __global__ void __launch_bounds__(256) k_batch_bulk(const InstDesc* __restrict__
 #ifndef LBM_BATCH_STAGE_MIN_BLOCKS
 #define LBM_BATCH_STAGE_MIN_BLOCKS 5
 #endif
+#ifndef LBM_BATCH_STAGE_MAX_ROWS
+#define LBM_BATCH_STAGE_MAX_ROWS 16
+#endif
 constexpr int BATCH_STAGE_NT = LBM_BATCH_STAGE_NT;
-constexpr int BATCH_STAGE_RPT = 4;
 template <int STO>
 __global__ void __launch_bounds__(BATCH_STAGE_NT, LBM_BATCH_STAGE_MIN_BLOCKS) k_batch_stage(
     const InstDesc* __restrict__ desc, char* __restrict__ pool, int parity, const int4* __restrict__ tiles, int spin,
@@ -2572,8 +2574,8 @@ __global__ void __launch_bounds__(BATCH_STAGE_NT, LBM_BATCH_STAGE_MIN_BLOCKS) k_
         reinterpret_cast<int*>(&sd)[w] = reinterpret_cast<const int*>(desc + t.x)[w];
     __syncthreads();
     const Buf<STO> A = inst_buf<STO>(sd, pool, parity), B = inst_buf<STO>(sd, pool, parity ^ 1);
-    stage_block<STO, BATCH_STAGE_RPT, BATCH_STAGE_NT, false>(sd.c, A, B, (const float*)(pool + sd.off_phi), (int)sd.plane,
-                                                      t.y, t.z, spin, status, sb);
+    stage_block<STO, BATCH_STAGE_NT, false>(sd.c, A, B, (const float*)(pool + sd.off_phi), (int)sd.plane, t.y, t.w, t.z,
+                                            spin, status, sb);
 }
 
 // Flow reference refresh of every node the tiles cover (all nodes of the active instances),
@@ -2778,6 +2780,7 @@ struct lbm_batch {
     int* wait_status = nullptr;       // 16-bit: LBM_ERR_TIMEOUT once a bounded wait of k_batch_stage ran out
     int spin = STAGE_SPIN;            // try_wait rounds of its per-row waits
     int stage = 1;                    // 16-bit: staged tiles for the even-nz instances (lbm_batch_set_staging)
+    int sms = 0;                      // multiprocessors of the device
     cudaGraphExec_t graph = nullptr;
     int64_t graph_steps = 0;
     int graph_parity = 0;             // batch parity the graph was captured at
@@ -2793,6 +2796,23 @@ static void batch_free_graph(lbm_batch* b) {
 
 // Rebuild the tile list, the active list and the wall prefix for the current active
 // set and block shape.
+// Rows per staged tile: the most (of 16, 8, 4, 2) that still leave the tiles at least four
+// waves of resident blocks, since a block overlaps only the copies of its own next row
+// with its compute (the 256-instance sweep ran at 0.844 ms per step with 16 rows, 0.847
+// with 8, 0.874 with 4 and 0.944 with 2; 16 small instances of 1 M nodes at 31.8 us with
+// 8 rows, 27.8 with 4 and 26.5 with 2).
+static int batch_stage_rows(const lbm_batch* b, const std::vector<int>& act) {
+    const int64_t want = 4LL * LBM_BATCH_STAGE_MIN_BLOCKS * b->sms;
+    for (int r = LBM_BATCH_STAGE_MAX_ROWS; r > 2; r /= 2) {
+        int64_t n = 0;
+        for (int i : act)
+            if (!(b->p[i].nz & 1))
+                n += (int64_t)((b->p[i].nr + r - 1) / r) * ((b->p[i].nz + 2 * BATCH_STAGE_NT - 1) / (2 * BATCH_STAGE_NT));
+        if (n >= want) return r;
+    }
+    return 2;
+}
+
 static int batch_rebuild(lbm_batch* b) {
     std::vector<int4> tiles, odd;   // tiles of instances with odd nz last (k_batch_bulk's VEC)
     std::vector<int> act, prefix(1, 0);
@@ -2808,11 +2828,13 @@ static int batch_rebuild(lbm_batch* b) {
     b->ntiles_even = (int)tiles.size();
     tiles.insert(tiles.end(), odd.begin(), odd.end());
     std::vector<int4> st;
-    if (b->storage != LBM_F32 && b->stage)
+    if (b->storage != LBM_F32 && b->stage) {
+        const int rpt = batch_stage_rows(b, act);
         for (int i : act)
             if (!(b->p[i].nz & 1))
-                for (int kr = 0; kr < b->p[i].nr; kr += BATCH_STAGE_RPT)
-                    for (int z0 = 0; z0 < b->p[i].nz; z0 += 2 * BATCH_STAGE_NT) st.push_back(make_int4(i, kr, z0, 0));
+                for (int kr = 0; kr < b->p[i].nr; kr += rpt)
+                    for (int z0 = 0; z0 < b->p[i].nz; z0 += 2 * BATCH_STAGE_NT) st.push_back(make_int4(i, kr, z0, rpt));
+    }
     b->nstiles = (int)st.size();
     if (st.size() > b->cap_stiles) {
         cudaFree(b->d_stiles);
@@ -2969,6 +2991,7 @@ int lbm_batch_create(const lbm_params* p, int32_t n, lbm_batch** out) {
     b->active.assign(n, 1);
     b->iparity.assign(n, 0);
     cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->wstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->wfork, cudaEventDisableTiming);
