@@ -194,6 +194,12 @@ def _bulk_bytes(info):
     return (NR - 2) * (NZ - 2) * (info.bytes_per_step // (NR * NZ))
 
 
+def _bulk_kernel(storage: str, inplace: int) -> str:
+    """The bulk kernel this workload launches: one node per thread for FP32 storage and in
+    place, the staged two-column kernel for 16-bit storage on two buffers."""
+    return f"k_bulk<{storage}>" if storage == "f32" or inplace else f"k_bulk_stage<{storage}>"
+
+
 def storage_variant(lbm, storage, phi, steps, warmup, peak, inplace=0):
     """Single-domain line for another storage type (or in-place storage): MLUPS, the bulk
     kernel's roofline fraction on its own bytes per node, and each kernel's mean launch
@@ -207,7 +213,7 @@ def storage_variant(lbm, storage, phi, steps, warmup, peak, inplace=0):
     info = s.info()
     s.close()
     achieved = _bulk_bytes(info) / (bulk_avg * 1e-3) / 1e9
-    return {"value": round(NR * NZ * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+    return {"value": round(NR * NZ * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS", "kernel": _bulk_kernel(storage, inplace),
             "ms_per_step": round(ms / steps, 5), "bytes_per_node": info.bytes_per_step // (NR * NZ),
             "bulk_avg_ms": round(bulk_avg, 5), "wall_avg_ms": round(wall_avg, 5),
             "achieved_gbs": round(achieved, 1), "frac": round(achieved / peak, 4),
@@ -291,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
                      "traffic": None if args.inplace else _traffic(args.storage),
-                     "kernel": f"k_bulk<{args.storage}>", "peak_source": f"{peak_kind} hbm_gbs",
+                     "kernel": _bulk_kernel(args.storage, int(args.inplace)), "peak_source": f"{peak_kind} hbm_gbs",
                      "avg_launch_ms": round(bulk_avg, 5), "bytes_per_launch": bulk_bytes,
                      "wall_kernel_avg_ms": round(wall_avg, 5)},
         "e2e": {"value": round(e2e_val, 2), "unit": "MLUPS", "h2d_bytes_per_step": nodes * 4,
