@@ -41,9 +41,9 @@ E2E_STEPS = 50                    # minimum length of the end-to-end window (ste
 # DRAM traffic of one k_bulk launch on the 4096 x 8192 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum of the bulk kernel in one single-pass ncu capture of this
 # benchmark), valid only for the bulk kernel's source it was taken on (_kernel_hash).
-TRAFFIC = {("f32", 4096, 8192): ("02bba3cda8e4e577", 2090031104 + 1827851264),
-           ("f16", 4096, 8192): ("02bba3cda8e4e577", 1690803968 + 1228190720),
-           ("bf16", 4096, 8192): ("02bba3cda8e4e577", 1689968640 + 1228090368)}
+TRAFFIC = {("f32", 4096, 8192): ("e47fb4700593f444", 2089953280 + 1827634944),
+           ("f16", 4096, 8192): ("e47fb4700593f444", 1690808064 + 1227835648),
+           ("bf16", 4096, 8192): ("e47fb4700593f444", 1689640704 + 1228074496)}
 
 
 def _kernel_hash() -> str:

@@ -553,11 +553,17 @@ __device__ __forceinline__ uint2 fref_make(float A, float Jr, float Jz, __half R
 // compiler's nine (measured 0.5303 vs 0.5425 ms at 4096 x 8192); FP32 is bandwidth-bound
 // and does best with the compiler's own allocation (56 registers, 0.6079 ms; 0.6119 with
 // nine blocks required, 0.6376 with ten).
-template <int STO>
-constexpr int bulk_min_blocks() { return STO == LBM_F32 ? 0 : 10; }
+// In place with 16-bit storage (one node per thread, shifted reads or stores): eight blocks
+// (64 registers) measured 0.693 ms at 4096 x 8192 against 0.716 with nine and 0.737 with
+// ten (48 registers, 36 bytes spilled).
+#ifndef LBM_INPLACE16_MIN_BLOCKS
+#define LBM_INPLACE16_MIN_BLOCKS 8
+#endif
+template <int STO, int LIN = LAY_N>
+constexpr int bulk_min_blocks() { return STO == LBM_F32 ? 0 : (LIN == LAY_N ? 10 : LBM_INPLACE16_MIN_BLOCKS); }
 
 template <int STO, typename I, int RPT, int LIN = LAY_N, int LOUT = LAY_N>
-__global__ void __launch_bounds__(BULK_THREADS, bulk_min_blocks<STO>()) k_bulk(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
+__global__ void __launch_bounds__(BULK_THREADS, bulk_min_blocks<STO, LIN>()) k_bulk(const Consts<float> c, const Buf<STO> A, const Buf<STO> B,
                                                        const typename St<STO>::P* __restrict__ phi, I plane) {
     const int kz = blockIdx.x * BULK_THREADS + threadIdx.x;
     if (kz >= c.nz) return;
